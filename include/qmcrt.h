@@ -1,0 +1,218 @@
+/*
+ * qmcrt.h -- C ABI of the GB300 (sm_103a) quasi-Monte Carlo radiative-transfer library.
+ *
+ * The library traces photon packets driven by low-discrepancy point sets through a
+ * dusty medium and accumulates their peel-off contributions into Stokes I/Q/U images,
+ * the method of S. G. Shulman, "Quasi-Monte Carlo Radiative Transfer" (arXiv:2406.15632).
+ * Section numbers below refer to that paper.
+ *
+ * Conventions for every entry point:
+ *  - Return an int status: QMCRT_OK (0) or a negative QMCRT_ERR_* code.  No C++
+ *    exception crosses the ABI.  qmcrt_last_error() returns a message for the last
+ *    failure on the calling thread (valid until that thread's next call).
+ *  - Pointers named d_* are device pointers owned by the caller; pointers to the
+ *    descriptor structs are host pointers read during the call only.  The library
+ *    allocates no device memory in any entry point.
+ *  - stream is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *    Work is enqueued asynchronously on it; the call returns after the launch.
+ *    Argument errors are detected on the host before anything is enqueued.
+ *  - Every descriptor starts with struct_size, which must equal sizeof(the struct);
+ *    a mismatch is QMCRT_ERR_INVALID_ARG (ABI version check).
+ *  - Point index i of a packet is its index in the point set; packets are numbered
+ *    from first_index (>= 1: the leading zero point is skipped, Sec. 3.1).
+ */
+#ifndef QMCRT_H
+#define QMCRT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QMCRT_ABI_VERSION 1
+
+/* ---- status codes ---- */
+#define QMCRT_OK 0
+#define QMCRT_ERR_INVALID_ARG (-1)    /* a NULL pointer, a size out of range, a bad enum */
+#define QMCRT_ERR_UNSUPPORTED (-2)    /* a valid combination the library does not implement */
+#define QMCRT_ERR_CUDA (-3)           /* a CUDA runtime call failed (launch, attribute query) */
+#define QMCRT_ERR_DEVICE_TIMEOUT (-4) /* a bounded device-side wait gave up */
+
+/* ---- point sets (Sec. 3.1) ---- */
+#define QMCRT_SOBOL 0      /* Sobol, Joe-Kuo direction numbers, Gray-code order */
+#define QMCRT_SOBOL_OWEN 1 /* Sobol with a hash-based nested uniform (Owen) scramble */
+#define QMCRT_HALTON 2     /* Halton, prime bases 2, 3, 5, ... */
+#define QMCRT_HAMMERSLEY 3 /* i/N in the first coordinate, Halton in the others */
+#define QMCRT_PHILOX 4     /* Philox4x32-10 pseudo-random numbers (Monte Carlo) */
+
+#define QMCRT_FMT_U32 0 /* raw 32-bit integers (Sobol, scrambled Sobol, Philox only) */
+#define QMCRT_FMT_F32 1 /* the FP64 value rounded toward zero to float */
+#define QMCRT_FMT_F64 2 /* integers: x * 2^-32 exactly; Halton: correctly rounded b-adic fraction */
+
+#define QMCRT_MAX_DIMS 256 /* coordinates per point */
+
+typedef struct qmcrt_points_desc {
+    uint32_t struct_size;
+    int32_t kind;         /* QMCRT_SOBOL .. QMCRT_PHILOX */
+    uint32_t dims;        /* 1 .. QMCRT_MAX_DIMS */
+    int32_t format;       /* QMCRT_FMT_* (used by qmcrt_generate_points only) */
+    uint64_t first_index; /* >= 1 */
+    uint64_t count;       /* points to produce / packets to trace */
+    uint64_t total_n;     /* Hammersley: N of the set (first_index + count - 1 <= total_n) */
+    uint64_t seed;        /* Owen scramble seed or Philox key */
+} qmcrt_points_desc;
+
+/*
+ * qmcrt_generate_points -- points first_index .. first_index+count-1 of the set (Sec. 3.1).
+ * d_out: device, row-major [count][dims] of uint32, float or double per d->format.
+ * Sobol point i is the XOR of the direction numbers over the set bits of the Gray code
+ * of i (random access; equal to the sequential construction of Bratley & Fox).
+ * Errors: INVALID_ARG for NULL pointers, dims outside 1..QMCRT_MAX_DIMS,
+ * first_index == 0, indices >= 2^32 for Sobol kinds, Halton/Hammersley with
+ * QMCRT_FMT_U32, a Hammersley index above total_n.
+ */
+int qmcrt_generate_points(const qmcrt_points_desc *d, void *d_out, void *stream);
+
+/* ---- medium (Sec. 2.1, 3.4) ---- */
+#define QMCRT_MEDIUM_GRID 0   /* Cartesian grid, constant kappa*rho per cell */
+#define QMCRT_MEDIUM_SPHERE 1 /* homogeneous sphere centred at the origin (analytic chords) */
+
+typedef struct qmcrt_medium {
+    uint32_t struct_size;
+    int32_t kind;
+    const float *d_k;  /* grid: device [nz][ny][nx] extinction kappa*rho per unit length, x fastest */
+    int32_t nx, ny, nz;
+    int32_t reserved;
+    double lo[3], hi[3]; /* grid box; every packet starts inside it */
+    double kscale;       /* multiplier on every cell (opacity at another wavelength) */
+    double sphere_r;     /* sphere medium: radius */
+    double sphere_k;     /* sphere medium: extinction per unit length */
+} qmcrt_medium;
+
+/* ---- source (Sec. 3.2, 3.3) ---- */
+#define QMCRT_SOURCE_POINT 0  /* point source at the origin: 3 coordinates (u, v, w) */
+#define QMCRT_SOURCE_SPHERE 1 /* star of radius r at the origin: 5 coordinates */
+#define QMCRT_ORDER_DIRECT 0  /* emission point, local direction, depth */
+#define QMCRT_ORDER_INVERSE 1 /* direction, depth, emission point relative to it */
+
+typedef struct qmcrt_source {
+    uint32_t struct_size;
+    int32_t kind;
+    double radius;  /* star radius (> 0 for a sphere source) */
+    double limb_u;  /* linear limb darkening I(mu) ~ 1 - u + u mu, 0 <= u <= 1 */
+    int32_t order;  /* QMCRT_ORDER_* */
+    int32_t reserved;
+} qmcrt_source;
+
+/* ---- dust (Sec. 2.2, 2.3): albedo, HG asymmetry g (|g| < 1), max linear polarization ---- */
+typedef struct qmcrt_dust {
+    uint32_t struct_size;
+    int32_t reserved;
+    double albedo, g, p_l;
+} qmcrt_dust;
+
+/* ---- observer and image (Sec. 3.6) ---- */
+#define QMCRT_SPLAT_NEAREST 0  /* whole contribution to the pixel that holds the point */
+#define QMCRT_SPLAT_BILINEAR 1 /* tent weights over the 4 nearest pixel centres */
+
+typedef struct qmcrt_observer {
+    uint32_t struct_size;
+    int32_t splat;
+    double theta, phi;  /* direction toward the observer, polar and azimuth angles */
+    double half_width;  /* the image covers [-hw, hw]^2 of the sky plane */
+    int32_t nx, ny;     /* pixels */
+} qmcrt_observer;
+/* Sky axes: ex = (-sin phi, cos phi, 0), ey = (-cos theta cos phi, -cos theta sin phi,
+ * sin theta); (ex, ey, k) is right-handed.  Stokes Q > 0 along ey, U > 0 along
+ * (ey - ex)/sqrt(2).  Pixel (ix, iy) = floor((x + hw) / (2 hw) * n); image layout
+ * [n_images][3 = I, Q, U][ny][nx]. */
+
+/* ---- accumulation buffer ---- */
+#define QMCRT_ACCUM_I64 0 /* two's-complement fixed point: value = raw * 2^-frac_bits (order-independent) */
+#define QMCRT_ACCUM_F64 1 /* IEEE double atomics */
+
+typedef struct qmcrt_image {
+    uint32_t struct_size;
+    int32_t accum;      /* QMCRT_ACCUM_* */
+    void *d_accum;      /* device [n_images][3][ny][nx] int64 or double; contributions are ADDED */
+    int32_t n_images;   /* 1, or max_orders with per-order images */
+    int32_t frac_bits;  /* I64: 0..62; pick so that |sum| * 2^frac_bits < 2^63 */
+} qmcrt_image;
+
+/* ---- trace options ---- */
+#define QMCRT_PREC_F32 0 /* march and phase math in float, compensated optical-depth sums */
+#define QMCRT_PREC_F64 1 /* everything in double (reference-grade, slow on this part) */
+#define QMCRT_FORCE_ALL 0   /* every order forced (weight 1 - e^-tau_edge) */
+#define QMCRT_FORCE_FIRST 1 /* only the first order forced; later depths -ln w (Sec. 3.5) */
+
+typedef struct qmcrt_trace_opts {
+    uint32_t struct_size;
+    int32_t precision;     /* QMCRT_PREC_* */
+    double tau_min;        /* packets with tau_1 below this contribute nothing (Sec. 3.2) */
+    int32_t max_orders;    /* qmcrt_trace_multiple: scatterings per packet, 1 .. 64 */
+    int32_t force_mode;    /* QMCRT_FORCE_* */
+    double rr_threshold;   /* Russian roulette when the weight drops below (0: off) */
+    double rr_survival;    /* survival probability (0, 1]; survivors' weight / rr_survival */
+    int32_t per_order;     /* 1: image k-1 receives scattering order k */
+    int32_t block_size;    /* threads per block, 0 = library default (multiple of 32, <= 1024) */
+} qmcrt_trace_opts;
+
+/*
+ * qmcrt_trace_single -- single scattering (Sec. 3.2-3.6).  For each packet i:
+ * emission from the first coordinates (Eq. point_source_propagation_direction, or the
+ * sphere-source orders of Sec. 3.3 with the limb weight); optical depth tau_1 to the
+ * grid edge; if tau_1 >= tau_min the packet is forced to scatter with weight
+ * 1 - e^{-tau_1} at depth -ln[1 - w (1 - e^{-tau_1})] (Eq. random_depth); the albedo
+ * multiplies the weight; the peel-off packet toward the observer carries
+ * W0 e^{-tau_obs} P(Theta_obs)/(4 pi) with the White polarization, is hidden if the
+ * star blocks its path, and is added to the pixel under its projection.
+ * Coordinates: point source (u, v, w) = dims (0, 1, 2); sphere source dims 0..4.
+ * pts->dims must be >= the coordinates used; pts->format is ignored.
+ * d_log (optional, NULL to skip): device double [count][9] = scattering x, y, z,
+ * peel-off I, Q, U, sky x, y, status (0 contributed, 1 tau_1 < tau_min, 2 occulted).
+ * Errors: INVALID_ARG (NULL descriptors, bad sizes or enums, |g| >= 1, albedo outside
+ * [0,1], a grid with NULL d_k or zero cells, first_index == 0), CUDA.
+ */
+int qmcrt_trace_single(const qmcrt_medium *medium, const qmcrt_source *source, const qmcrt_dust *dust,
+                       const qmcrt_observer *obs, const qmcrt_points_desc *pts, const qmcrt_trace_opts *opts,
+                       const qmcrt_image *image, double *d_log, void *stream);
+
+/*
+ * qmcrt_trace_multiple -- multiple scattering of a point source (Sec. 3.5, 3.7).
+ * Order k (1-based) reads coordinates 4(k-1) + {0: azimuth i1 = 2 pi u (emission
+ * phi at k = 1), 1: cos Theta from the HG inverse (emission theta at k = 1), 2: depth,
+ * 3: roulette}.  After the peel-off of order k the packet is rouletted if its weight
+ * is below rr_threshold, then scattered: the direction from HG, the Stokes vector
+ * rotated into the scattering plane and multiplied by M(Theta)/P11.  Orders stop at
+ * max_orders, at tau_edge < tau_min, on leaving the grid (FORCE_FIRST) or by roulette.
+ * pts->dims must be >= 4 * max_orders.  image->n_images must be max_orders when
+ * per_order is set, else 1.
+ * Errors: as qmcrt_trace_single; UNSUPPORTED for a sphere source.
+ */
+int qmcrt_trace_multiple(const qmcrt_medium *medium, const qmcrt_source *source, const qmcrt_dust *dust,
+                         const qmcrt_observer *obs, const qmcrt_points_desc *pts, const qmcrt_trace_opts *opts,
+                         const qmcrt_image *image, void *stream);
+
+/*
+ * qmcrt_image_reduce -- final image in units of the source luminosity (Sec. 3.6):
+ * d_out[j] = sum over the n_replicas accumulation buffers (each image->n_images x 3 x
+ * ny x nx, consecutive in memory from image->d_accum) of raw[j] * 2^-frac_bits
+ * (I64) or raw[j] (F64), times scale (normally 1/N).  d_out: device double, same
+ * layout as one buffer.
+ * Errors: INVALID_ARG (NULL pointers, sizes <= 0, n_replicas < 1), CUDA.
+ */
+int qmcrt_image_reduce(const qmcrt_image *image, int32_t nx, int32_t ny, int32_t n_replicas, double scale,
+                       double *d_out, void *stream);
+
+/* Thread-local message describing the last error (empty if none). */
+const char *qmcrt_last_error(void);
+
+/* QMCRT_ABI_VERSION of the loaded library. */
+int qmcrt_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QMCRT_H */

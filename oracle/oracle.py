@@ -235,11 +235,11 @@ def default_threads() -> int:
 
 def trace_single(prob, first: int, count: int, log: bool = False, nthreads: int | None = None):
     """Raw image sums [3][ny][nx] (not divided by N) of packets first..first+count-1,
-    and optionally the per-packet log [count][9]: scattering x, y, z, peel-off I, Q, U,
-    sky x, y, status."""
+    and optionally the per-packet log [count][10]: scattering x, y, z, peel-off I, Q, U,
+    sky x, y, status, grid cells visited."""
     h = _Holder(prob)
     img = np.zeros((3, prob.ny, prob.nx), dtype=np.float64)
-    lg = np.zeros((count, 9), dtype=np.float64) if log else None
+    lg = np.zeros((count, 10), dtype=np.float64) if log else None
     rc = lib().or_trace_single(h.ptr, first, count, img.ctypes.data_as(C.POINTER(C.c_double)),
                                lg.ctypes.data_as(C.POINTER(C.c_double)) if log else None,
                                nthreads or default_threads())

@@ -325,6 +325,10 @@ static int or_start_cell(double x, double lo, double h, double dir)
  * *t_last the far end of the last segment with nonzero density; return 0.
  * Ties between faces step x first, then y, then z (zero-length segments add 0).
  */
+/* Cells visited by the walks of the packet being traced on this thread (a count of the
+ * algorithm's work, reported in the packet log). */
+static _Thread_local long long or_cells_visited;
+
 static int or_grid_walk(const or_medium *M, const double p[3], const double d[3], double target,
                         double *tau_sum, double *t_hit, double *t_last)
 {
@@ -352,6 +356,7 @@ static int or_grid_walk(const or_medium *M, const double p[3], const double d[3]
         double te = tn[a] > t ? tn[a] : t;
         double kc = M->kscale * (double)M->k[((size_t)c[2] * M->n[1] + c[1]) * M->n[0] + c[0]];
         double dtau = (te - t) * kc;
+        ++or_cells_visited;
         if (target >= 0 && kc > 0 && tau + dtau >= target) {
             *t_hit = t + (target - tau) / kc;
             *tau_sum = target;
@@ -645,6 +650,8 @@ static int or_forced_step(const or_problem *Pr, double pos[3], const double dir[
     return 1;
 }
 
+#define OR_LOG_COLS 10
+
 typedef struct {
     const or_problem *Pr;
     uint64_t first, count;
@@ -661,6 +668,7 @@ static void or_trace_single_range(const or_problem *Pr, uint64_t first, uint64_t
     for (uint64_t j = 0; j < count; ++j) {
         uint64_t i = first + j;
         double pos[3], dir[3], eref[3], wgt, W1 = 0, tau1 = 0, S[3], out[3], x = 0, y = 0;
+        or_cells_visited = 0;
         double w = or_emit(&Pr->source, &Pr->points, i, pos, dir, eref, &wgt);
         int status = 0;
         out[0] = out[1] = out[2] = 0;
@@ -673,10 +681,11 @@ static void or_trace_single_range(const or_problem *Pr, uint64_t first, uint64_t
             else or_splat(&Pr->obs, img, x, y, out);
         }
         if (log) {
-            double *r = log + j * 9;
+            double *r = log + j * OR_LOG_COLS;
             r[0] = pos[0]; r[1] = pos[1]; r[2] = pos[2];
             r[3] = out[0]; r[4] = out[1]; r[5] = out[2];
             r[6] = x; r[7] = y; r[8] = status;
+            r[9] = (double)or_cells_visited;
         }
     }
 }
@@ -769,9 +778,9 @@ static void *or_worker(void *arg)
 }
 
 /* Trace packets first .. first+count-1 on nthreads threads; adds the raw sums
- * (not divided by N) to image; log (optional, single only) gets 9 doubles per packet:
- * scattering position, peel-off I, Q, U, sky x, y, status (0 ok, 1 tau_1 < tau_min,
- * 2 occulted). */
+ * (not divided by N) to image; log (optional, single only) gets OR_LOG_COLS doubles per
+ * packet: scattering position, peel-off I, Q, U, sky x, y, status (0 ok, 1 tau_1 <
+ * tau_min, 2 occulted), grid cells visited by the packet's walks. */
 static int or_trace(const or_problem *Pr, uint64_t first, uint64_t count, double *image, double *log,
                     int nthreads, int multiple)
 {
@@ -787,7 +796,7 @@ static int or_trace(const or_problem *Pr, uint64_t first, uint64_t count, double
         jobs[t].first = first + a;
         jobs[t].count = b - a;
         jobs[t].img = calloc(img_size, sizeof(double));
-        jobs[t].log = log ? log + a * 9 : NULL;
+        jobs[t].log = log ? log + a * OR_LOG_COLS : NULL;
         jobs[t].multiple = multiple;
         if (!jobs[t].img) return -1;
         pthread_create(&th[t], NULL, or_worker, &jobs[t]);

@@ -1,0 +1,287 @@
+// qmcrt_api.cu -- host side of the C ABI declared in include/qmcrt.h: argument
+// validation, kernel parameter blocks, launches.  No device memory is allocated here.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "qmcrt.h"
+#include "qmcrt_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int cuda_status(cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return QMCRT_OK;
+    return fail(QMCRT_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CHECK_STRUCT(p, T)                                                                         \
+    do {                                                                                           \
+        if (!(p)) return fail(QMCRT_ERR_INVALID_ARG, #p " is NULL");                               \
+        if ((p)->struct_size != sizeof(T))                                                         \
+            return fail(QMCRT_ERR_INVALID_ARG, #p "->struct_size %u != %zu (ABI mismatch)",        \
+                        (unsigned)(p)->struct_size, sizeof(T));                                    \
+    } while (0)
+
+int check_points(const qmcrt_points_desc *d, uint32_t dims_needed)
+{
+    CHECK_STRUCT(d, qmcrt_points_desc);
+    if (d->kind < QMCRT_SOBOL || d->kind > QMCRT_PHILOX) return fail(QMCRT_ERR_INVALID_ARG, "unknown point kind %d", d->kind);
+    if (d->dims < 1 || d->dims > QMCRT_MAX_DIMS)
+        return fail(QMCRT_ERR_INVALID_ARG, "dims %u outside 1..%d", d->dims, QMCRT_MAX_DIMS);
+    if (d->dims < dims_needed)
+        return fail(QMCRT_ERR_INVALID_ARG, "dims %u < %u coordinates used per packet", d->dims, dims_needed);
+    if (d->first_index == 0) return fail(QMCRT_ERR_INVALID_ARG, "first_index must be >= 1 (the zero point is skipped)");
+    const uint64_t last = d->first_index + (d->count ? d->count - 1 : 0);
+    if (last < d->first_index) return fail(QMCRT_ERR_INVALID_ARG, "index range overflows");
+    if (d->kind != QMCRT_PHILOX && last > 0xffffffffull)
+        return fail(QMCRT_ERR_INVALID_ARG, "point index %llu >= 2^32", (unsigned long long)last);
+    if (d->kind == QMCRT_HAMMERSLEY && (d->total_n == 0 || last > d->total_n))
+        return fail(QMCRT_ERR_INVALID_ARG, "Hammersley index %llu beyond N = %llu", (unsigned long long)last,
+                    (unsigned long long)d->total_n);
+    return QMCRT_OK;
+}
+
+qmcrt::PointsP make_points(const qmcrt_points_desc *d)
+{
+    qmcrt::PointsP p;
+    p.kind = d->kind;
+    p.dims = (int)d->dims;
+    p.seed = d->seed;
+    p.total_n = d->total_n;
+    p.inv_total_n = d->total_n ? 1.0 / (double)d->total_n : 0.0;
+    return p;
+}
+
+template <class T>
+int fill_trace(const qmcrt_medium *md, const qmcrt_source *src, const qmcrt_dust *du, const qmcrt_observer *ob,
+               const qmcrt_points_desc *pts, const qmcrt_trace_opts *op, const qmcrt_image *im, int multiple,
+               qmcrt::TraceP<T> &P)
+{
+    memset(&P, 0, sizeof P);
+    // medium
+    P.med.kind = md->kind;
+    if (!(md->kscale > 0) || !std::isfinite(md->kscale)) return fail(QMCRT_ERR_INVALID_ARG, "kscale must be > 0");
+    P.med.kscale = (T)md->kscale;
+    P.med.inv_kscale = (T)(1.0 / md->kscale);
+    if (md->kind == QMCRT_MEDIUM_GRID) {
+        if (!md->d_k) return fail(QMCRT_ERR_INVALID_ARG, "grid medium with NULL d_k");
+        if (md->nx < 1 || md->ny < 1 || md->nz < 1) return fail(QMCRT_ERR_INVALID_ARG, "grid has zero cells");
+        if ((double)md->nx * md->ny * md->nz > 2147483647.0)
+            return fail(QMCRT_ERR_INVALID_ARG, "grid larger than 2^31 cells");
+        const int n[3] = {md->nx, md->ny, md->nz};
+        for (int a = 0; a < 3; ++a) {
+            if (!(md->hi[a] > md->lo[a])) return fail(QMCRT_ERR_INVALID_ARG, "grid box axis %d is empty", a);
+            P.med.n[a] = n[a];
+            P.med.lo[a] = (T)md->lo[a];
+            P.med.hi[a] = (T)md->hi[a];
+            P.med.h[a] = (T)((md->hi[a] - md->lo[a]) / n[a]);
+        }
+        P.med.stride[0] = 1;
+        P.med.stride[1] = md->nx;
+        P.med.stride[2] = md->nx * md->ny;
+        P.med.k = md->d_k;
+    } else if (md->kind == QMCRT_MEDIUM_SPHERE) {
+        if (!(md->sphere_r > 0) || !(md->sphere_k >= 0)) return fail(QMCRT_ERR_INVALID_ARG, "sphere medium needs r > 0, k >= 0");
+        P.med.sph_r = (T)md->sphere_r;
+        P.med.sph_k = (T)(md->sphere_k * md->kscale);
+    } else {
+        return fail(QMCRT_ERR_INVALID_ARG, "unknown medium kind %d", md->kind);
+    }
+    // source
+    if (src->kind == QMCRT_SOURCE_POINT) {
+        P.src.kind = src->kind;
+        P.src.limb_u = T(0);
+        P.src.limb_norm = T(1);
+    } else if (src->kind == QMCRT_SOURCE_SPHERE) {
+        if (!(src->radius > 0)) return fail(QMCRT_ERR_INVALID_ARG, "sphere source needs radius > 0");
+        if (!(src->limb_u >= 0 && src->limb_u <= 1)) return fail(QMCRT_ERR_INVALID_ARG, "limb_u outside [0, 1]");
+        if (src->order != QMCRT_ORDER_DIRECT && src->order != QMCRT_ORDER_INVERSE)
+            return fail(QMCRT_ERR_INVALID_ARG, "unknown emission order %d", src->order);
+        if (multiple) return fail(QMCRT_ERR_UNSUPPORTED, "multiple scattering supports the point source only");
+        P.src.kind = src->kind;
+        P.src.order = src->order;
+        P.src.R = (T)src->radius;
+        P.src.limb_u = (T)src->limb_u;
+        P.src.limb_norm = (T)(1.0 / (1.0 - src->limb_u / 3.0));
+    } else {
+        return fail(QMCRT_ERR_INVALID_ARG, "unknown source kind %d", src->kind);
+    }
+    // dust
+    if (!(du->albedo >= 0 && du->albedo <= 1)) return fail(QMCRT_ERR_INVALID_ARG, "albedo outside [0, 1]");
+    if (!(std::fabs(du->g) < 1)) return fail(QMCRT_ERR_INVALID_ARG, "|g| must be < 1");
+    if (!(du->p_l >= 0 && du->p_l <= 1)) return fail(QMCRT_ERR_INVALID_ARG, "p_l outside [0, 1]");
+    P.dust.albedo = (T)du->albedo;
+    P.dust.g = (T)du->g;
+    P.dust.p_l = (T)du->p_l;
+    P.dust.one_m_g2 = (T)(1.0 - du->g * du->g);
+    P.dust.one_p_g2 = (T)(1.0 + du->g * du->g);
+    P.dust.two_g = (T)(2.0 * du->g);
+    P.dust.isotropic = std::fabs(du->g) < 1e-6;
+    // observer
+    if (ob->nx < 1 || ob->ny < 1) return fail(QMCRT_ERR_INVALID_ARG, "image has no pixels");
+    if (!(ob->half_width > 0)) return fail(QMCRT_ERR_INVALID_ARG, "half_width must be > 0");
+    if (ob->splat != QMCRT_SPLAT_NEAREST && ob->splat != QMCRT_SPLAT_BILINEAR)
+        return fail(QMCRT_ERR_INVALID_ARG, "unknown splat mode %d", ob->splat);
+    {
+        const double st = std::sin(ob->theta), ct = std::cos(ob->theta), sp = std::sin(ob->phi), cp = std::cos(ob->phi);
+        const double k[3] = {st * cp, st * sp, ct}, ex[3] = {-sp, cp, 0.0}, ey[3] = {-ct * cp, -ct * sp, st};
+        for (int a = 0; a < 3; ++a) {
+            P.obs.k[a] = (T)k[a];
+            P.obs.ex[a] = (T)ex[a];
+            P.obs.ey[a] = (T)ey[a];
+        }
+        P.obs.hw = (T)ob->half_width;
+        P.obs.pix_x = (T)(ob->nx / (2.0 * ob->half_width));
+        P.obs.pix_y = (T)(ob->ny / (2.0 * ob->half_width));
+        P.obs.nx = ob->nx;
+        P.obs.ny = ob->ny;
+        P.obs.splat = ob->splat;
+    }
+    // options
+    if (op->precision != QMCRT_PREC_F32 && op->precision != QMCRT_PREC_F64)
+        return fail(QMCRT_ERR_INVALID_ARG, "unknown precision %d", op->precision);
+    if (!(op->tau_min >= 0)) return fail(QMCRT_ERR_INVALID_ARG, "tau_min must be >= 0");
+    if (op->block_size != 0 && (op->block_size % 32 != 0 || op->block_size < 32 || op->block_size > 256))
+        return fail(QMCRT_ERR_INVALID_ARG, "block_size must be a multiple of 32 in 32..256");
+    P.tau_min = (T)op->tau_min;
+    P.max_orders = multiple ? op->max_orders : 1;
+    if (multiple) {
+        if (op->max_orders < 1 || op->max_orders > 64) return fail(QMCRT_ERR_INVALID_ARG, "max_orders outside 1..64");
+        if (op->force_mode != QMCRT_FORCE_ALL && op->force_mode != QMCRT_FORCE_FIRST)
+            return fail(QMCRT_ERR_INVALID_ARG, "unknown force mode %d", op->force_mode);
+        if (!(op->rr_threshold >= 0)) return fail(QMCRT_ERR_INVALID_ARG, "rr_threshold must be >= 0");
+        if (!(op->rr_survival > 0 && op->rr_survival <= 1)) return fail(QMCRT_ERR_INVALID_ARG, "rr_survival outside (0, 1]");
+        P.force_all = op->force_mode == QMCRT_FORCE_ALL;
+        P.per_order = op->per_order != 0;
+        P.rr_threshold = (T)op->rr_threshold;
+        P.rr_survival = (T)op->rr_survival;
+        P.inv_rr_survival = (T)(1.0 / op->rr_survival);
+    }
+    // points
+    const uint32_t need = multiple ? 4u * (uint32_t)op->max_orders : (src->kind == QMCRT_SOURCE_SPHERE ? 5u : 3u);
+    int rc = check_points(pts, need);
+    if (rc) return rc;
+    P.pts = make_points(pts);
+    P.first = pts->first_index;
+    P.count = pts->count;
+    P.stride = (pts->count + 31) / 32;
+    // image
+    if (!im->d_accum) return fail(QMCRT_ERR_INVALID_ARG, "image->d_accum is NULL");
+    if (im->accum != QMCRT_ACCUM_I64 && im->accum != QMCRT_ACCUM_F64)
+        return fail(QMCRT_ERR_INVALID_ARG, "unknown accumulation mode %d", im->accum);
+    if (im->accum == QMCRT_ACCUM_I64 && (im->frac_bits < 0 || im->frac_bits > 62))
+        return fail(QMCRT_ERR_INVALID_ARG, "frac_bits outside 0..62");
+    const int want_images = (multiple && op->per_order) ? op->max_orders : 1;
+    if (im->n_images != want_images)
+        return fail(QMCRT_ERR_INVALID_ARG, "image->n_images = %d, expected %d", im->n_images, want_images);
+    P.acc.ptr = im->d_accum;
+    P.acc.mode = im->accum;
+    P.acc.n_images = im->n_images;
+    P.acc.scale = std::ldexp(1.0, im->frac_bits);
+    P.acc.plane = (size_t)ob->nx * ob->ny;
+    return QMCRT_OK;
+}
+
+int trace_common(const qmcrt_medium *md, const qmcrt_source *src, const qmcrt_dust *du, const qmcrt_observer *ob,
+                 const qmcrt_points_desc *pts, const qmcrt_trace_opts *op, const qmcrt_image *im, double *d_log,
+                 void *stream, int multiple)
+{
+    CHECK_STRUCT(md, qmcrt_medium);
+    CHECK_STRUCT(src, qmcrt_source);
+    CHECK_STRUCT(du, qmcrt_dust);
+    CHECK_STRUCT(ob, qmcrt_observer);
+    CHECK_STRUCT(op, qmcrt_trace_opts);
+    CHECK_STRUCT(im, qmcrt_image);
+    const int block = op->block_size ? op->block_size : 256;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (op->precision == QMCRT_PREC_F64) {
+        qmcrt::TraceP<double> P;
+        int rc = fill_trace<double>(md, src, du, ob, pts, op, im, multiple, P);
+        if (rc) return rc;
+        P.log = d_log;
+        return cuda_status(multiple ? qmcrt::launch_trace_multiple_f64(P, block, s)
+                                    : qmcrt::launch_trace_single_f64(P, block, s),
+                           "trace launch");
+    }
+    qmcrt::TraceP<float> P;
+    int rc = fill_trace<float>(md, src, du, ob, pts, op, im, multiple, P);
+    if (rc) return rc;
+    P.log = d_log;
+    return cuda_status(multiple ? qmcrt::launch_trace_multiple_f32(P, block, s) : qmcrt::launch_trace_single_f32(P, block, s),
+                       "trace launch");
+}
+
+}  // namespace
+
+extern "C" {
+
+int qmcrt_abi_version(void) { return QMCRT_ABI_VERSION; }
+
+const char *qmcrt_last_error(void) { return g_last_error.c_str(); }
+
+int qmcrt_generate_points(const qmcrt_points_desc *d, void *d_out, void *stream)
+{
+    g_last_error.clear();
+    int rc = check_points(d, 1);
+    if (rc) return rc;
+    if (!d_out) return fail(QMCRT_ERR_INVALID_ARG, "d_out is NULL");
+    if (d->format != QMCRT_FMT_U32 && d->format != QMCRT_FMT_F32 && d->format != QMCRT_FMT_F64)
+        return fail(QMCRT_ERR_INVALID_ARG, "unknown format %d", d->format);
+    if (d->format == QMCRT_FMT_U32 && (d->kind == QMCRT_HALTON || d->kind == QMCRT_HAMMERSLEY))
+        return fail(QMCRT_ERR_INVALID_ARG, "Halton/Hammersley points have no 32-bit integer form");
+    return cuda_status(qmcrt::launch_generate_points(make_points(d), d->first_index, d->count, d->format, d_out,
+                                                     (cudaStream_t)stream),
+                       "generate_points launch");
+}
+
+int qmcrt_trace_single(const qmcrt_medium *medium, const qmcrt_source *source, const qmcrt_dust *dust,
+                       const qmcrt_observer *obs, const qmcrt_points_desc *pts, const qmcrt_trace_opts *opts,
+                       const qmcrt_image *image, double *d_log, void *stream)
+{
+    g_last_error.clear();
+    return trace_common(medium, source, dust, obs, pts, opts, image, d_log, stream, 0);
+}
+
+int qmcrt_trace_multiple(const qmcrt_medium *medium, const qmcrt_source *source, const qmcrt_dust *dust,
+                         const qmcrt_observer *obs, const qmcrt_points_desc *pts, const qmcrt_trace_opts *opts,
+                         const qmcrt_image *image, void *stream)
+{
+    g_last_error.clear();
+    return trace_common(medium, source, dust, obs, pts, opts, image, nullptr, stream, 1);
+}
+
+int qmcrt_image_reduce(const qmcrt_image *image, int32_t nx, int32_t ny, int32_t n_replicas, double scale,
+                       double *d_out, void *stream)
+{
+    g_last_error.clear();
+    CHECK_STRUCT(image, qmcrt_image);
+    if (!image->d_accum || !d_out) return fail(QMCRT_ERR_INVALID_ARG, "NULL buffer");
+    if (nx < 1 || ny < 1 || image->n_images < 1 || n_replicas < 1)
+        return fail(QMCRT_ERR_INVALID_ARG, "sizes must be >= 1");
+    if (image->accum != QMCRT_ACCUM_I64 && image->accum != QMCRT_ACCUM_F64)
+        return fail(QMCRT_ERR_INVALID_ARG, "unknown accumulation mode %d", image->accum);
+    if (image->accum == QMCRT_ACCUM_I64 && (image->frac_bits < 0 || image->frac_bits > 62))
+        return fail(QMCRT_ERR_INVALID_ARG, "frac_bits outside 0..62");
+    const size_t elems = (size_t)image->n_images * 3 * nx * ny;
+    return cuda_status(qmcrt::launch_image_reduce(image->d_accum, image->accum, std::ldexp(1.0, -image->frac_bits), elems,
+                                                  n_replicas, scale, d_out, (cudaStream_t)stream),
+                       "image_reduce launch");
+}
+
+}  // extern "C"

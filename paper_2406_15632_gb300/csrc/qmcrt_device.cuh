@@ -1,0 +1,712 @@
+// qmcrt_device.cuh -- device building blocks of the tracer: point generators (Sec. 3.1),
+// sources (Sec. 3.2, 3.3), the cell walk (Sec. 3.4), Henyey-Greenstein / White
+// scattering (Sec. 2.2, 3.5), peel-off (Sec. 3.6) and warp-aggregated image deposits.
+//
+// Everything is templated on the arithmetic type T: float is the production path
+// (compensated optical-depth sums, FP64 or fixed-point images), double the
+// reference-grade path.  One thread traces one packet.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "qmcrt.h"
+#include "qmcrt_internal.h"
+#include "qmcrt_tables.h"
+
+namespace qmcrt {
+
+// Sobol direction numbers V[d][k] for bit k of the Gray-code index, and Halton bases.
+static __constant__ uint32_t c_sobol_v[QMCRT_GEN_DIMS][32] = QMCRT_GEN_SOBOL_V_INIT;
+static __constant__ uint32_t c_primes[QMCRT_GEN_DIMS] = QMCRT_GEN_PRIMES_INIT;
+
+constexpr unsigned FULL_MASK = 0xffffffffu;
+
+// ------------------------------------------------------------------------------------
+// Math in T
+// ------------------------------------------------------------------------------------
+template <class T>
+struct Mth;
+
+template <>
+struct Mth<float> {
+    static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+    static __device__ __forceinline__ float exp_(float x) { return expf(x); }
+    static __device__ __forceinline__ float expm1_(float x) { return expm1f(x); }
+    static __device__ __forceinline__ float log1p_(float x) { return log1pf(x); }
+    static __device__ __forceinline__ float log_(float x) { return logf(x); }
+    static __device__ __forceinline__ void sincospi_(float x, float *s, float *c) { sincospif(x, s, c); }
+    static __device__ __forceinline__ float floor_(float x) { return floorf(x); }
+    static __device__ __forceinline__ float min_(float a, float b) { return fminf(a, b); }
+    static __device__ __forceinline__ float max_(float a, float b) { return fmaxf(a, b); }
+    static __device__ __forceinline__ float inf() { return __int_as_float(0x7f800000); }
+    // value of a 32-bit point coordinate: x * 2^-32 rounded toward zero
+    static __device__ __forceinline__ float from_u32(uint32_t x) { return __uint2float_rz(x) * 0x1p-32f; }
+    static __device__ __forceinline__ float from_f64(double v) { return __double2float_rz(v); }
+    static __device__ __forceinline__ long long to_fixed(float v, double scale)
+    {
+        return __float2ll_rn(v * (float)scale);  // exact power-of-two scaling, one rounding
+    }
+};
+
+template <>
+struct Mth<double> {
+    static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+    static __device__ __forceinline__ double exp_(double x) { return exp(x); }
+    static __device__ __forceinline__ double expm1_(double x) { return expm1(x); }
+    static __device__ __forceinline__ double log1p_(double x) { return log1p(x); }
+    static __device__ __forceinline__ double log_(double x) { return log(x); }
+    static __device__ __forceinline__ void sincospi_(double x, double *s, double *c) { sincospi(x, s, c); }
+    static __device__ __forceinline__ double floor_(double x) { return floor(x); }
+    static __device__ __forceinline__ double min_(double a, double b) { return fmin(a, b); }
+    static __device__ __forceinline__ double max_(double a, double b) { return fmax(a, b); }
+    static __device__ __forceinline__ double inf() { return __longlong_as_double(0x7ff0000000000000ll); }
+    static __device__ __forceinline__ double from_u32(uint32_t x) { return (double)x * 0x1p-32; }
+    static __device__ __forceinline__ double from_f64(double v) { return v; }
+    static __device__ __forceinline__ long long to_fixed(double v, double scale) { return __double2ll_rn(v * scale); }
+};
+
+template <class T>
+__device__ __forceinline__ T dot3(const T a[3], const T b[3])
+{
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+template <class T>
+__device__ __forceinline__ void cross3(const T a[3], const T b[3], T c[3])
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+template <class T>
+__device__ __forceinline__ void normalize3(T a[3])
+{
+    T inv = T(1) / Mth<T>::sqrt_(dot3(a, a));
+    a[0] *= inv;
+    a[1] *= inv;
+    a[2] *= inv;
+}
+
+// ------------------------------------------------------------------------------------
+// Point generators (Sec. 3.1)
+// ------------------------------------------------------------------------------------
+
+// Sobol: XOR of the direction numbers over the set bits of gray(i).  The loop is
+// uniform across the warp so every constant load is a broadcast.
+__device__ __forceinline__ uint32_t sobol_u32(uint32_t i, int d)
+{
+    const uint32_t g = i ^ (i >> 1);
+    uint32_t x = 0;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) x ^= (g & (1u << k)) ? c_sobol_v[d][k] : 0u;
+    return x;
+}
+
+// MurmurHash3 finaliser, for per-dimension scramble seeds.
+__device__ __forceinline__ uint32_t fmix32(uint32_t h)
+{
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
+__device__ __forceinline__ uint32_t owen_seed(uint64_t seed, int d)
+{
+    return fmix32((uint32_t)seed ^ fmix32((uint32_t)(seed >> 32) + 0x9e3779b9u * (uint32_t)(d + 1)));
+}
+
+// Hash-based nested uniform scramble (Owen 1997, in the Laine-Karras / Burley 2020
+// form): in bit-reversed order, output bit j = input bit j XOR f(bits below j, seed).
+__device__ __forceinline__ uint32_t owen_scramble(uint32_t x, uint32_t s)
+{
+    uint32_t r = __brev(x);
+    r += s;
+    r ^= r * 0x6a09e666u;
+    r ^= r * 0xbb67ae84u;
+    r ^= r * 0x3c6ef372u;
+    r ^= r * 0xa54ff53au;
+    return __brev(r);
+}
+
+// Philox4x32-10 (Salmon et al. 2011).
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint32_t philox_u32(uint64_t seed, uint64_t i, int d)
+{
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)(i >> 32), (uint32_t)(d >> 2), 0u),
+                                  make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+    const int s = d & 3;
+    return s == 0 ? w.x : s == 1 ? w.y : s == 2 ? w.z : w.w;
+}
+
+// Radical inverse in base b as the exact fraction num / b^k, one correctly rounded
+// division (b^k < 2^53 for every index < 2^32 and base in the table).
+__device__ __forceinline__ double radical_inverse(uint32_t i, uint32_t b)
+{
+    if (b == 2) return (double)__brev(i) * 0x1p-32;
+    uint64_t num = 0, den = 1;
+    while (i) {
+        const uint32_t q = i / b;
+        num = num * b + (i - q * b);
+        den *= b;
+        i = q;
+    }
+    return (double)num / (double)den;
+}
+
+__device__ __forceinline__ bool is_integer_kind(int kind)
+{
+    return kind == QMCRT_SOBOL || kind == QMCRT_SOBOL_OWEN || kind == QMCRT_PHILOX;
+}
+
+__device__ __forceinline__ uint32_t point_u32(const PointsP &P, uint64_t i, int d)
+{
+    if (P.kind == QMCRT_PHILOX) return philox_u32(P.seed, i, d);
+    uint32_t x = sobol_u32((uint32_t)i, d);
+    if (P.kind == QMCRT_SOBOL_OWEN) x = owen_scramble(x, owen_seed(P.seed, d));
+    return x;
+}
+
+__device__ __forceinline__ double point_f64(const PointsP &P, uint64_t i, int d)
+{
+    if (P.kind == QMCRT_HALTON) return radical_inverse((uint32_t)i, c_primes[d]);
+    if (P.kind == QMCRT_HAMMERSLEY) {
+        if (d == 0) return (double)i / (double)P.total_n;
+        return radical_inverse((uint32_t)i, c_primes[d - 1]);
+    }
+    return (double)point_u32(P, i, d) * 0x1p-32;
+}
+
+template <class T>
+__device__ __forceinline__ T point(const PointsP &P, uint64_t i, int d)
+{
+    if (is_integer_kind(P.kind)) return Mth<T>::from_u32(point_u32(P, i, d));
+    return Mth<T>::from_f64(point_f64(P, i, d));
+}
+
+// ------------------------------------------------------------------------------------
+// Optical depth along a ray (Sec. 3.4)
+// ------------------------------------------------------------------------------------
+
+// Cell of coordinate x; on a face, the cell the ray enters.
+template <class T>
+__device__ __forceinline__ int start_cell(T x, T lo, T h, T d)
+{
+    const T f = (x - lo) / h;
+    const T fl = Mth<T>::floor_(f);
+    int c = (int)fl;
+    if (f == fl && d < T(0)) c -= 1;
+    return c;
+}
+
+template <class T>
+struct AxisWalk {
+    T t_next, dt;
+    int step, left;
+};
+
+template <class T>
+__device__ __forceinline__ AxisWalk<T> axis_setup(T p, T d, int c, T lo, T h, int n, int stride)
+{
+    AxisWalk<T> a;
+    if (d > T(0)) {
+        a.t_next = (lo + T(c + 1) * h - p) / d;
+        a.dt = h / d;
+        a.step = stride;
+        a.left = n - 1 - c;
+    } else if (d < T(0)) {
+        a.t_next = (lo + T(c) * h - p) / d;
+        a.dt = -h / d;
+        a.step = -stride;
+        a.left = c;
+    } else {
+        // never the nearest face unless every axis is (a zero direction): then the
+        // walk ends at once instead of stepping in place
+        a.t_next = Mth<T>::inf();
+        a.dt = T(0);
+        a.step = 0;
+        a.left = 0;
+    }
+    return a;
+}
+
+// Walk through the grid cells from p along unit d.
+//   TARGET = false: returns the optical depth to the grid edge in tau_out.
+//   TARGET = true : stops where the optical depth reaches target (true, t_out = path
+//                   length), or leaves the grid first (false, t_out = far end of the
+//                   last segment with nonzero density).
+// Sums run over raw cell values (the caller scales by kscale) with Kahan compensation.
+template <class T, bool TARGET>
+__device__ __forceinline__ bool grid_walk(const MediumP<T> &G, const T p[3], const T d[3], T target_raw, T &tau_raw,
+                                          T &t_out)
+{
+    const int cx = start_cell(p[0], G.lo[0], G.h[0], d[0]);
+    const int cy = start_cell(p[1], G.lo[1], G.h[1], d[1]);
+    const int cz = start_cell(p[2], G.lo[2], G.h[2], d[2]);
+    tau_raw = T(0);
+    t_out = T(0);
+    if (cx < 0 || cx >= G.n[0] || cy < 0 || cy >= G.n[1] || cz < 0 || cz >= G.n[2]) return false;
+    AxisWalk<T> X = axis_setup(p[0], d[0], cx, G.lo[0], G.h[0], G.n[0], G.stride[0]);
+    AxisWalk<T> Y = axis_setup(p[1], d[1], cy, G.lo[1], G.h[1], G.n[1], G.stride[1]);
+    AxisWalk<T> Z = axis_setup(p[2], d[2], cz, G.lo[2], G.h[2], G.n[2], G.stride[2]);
+    int idx = cx * G.stride[0] + cy * G.stride[1] + cz * G.stride[2];
+    const float *__restrict__ K = G.k;
+    T t = T(0), acc = TARGET ? target_raw : T(0), comp = T(0), t_last = T(0);
+    for (;;) {
+        const T kc = (T)__ldg(K + idx);
+        const T tm = Mth<T>::min_(X.t_next, Mth<T>::min_(Y.t_next, Z.t_next));
+        const T dtau = (tm - t) * kc;
+        if (TARGET) {
+            const T rem = acc - comp;
+            if (kc > T(0) && dtau >= rem) {
+                t_out = t + rem / kc;
+                tau_raw = target_raw;
+                return true;
+            }
+            const T y = -dtau - comp;  // acc -= dtau, compensated
+            const T s = acc + y;
+            comp = (s - acc) - y;
+            acc = s;
+            if (kc > T(0) && tm > t) t_last = tm;
+        } else {
+            const T y = dtau - comp;  // acc += dtau, compensated
+            const T s = acc + y;
+            comp = (s - acc) - y;
+            acc = s;
+        }
+        t = tm;
+        if (X.t_next == tm) {
+            if (X.left-- == 0) break;
+            idx += X.step;
+            X.t_next += X.dt;
+        } else if (Y.t_next == tm) {
+            if (Y.left-- == 0) break;
+            idx += Y.step;
+            Y.t_next += Y.dt;
+        } else {
+            if (Z.left-- == 0) break;
+            idx += Z.step;
+            Z.t_next += Z.dt;
+        }
+    }
+    if (TARGET) {
+        t_out = t_last;
+        tau_raw = target_raw - (acc - comp);
+    } else {
+        tau_raw = acc - comp;
+    }
+    return false;
+}
+
+// Distance from p (inside) along unit d to the sphere of radius r at the origin.
+template <class T>
+__device__ __forceinline__ T sphere_exit(const T p[3], const T d[3], T r)
+{
+    const T b = dot3(p, d);
+    const T c = dot3(p, p) - r * r;
+    const T disc = Mth<T>::max_(b * b - c, T(0));
+    return Mth<T>::max_(-b + Mth<T>::sqrt_(disc), T(0));
+}
+
+// Optical depth from p along d to the edge of the medium.
+template <class T>
+__device__ __forceinline__ T tau_to_edge(const MediumP<T> &G, const T p[3], const T d[3])
+{
+    if (G.kind == QMCRT_MEDIUM_SPHERE) {
+        if (dot3(p, p) > G.sph_r * G.sph_r) return T(0);
+        return G.sph_k * sphere_exit(p, d, G.sph_r);
+    }
+    T raw, t;
+    grid_walk<T, false>(G, p, d, T(0), raw, t);
+    return raw * G.kscale;
+}
+
+// Move pos along d through optical depth tau; false if the ray leaves first (pos is
+// then the far end of the last nonempty segment).
+template <class T>
+__device__ __forceinline__ bool march(const MediumP<T> &G, T pos[3], const T d[3], T tau)
+{
+    T t;
+    bool hit;
+    if (G.kind == QMCRT_MEDIUM_SPHERE) {
+        const T s = sphere_exit(pos, d, G.sph_r);
+        hit = G.sph_k > T(0) && tau < G.sph_k * s;
+        t = hit ? tau / G.sph_k : s;
+    } else {
+        T raw;
+        hit = grid_walk<T, true>(G, pos, d, tau * G.inv_kscale, raw, t);
+    }
+    pos[0] += t * d[0];
+    pos[1] += t * d[1];
+    pos[2] += t * d[2];
+    return hit;
+}
+
+// Forced scattering (Sec. 3.2): weight 1 - e^{-tau_1}, depth -ln[1 - w (1 - e^{-tau_1})].
+template <class T>
+__device__ __forceinline__ bool forced_step(const TraceP<T> &P, T pos[3], const T d[3], T w, T &W1)
+{
+    const T tau1 = tau_to_edge(P.med, pos, d);
+    if (!(tau1 >= P.tau_min)) return false;
+    W1 = -Mth<T>::expm1_(-tau1);
+    const T tau = -Mth<T>::log1p_(-w * W1);
+    march(P.med, pos, d, tau);
+    return true;
+}
+
+// ------------------------------------------------------------------------------------
+// Sources (Sec. 3.2, 3.3)
+// ------------------------------------------------------------------------------------
+
+// Unit vector from cos(theta) = c and phi = 2 pi u, with its e_theta axis.
+template <class T>
+__device__ __forceinline__ void direction_from(T u, T v, T d[3], T et[3], T &sp, T &cp)
+{
+    Mth<T>::sincospi_(T(2) * u, &sp, &cp);
+    const T ct = T(2) * v - T(1);
+    const T st = T(2) * Mth<T>::sqrt_(Mth<T>::max_(v * (T(1) - v), T(0)));
+    d[0] = st * cp;
+    d[1] = st * sp;
+    d[2] = ct;
+    et[0] = ct * cp;
+    et[1] = ct * sp;
+    et[2] = -st;
+}
+
+// e_theta of a unit vector given by components.
+template <class T>
+__device__ __forceinline__ void e_theta_of(const T d[3], T et[3])
+{
+    const T s = Mth<T>::sqrt_(d[0] * d[0] + d[1] * d[1]);
+    T cp = T(1), sp = T(0);
+    if (s > T(0)) {
+        cp = d[0] / s;
+        sp = d[1] / s;
+    }
+    et[0] = d[2] * cp;
+    et[1] = d[2] * sp;
+    et[2] = -s;
+}
+
+// Emission of packet i: position, direction, Stokes axis, weight; returns the depth
+// coordinate w.
+template <class T>
+__device__ __forceinline__ T emit(const TraceP<T> &P, uint64_t i, T pos[3], T d[3], T a[3], T &wgt)
+{
+    wgt = T(1);
+    T sp, cp;
+    if (P.src.kind == QMCRT_SOURCE_POINT) {
+        direction_from(point<T>(P.pts, i, 0), point<T>(P.pts, i, 1), d, a, sp, cp);
+        pos[0] = pos[1] = pos[2] = T(0);
+        return point<T>(P.pts, i, 2);
+    }
+    const T R = P.src.R;
+    T mu, w;
+    if (P.src.order == QMCRT_ORDER_DIRECT) {
+        // v1, v2: emission point; v3, v4: local direction (cos theta_l = sqrt(v4),
+        // cosine-weighted outward hemisphere); v5: depth.
+        T ne[3], et[3];
+        direction_from(point<T>(P.pts, i, 0), point<T>(P.pts, i, 1), ne, et, sp, cp);
+        const T ep[3] = {-sp, cp, T(0)};
+        T spl, cpl;
+        Mth<T>::sincospi_(T(2) * point<T>(P.pts, i, 2), &spl, &cpl);
+        const T v4 = point<T>(P.pts, i, 3);
+        mu = Mth<T>::sqrt_(v4);
+        const T sl = Mth<T>::sqrt_(Mth<T>::max_(T(1) - v4, T(0)));
+        for (int q = 0; q < 3; ++q) {
+            pos[q] = R * ne[q];
+            d[q] = sl * cpl * et[q] + sl * spl * ep[q] + mu * ne[q];
+        }
+        normalize3(d);
+        e_theta_of(d, a);
+        w = point<T>(P.pts, i, 4);
+    } else {
+        // v1, v2: direction; v3: depth; v4, v5: emission point uniform on the star's
+        // projected disk across the direction, lifted onto the facing hemisphere.
+        direction_from(point<T>(P.pts, i, 0), point<T>(P.pts, i, 1), d, a, sp, cp);
+        const T ep[3] = {-sp, cp, T(0)};
+        w = point<T>(P.pts, i, 2);
+        const T v4 = point<T>(P.pts, i, 3);
+        T sps, cps;
+        Mth<T>::sincospi_(T(2) * point<T>(P.pts, i, 4), &sps, &cps);
+        const T rho = R * Mth<T>::sqrt_(v4);
+        mu = Mth<T>::sqrt_(Mth<T>::max_(T(1) - v4, T(0)));
+        const T lift = R * mu;
+        for (int q = 0; q < 3; ++q) pos[q] = rho * (cps * a[q] + sps * ep[q]) + lift * d[q];
+    }
+    wgt = (T(1) - P.src.limb_u + P.src.limb_u * mu) * P.src.limb_norm;
+    return w;
+}
+
+// ------------------------------------------------------------------------------------
+// Scattering and peel-off (Sec. 2.2, 3.5, 3.6)
+// ------------------------------------------------------------------------------------
+
+// Henyey-Greenstein function x_HG(mu) = P11.
+template <class T>
+__device__ __forceinline__ T hg_p11(const DustP<T> &D, T mu)
+{
+    const T den = D.one_p_g2 - D.two_g * mu;
+    return D.one_m_g2 / (den * Mth<T>::sqrt_(den));
+}
+
+// cos Theta from v by inverting the HG distribution (Sec. 3.5).
+template <class T>
+__device__ __forceinline__ T hg_cos(const DustP<T> &D, T v)
+{
+    T c;
+    if (D.isotropic) {
+        c = T(2) * v - T(1);
+    } else {
+        const T f = D.one_m_g2 / (T(1) - D.g + D.two_g * v);
+        c = (D.one_p_g2 - f * f) / D.two_g;
+    }
+    return Mth<T>::min_(Mth<T>::max_(c, T(-1)), T(1));
+}
+
+// Q' = Q cos 2psi + U sin 2psi, U' = -Q sin 2psi + U cos 2psi for a reference axis
+// turned by psi (given cos psi, sin psi up to a common positive factor s: c2, s2 are
+// then scaled by s^2; callers pass unit values or divide).
+template <class T>
+__device__ __forceinline__ void rotate_stokes(T cps, T sps, T &Q, T &U)
+{
+    const T c2 = cps * cps - sps * sps, s2 = T(2) * cps * sps;
+    const T q = Q * c2 + U * s2;
+    U = -Q * s2 + U * c2;
+    Q = q;
+}
+
+template <class T>
+__device__ __forceinline__ bool occulted(const TraceP<T> &P, const T pos[3])
+{
+    if (P.src.kind != QMCRT_SOURCE_SPHERE) return false;
+    const T b = dot3(pos, P.obs.k);
+    const T c = dot3(pos, pos) - P.src.R * P.src.R;
+    return c <= T(0) || (b < T(0) && b * b - c > T(0));
+}
+
+// Peel-off of an unpolarized packet of weight W0 travelling along d, scattering at
+// pos.  In the image frame the White polarization is perpendicular to the scattering
+// plane; with (dx, dy) the sky projection of d this is
+//   Q = W p_l (dx^2 - dy^2) / (1 + mu^2),  U = W p_l 2 dx dy / (1 + mu^2).
+template <class T>
+__device__ __forceinline__ bool peel_unpolarized(const TraceP<T> &P, const T pos[3], const T d[3], T W0, T S[3],
+                                                 T &x, T &y)
+{
+    const ObsP<T> &O = P.obs;
+    x = dot3(pos, O.ex);
+    y = dot3(pos, O.ey);
+    if (occulted(P, pos)) return false;
+    const T tau_obs = tau_to_edge(P.med, pos, O.k);
+    const T mu = dot3(d, O.k);
+    const T f = W0 * Mth<T>::exp_(-tau_obs) * hg_p11(P.dust, mu) * T(0.07957747154594767);  // 1/(4 pi)
+    const T dx = dot3(d, O.ex), dy = dot3(d, O.ey);
+    const T q = f * P.dust.p_l / (T(1) + mu * mu);
+    S[0] = f;
+    S[1] = q * (dx * dx - dy * dy);
+    S[2] = q * T(2) * dx * dy;
+    return true;
+}
+
+// Peel-off of a polarized packet (direction n, Stokes S in the frame of axis a).
+template <class T>
+__device__ __forceinline__ bool peel_polarized(const TraceP<T> &P, const T pos[3], const T n[3], const T a[3],
+                                               const T S[3], T out[3], T &x, T &y)
+{
+    const ObsP<T> &O = P.obs;
+    x = dot3(pos, O.ex);
+    y = dot3(pos, O.ey);
+    if (occulted(P, pos)) return false;
+    const T tau_obs = tau_to_edge(P.med, pos, O.k);
+    const T mu = dot3(n, O.k);
+    const T inv1pm2 = T(1) / (T(1) + mu * mu);
+    const T r12 = -P.dust.p_l * (T(1) - mu * mu) * inv1pm2;
+    const T r33 = T(2) * mu * inv1pm2;
+    T b[3], m[3], pin[3];
+    cross3(n, a, b);
+    cross3(n, O.k, m);
+    if (dot3(m, m) < T(1e-24)) {
+        m[0] = b[0];
+        m[1] = b[1];
+        m[2] = b[2];
+    }
+    normalize3(m);
+    cross3(m, n, pin);
+    T Q = S[1], U = S[2];
+    rotate_stokes(dot3(a, pin), dot3(b, pin), Q, U);
+    const T f = Mth<T>::exp_(-tau_obs) * hg_p11(P.dust, mu) * T(0.07957747154594767);
+    T Io = f * (S[0] + r12 * Q);
+    T Qo = f * (r12 * S[0] + Q);
+    T Uo = f * r33 * U;
+    // scattering frame (m x k, m, k) -> image frame (ey, -ex, k): cos psi = -m.ex, sin psi = m.ey
+    rotate_stokes(-dot3(m, O.ex), dot3(m, O.ey), Qo, Uo);
+    out[0] = Io;
+    out[1] = Qo;
+    out[2] = Uo;
+    return true;
+}
+
+// HG scattering of a polarized packet (Sec. 3.5): Theta from v, azimuth 2 pi u from
+// axis a; Stokes rotated into the scattering plane and multiplied by M/P11.
+template <class T>
+__device__ __forceinline__ void scatter(const DustP<T> &D, T u, T v, T n[3], T a[3], T S[3])
+{
+    const T ct = hg_cos(D, v);
+    const T st = Mth<T>::sqrt_(Mth<T>::max_((T(1) - ct) * (T(1) + ct), T(0)));
+    T si, ci;
+    Mth<T>::sincospi_(T(2) * u, &si, &ci);
+    T b[3], nn[3], m[3], an[3];
+    cross3(n, a, b);
+    for (int q = 0; q < 3; ++q) {
+        nn[q] = ct * n[q] + st * (ci * a[q] + si * b[q]);
+        m[q] = ci * b[q] - si * a[q];
+    }
+    normalize3(nn);
+    T Q = S[1], U = S[2];
+    rotate_stokes(ci, si, Q, U);
+    const T inv1pm2 = T(1) / (T(1) + ct * ct);
+    const T r12 = -D.p_l * (T(1) - ct * ct) * inv1pm2;
+    const T r33 = T(2) * ct * inv1pm2;
+    const T I = S[0];
+    S[0] = I + r12 * Q;
+    S[1] = r12 * I + Q;
+    S[2] = r33 * U;
+    cross3(m, nn, an);
+    normalize3(an);
+    for (int q = 0; q < 3; ++q) {
+        n[q] = nn[q];
+        a[q] = an[q];
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Image deposits
+// ------------------------------------------------------------------------------------
+
+// Add (I, Q, U) at accumulation element e (I plane; Q, U one and two planes further).
+// Lanes of a warp that hit the same pixel are summed with shuffles first (exactly, in
+// fixed point) so that a coherent warp issues one atomic per Stokes component; warps
+// spread over many pixels add directly.  Must be called by all 32 lanes.
+template <class T>
+__device__ __forceinline__ void deposit(const AccumP &A, bool valid, size_t e, T I, T Q, T U)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned vmask = __ballot_sync(FULL_MASK, valid);
+    if (vmask == 0) return;
+    const unsigned long long key = valid ? (unsigned long long)e : ~0ull;
+    const unsigned peers = __match_any_sync(FULL_MASK, key);
+    const bool leader = valid && ((peers & ((1u << lane) - 1u)) == 0u);
+    unsigned leaders = __ballot_sync(FULL_MASK, leader);
+    const bool aggregate = __popc(leaders) <= 4;
+    if (A.mode == QMCRT_ACCUM_I64) {
+        unsigned long long *dst = (unsigned long long *)A.ptr;
+        long long qi = valid ? Mth<T>::to_fixed(I, A.scale) : 0;
+        long long qq = valid ? Mth<T>::to_fixed(Q, A.scale) : 0;
+        long long qu = valid ? Mth<T>::to_fixed(U, A.scale) : 0;
+        if (!aggregate) {
+            if (valid) {
+                atomicAdd(dst + e, (unsigned long long)qi);
+                atomicAdd(dst + e + A.plane, (unsigned long long)qq);
+                atomicAdd(dst + e + 2 * A.plane, (unsigned long long)qu);
+            }
+            return;
+        }
+        while (leaders) {
+            const int l = __ffs(leaders) - 1;
+            const unsigned grp = __shfl_sync(FULL_MASK, peers, l);
+            const bool in = (grp >> lane) & 1u;
+            long long a = in ? qi : 0, b = in ? qq : 0, c = in ? qu : 0;
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                a += __shfl_xor_sync(FULL_MASK, a, o);
+                b += __shfl_xor_sync(FULL_MASK, b, o);
+                c += __shfl_xor_sync(FULL_MASK, c, o);
+            }
+            if (lane == l) {
+                atomicAdd(dst + e, (unsigned long long)a);
+                atomicAdd(dst + e + A.plane, (unsigned long long)b);
+                atomicAdd(dst + e + 2 * A.plane, (unsigned long long)c);
+            }
+            leaders &= leaders - 1u;
+        }
+    } else {
+        double *dst = (double *)A.ptr;
+        if (!aggregate) {
+            if (valid) {
+                atomicAdd(dst + e, (double)I);
+                atomicAdd(dst + e + A.plane, (double)Q);
+                atomicAdd(dst + e + 2 * A.plane, (double)U);
+            }
+            return;
+        }
+        while (leaders) {
+            const int l = __ffs(leaders) - 1;
+            const unsigned grp = __shfl_sync(FULL_MASK, peers, l);
+            const bool in = (grp >> lane) & 1u;
+            double a = in ? (double)I : 0.0, b = in ? (double)Q : 0.0, c = in ? (double)U : 0.0;
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                a += __shfl_xor_sync(FULL_MASK, a, o);
+                b += __shfl_xor_sync(FULL_MASK, b, o);
+                c += __shfl_xor_sync(FULL_MASK, c, o);
+            }
+            if (lane == l) {
+                atomicAdd(dst + e, a);
+                atomicAdd(dst + e + A.plane, b);
+                atomicAdd(dst + e + 2 * A.plane, c);
+            }
+            leaders &= leaders - 1u;
+        }
+    }
+}
+
+// Bin a peel-off contribution at sky (x, y) into image img (Sec. 3.6).  Must be
+// called by all 32 lanes.
+template <class T>
+__device__ __forceinline__ void splat(const TraceP<T> &P, bool valid, int img, T x, T y, const T S[3])
+{
+    const ObsP<T> &O = P.obs;
+    const size_t img_base = (size_t)img * 3 * P.acc.plane;
+    if (O.splat == QMCRT_SPLAT_NEAREST) {
+        const T fx = Mth<T>::floor_((x + O.hw) * O.pix_x);
+        const T fy = Mth<T>::floor_((y + O.hw) * O.pix_y);
+        const bool in = valid && fx >= T(0) && fx < T(O.nx) && fy >= T(0) && fy < T(O.ny);
+        const size_t e = in ? img_base + (size_t)((int)fy * O.nx + (int)fx) : 0;
+        deposit<T>(P.acc, in, e, S[0], S[1], S[2]);
+        return;
+    }
+    const T fx = (x + O.hw) * O.pix_x - T(0.5);
+    const T fy = (y + O.hw) * O.pix_y - T(0.5);
+    const T x0 = Mth<T>::floor_(fx), y0 = Mth<T>::floor_(fy);
+    const T ax = fx - x0, ay = fy - y0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int dx = q & 1, dy = q >> 1;
+        const T ix = x0 + T(dx), iy = y0 + T(dy);
+        const bool in = valid && ix >= T(0) && ix < T(O.nx) && iy >= T(0) && iy < T(O.ny);
+        const T w = (dx ? ax : T(1) - ax) * (dy ? ay : T(1) - ay);
+        const size_t e = in ? img_base + (size_t)((int)iy * O.nx + (int)ix) : 0;
+        deposit<T>(P.acc, in, e, w * S[0], w * S[1], w * S[2]);
+    }
+}
+
+}  // namespace qmcrt

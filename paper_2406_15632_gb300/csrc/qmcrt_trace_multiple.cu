@@ -1,0 +1,88 @@
+// qmcrt_trace_multiple.cu -- multiple-scattering tracer kernel (Sec. 3.5, 3.7).
+//
+// One thread per packet, the same warp-coherent packet mapping as the single-
+// scattering kernel.  Order k reads coordinates 4(k-1) + {0 azimuth, 1 cos Theta,
+// 2 depth, 3 roulette}; the order loop is uniform across the warp so deposits stay
+// convergent, and the warp leaves the loop once all its packets are done.
+#include "qmcrt_device.cuh"
+
+namespace qmcrt {
+
+template <class T>
+__global__ void __launch_bounds__(256) k_trace_multiple(const __grid_constant__ TraceP<T> P)
+{
+    const int lane = threadIdx.x & 31;
+    const uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= P.stride) return;  // uniform per warp
+    const uint64_t j = (uint64_t)lane * P.stride + w;
+    bool alive = j < P.count;
+    const uint64_t i = P.first + j;
+    T pos[3] = {T(0), T(0), T(0)}, n[3] = {T(0), T(0), T(1)}, a[3] = {T(1), T(0), T(0)};
+    T S[3] = {T(0), T(0), T(0)};
+    T wd = T(0);
+    if (alive) {
+        T wgt;
+        wd = emit(P, i, pos, n, a, wgt);
+        S[0] = wgt;
+    }
+    for (int k = 1; k <= P.max_orders; ++k) {
+        if (!__any_sync(FULL_MASK, alive)) break;
+        const int base = 4 * (k - 1);
+        T out[3] = {T(0), T(0), T(0)};
+        T x = T(0), y = T(0);
+        bool contrib = false;
+        if (alive) {
+            if (k > 1) {
+                scatter(P.dust, point<T>(P.pts, i, base), point<T>(P.pts, i, base + 1), n, a, S);
+                wd = point<T>(P.pts, i, base + 2);
+            }
+            if (k == 1 || P.force_all) {
+                T W1;
+                if (forced_step(P, pos, n, wd, W1)) {
+                    S[0] *= W1;
+                    S[1] *= W1;
+                    S[2] *= W1;
+                } else {
+                    alive = false;
+                }
+            } else if (!march(P.med, pos, n, -Mth<T>::log_(wd))) {
+                alive = false;
+            }
+            if (alive) {
+                S[0] *= P.dust.albedo;
+                S[1] *= P.dust.albedo;
+                S[2] *= P.dust.albedo;
+                contrib = peel_polarized(P, pos, n, a, S, out, x, y);
+            }
+        }
+        splat(P, contrib, P.per_order ? k - 1 : 0, x, y, out);
+        if (alive) {
+            if (k == P.max_orders) {
+                alive = false;
+            } else if (S[0] < P.rr_threshold) {
+                if (point<T>(P.pts, i, base + 3) < P.rr_survival) {
+                    S[0] /= P.rr_survival;
+                    S[1] /= P.rr_survival;
+                    S[2] /= P.rr_survival;
+                } else {
+                    alive = false;
+                }
+            }
+        }
+    }
+}
+
+template <class T>
+static cudaError_t launch(const TraceP<T> &p, int block, cudaStream_t s)
+{
+    if (p.count == 0) return cudaSuccess;
+    const uint64_t threads = p.stride * 32;
+    const uint64_t grid = (threads + block - 1) / block;
+    k_trace_multiple<T><<<(unsigned)grid, block, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trace_multiple_f32(const TraceP<float> &p, int block, cudaStream_t s) { return launch(p, block, s); }
+cudaError_t launch_trace_multiple_f64(const TraceP<double> &p, int block, cudaStream_t s) { return launch(p, block, s); }
+
+}  // namespace qmcrt

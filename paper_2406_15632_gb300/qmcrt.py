@@ -1,0 +1,315 @@
+"""Python binding of the qmcrt C ABI (include/qmcrt.h).
+
+Argument marshalling only: every step of the tracer runs in the CUDA library
+libqmcrt.so, built in-tree by build.py.  The functions named qmcrt_* mirror the C
+entry points one to one; the helpers below them turn a scene description and torch
+device tensors into those calls.  PyTorch provides device memory and streams.
+
+There is no CPU fallback: if the library is missing or no GPU is present, the calls
+raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import threading
+
+from . import scenes
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libqmcrt.so")
+
+OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_DEVICE_TIMEOUT = 0, -1, -2, -3, -4
+KINDS = {"sobol": 0, "sobol_owen": 1, "halton": 2, "hammersley": 3, "philox": 4}
+FORMATS = {"u32": 0, "f32": 1, "f64": 2}
+MEDIUM_GRID, MEDIUM_SPHERE = 0, 1
+SOURCE_POINT, SOURCE_SPHERE = 0, 1
+ORDER_DIRECT, ORDER_INVERSE = 0, 1
+SPLAT = {"nearest": 0, "bilinear": 1}
+ACCUM = {"i64": 0, "f64": 1}
+PREC = {"f32": 0, "f64": 1}
+FORCE = {"all": 0, "first": 1}
+MAX_DIMS = 256
+
+
+class QmcrtError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__(f"qmcrt error {code}: {message}")
+        self.code = code
+
+
+class qmcrt_points_desc(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("kind", C.c_int32), ("dims", C.c_uint32), ("format", C.c_int32),
+                ("first_index", C.c_uint64), ("count", C.c_uint64), ("total_n", C.c_uint64), ("seed", C.c_uint64)]
+
+
+class qmcrt_medium(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("kind", C.c_int32), ("d_k", C.c_void_p), ("nx", C.c_int32),
+                ("ny", C.c_int32), ("nz", C.c_int32), ("reserved", C.c_int32), ("lo", C.c_double * 3),
+                ("hi", C.c_double * 3), ("kscale", C.c_double), ("sphere_r", C.c_double), ("sphere_k", C.c_double)]
+
+
+class qmcrt_source(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("kind", C.c_int32), ("radius", C.c_double), ("limb_u", C.c_double),
+                ("order", C.c_int32), ("reserved", C.c_int32)]
+
+
+class qmcrt_dust(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("reserved", C.c_int32), ("albedo", C.c_double), ("g", C.c_double),
+                ("p_l", C.c_double)]
+
+
+class qmcrt_observer(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("splat", C.c_int32), ("theta", C.c_double), ("phi", C.c_double),
+                ("half_width", C.c_double), ("nx", C.c_int32), ("ny", C.c_int32)]
+
+
+class qmcrt_image(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("accum", C.c_int32), ("d_accum", C.c_void_p), ("n_images", C.c_int32),
+                ("frac_bits", C.c_int32)]
+
+
+class qmcrt_trace_opts(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("precision", C.c_int32), ("tau_min", C.c_double),
+                ("max_orders", C.c_int32), ("force_mode", C.c_int32), ("rr_threshold", C.c_double),
+                ("rr_survival", C.c_double), ("per_order", C.c_int32), ("block_size", C.c_int32)]
+
+
+def _new(cls, **kw):
+    s = cls()
+    s.struct_size = C.sizeof(cls)
+    for k, v in kw.items():
+        setattr(s, k, v)
+    return s
+
+
+_lock = threading.Lock()
+_lib = None
+
+# every C entry point: (name, restype, argtypes)
+_P = C.POINTER
+_SIGS = [
+    ("qmcrt_abi_version", C.c_int, []),
+    ("qmcrt_last_error", C.c_char_p, []),
+    ("qmcrt_generate_points", C.c_int, [_P(qmcrt_points_desc), C.c_void_p, C.c_void_p]),
+    ("qmcrt_trace_single", C.c_int, [_P(qmcrt_medium), _P(qmcrt_source), _P(qmcrt_dust), _P(qmcrt_observer),
+                                     _P(qmcrt_points_desc), _P(qmcrt_trace_opts), _P(qmcrt_image), C.c_void_p,
+                                     C.c_void_p]),
+    ("qmcrt_trace_multiple", C.c_int, [_P(qmcrt_medium), _P(qmcrt_source), _P(qmcrt_dust), _P(qmcrt_observer),
+                                       _P(qmcrt_points_desc), _P(qmcrt_trace_opts), _P(qmcrt_image), C.c_void_p]),
+    ("qmcrt_image_reduce", C.c_int, [_P(qmcrt_image), C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_void_p,
+                                     C.c_void_p]),
+]
+EXPORTED = [s[0] for s in _SIGS]
+
+
+def load(path: str = LIB_PATH):
+    """Load libqmcrt.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise QmcrtError(ERR_UNSUPPORTED, f"{path} missing: build the CUDA library first (build.py)")
+            L = C.CDLL(path)
+            for name, res, args in _SIGS:
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            if L.qmcrt_abi_version() != 1:
+                raise QmcrtError(ERR_UNSUPPORTED, "ABI version mismatch")
+            _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return load().qmcrt_last_error().decode()
+
+
+def _check(rc: int):
+    if rc != OK:
+        raise QmcrtError(rc, last_error())
+
+
+# --- the C entry points, one to one ----------------------------------------------------
+
+def qmcrt_generate_points(desc: qmcrt_points_desc, d_out: int, stream: int = 0) -> None:
+    _check(load().qmcrt_generate_points(C.byref(desc), C.c_void_p(d_out), C.c_void_p(stream)))
+
+
+def qmcrt_trace_single(medium, source, dust, obs, pts, opts, image, d_log: int = 0, stream: int = 0) -> None:
+    _check(load().qmcrt_trace_single(C.byref(medium), C.byref(source), C.byref(dust), C.byref(obs), C.byref(pts),
+                                     C.byref(opts), C.byref(image), C.c_void_p(d_log or None), C.c_void_p(stream)))
+
+
+def qmcrt_trace_multiple(medium, source, dust, obs, pts, opts, image, stream: int = 0) -> None:
+    _check(load().qmcrt_trace_multiple(C.byref(medium), C.byref(source), C.byref(dust), C.byref(obs), C.byref(pts),
+                                       C.byref(opts), C.byref(image), C.c_void_p(stream)))
+
+
+def qmcrt_image_reduce(image, nx: int, ny: int, n_replicas: int, scale: float, d_out: int, stream: int = 0) -> None:
+    _check(load().qmcrt_image_reduce(C.byref(image), nx, ny, n_replicas, scale, C.c_void_p(d_out),
+                                     C.c_void_p(stream)))
+
+
+# --- marshalling helpers ------------------------------------------------------------------
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _stream(stream) -> int:
+    torch = _torch()
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def points_desc(kind: str, dims: int, first: int, count: int, fmt: str = "f64", seed: int = 0,
+                total_n: int = 0) -> qmcrt_points_desc:
+    return _new(qmcrt_points_desc, kind=KINDS[kind], dims=dims, format=FORMATS[fmt], first_index=first, count=count,
+                total_n=total_n, seed=seed)
+
+
+def generate_points(kind: str, dims: int, first: int, count: int, fmt: str = "f64", seed: int = 0,
+                    total_n: int = 0, out=None, stream=None):
+    """Device tensor [count][dims] of points first..first+count-1."""
+    torch = _torch()
+    dt = {"u32": torch.int32, "f32": torch.float32, "f64": torch.float64}[fmt]
+    if out is None:
+        out = torch.empty((count, dims), dtype=dt, device="cuda")
+    qmcrt_generate_points(points_desc(kind, dims, first, count, fmt, seed, total_n), out.data_ptr(), _stream(stream))
+    return out
+
+
+def contribution_bound(prob: scenes.Problem) -> float:
+    """Upper bound on |I|, |Q|, |U| of one peel-off contribution: source weight x
+    max P11/(4 pi) x polarization growth over the orders (factor 1 + p_l each)."""
+    g = abs(prob.g)
+    p11 = (1 + g) / ((1 - g) ** 2)
+    limb = 1.0 / (1.0 - prob.limb_u / 3.0) if prob.source == "sphere" else 1.0
+    growth = (1 + prob.p_l) ** max(prob.max_orders - 1, 0)
+    rr = 1.0 / prob.rr_survival if prob.rr_threshold > 0 else 1.0
+    return limb * p11 / (4 * math.pi) * min(growth, 2.0 ** 20) * max(rr * prob.rr_threshold, 1.0)
+
+
+def default_frac_bits(prob: scenes.Problem, n_contributions: int) -> int:
+    """Largest fixed-point scale that cannot overflow: n * bound * 2^F < 2^62."""
+    n = max(int(n_contributions), 1) * max(prob.max_orders if not prob.per_order else 1, 1)
+    need = math.log2(n * contribution_bound(prob))
+    return int(max(0, min(62, math.floor(62 - need))))
+
+
+class Scene:
+    """The descriptor structs of one problem, with its grid resident on the device."""
+
+    def __init__(self, prob: scenes.Problem, grid_device=None, device="cuda"):
+        torch = _torch()
+        self.prob = prob
+        if prob.grid is not None:
+            if grid_device is None:
+                grid_device = torch.as_tensor(prob.grid, dtype=torch.float32).to(device).contiguous()
+            self.grid = grid_device
+            nz, ny, nx = self.grid.shape
+            self.medium = _new(qmcrt_medium, kind=MEDIUM_GRID, d_k=self.grid.data_ptr(), nx=nx, ny=ny, nz=nz,
+                               kscale=prob.kscale)
+        else:
+            self.grid = None
+            self.medium = _new(qmcrt_medium, kind=MEDIUM_SPHERE, d_k=None, kscale=prob.kscale,
+                               sphere_r=prob.sphere_r, sphere_k=prob.sphere_k)
+        for a in range(3):
+            self.medium.lo[a] = prob.lo[a]
+            self.medium.hi[a] = prob.hi[a]
+        self.source = _new(qmcrt_source, kind=SOURCE_POINT if prob.source == "point" else SOURCE_SPHERE,
+                           radius=prob.star_r, limb_u=prob.limb_u,
+                           order=ORDER_DIRECT if prob.emit_order == "direct" else ORDER_INVERSE)
+        self.dust = _new(qmcrt_dust, albedo=prob.albedo, g=prob.g, p_l=prob.p_l)
+        self.obs = _new(qmcrt_observer, splat=SPLAT[prob.splat], theta=prob.theta_obs, phi=prob.phi_obs,
+                        half_width=prob.half_width, nx=prob.nx, ny=prob.ny)
+
+    def opts(self, precision: str = "f32", block_size: int = 0) -> qmcrt_trace_opts:
+        p = self.prob
+        return _new(qmcrt_trace_opts, precision=PREC[precision], tau_min=p.tau_min, max_orders=p.max_orders,
+                    force_mode=FORCE[p.force], rr_threshold=p.rr_threshold, rr_survival=p.rr_survival,
+                    per_order=1 if p.per_order else 0, block_size=block_size)
+
+    def accum_buffer(self, accum: str = "i64", replicas: int = 1):
+        torch = _torch()
+        dt = torch.int64 if accum == "i64" else torch.float64
+        return torch.zeros((replicas, self.prob.n_images, 3, self.prob.ny, self.prob.nx), dtype=dt, device="cuda")
+
+    def image_desc(self, buf, accum: str = "i64", frac_bits: int = 0) -> qmcrt_image:
+        return _new(qmcrt_image, accum=ACCUM[accum], d_accum=buf.data_ptr(), n_images=self.prob.n_images,
+                    frac_bits=frac_bits)
+
+    def trace(self, first: int, count: int, buf, *, accum: str = "i64", frac_bits: int = 0, precision: str = "f32",
+              log=None, stream=None, block_size: int = 0) -> None:
+        """Add the contributions of packets first..first+count-1 to buf."""
+        p = self.prob
+        pts = points_desc(p.generator, p.dims, first, count, "f64", p.seed, p.total_n)
+        img = self.image_desc(buf, accum, frac_bits)
+        if p.max_orders > 1:
+            if log is not None:
+                raise QmcrtError(ERR_UNSUPPORTED, "the packet log is single-scattering only")
+            qmcrt_trace_multiple(self.medium, self.source, self.dust, self.obs, pts, self.opts(precision, block_size),
+                                 img, _stream(stream))
+        else:
+            qmcrt_trace_single(self.medium, self.source, self.dust, self.obs, pts, self.opts(precision, block_size),
+                               img, log.data_ptr() if log is not None else 0, _stream(stream))
+
+    def reduce(self, buf, scale: float, *, accum: str = "i64", frac_bits: int = 0, out=None, stream=None):
+        torch = _torch()
+        if out is None:
+            out = torch.empty((self.prob.n_images, 3, self.prob.ny, self.prob.nx), dtype=torch.float64, device="cuda")
+        replicas = buf.shape[0] if buf.dim() == 5 else 1
+        qmcrt_image_reduce(self.image_desc(buf, accum, frac_bits), self.prob.nx, self.prob.ny, replicas, scale,
+                           out.data_ptr(), _stream(stream))
+        return out
+
+
+def render(prob: scenes.Problem, n_packets: int, first: int = 1, *, precision: str = "f32", accum: str = "i64",
+           frac_bits: int | None = None, log: bool = False, scale: float | None = None):
+    """Trace packets first..first+n_packets-1 and return the image [n_images][3][ny][nx]
+    (float64, scaled by 1/n_packets unless scale is given), and the packet log if asked."""
+    torch = _torch()
+    sc = Scene(prob)
+    fb = default_frac_bits(prob, n_packets) if frac_bits is None else frac_bits
+    buf = sc.accum_buffer(accum)
+    lg = torch.zeros((n_packets, 9), dtype=torch.float64, device="cuda") if log else None
+    sc.trace(first, n_packets, buf, accum=accum, frac_bits=fb, precision=precision, log=lg)
+    img = sc.reduce(buf, 1.0 / n_packets if scale is None else scale, accum=accum, frac_bits=fb)
+    return (img, lg) if log else img
+
+
+class HostRenderer:
+    """The end-to-end call for host-resident inputs: each call copies the density grid
+    from (pinned) host memory to the device, traces a packet range, reduces the image
+    and copies it back to host memory, all on one stream.  Device buffers are allocated
+    once, at construction."""
+
+    def __init__(self, prob: scenes.Problem, max_packets: int, *, precision: str = "f32", accum: str = "i64",
+                 frac_bits: int | None = None):
+        torch = _torch()
+        self.scene = Scene(prob)
+        self.precision, self.accum = precision, accum
+        self.frac_bits = default_frac_bits(prob, max_packets) if frac_bits is None else frac_bits
+        self.buf = self.scene.accum_buffer(accum)
+        self.out = torch.empty((prob.n_images, 3, prob.ny, prob.nx), dtype=torch.float64, device="cuda")
+
+    def input_bytes(self) -> int:
+        return 0 if self.scene.grid is None else self.scene.grid.numel() * 4
+
+    def output_bytes(self) -> int:
+        return self.out.numel() * 8
+
+    def __call__(self, host_grid, first: int, count: int, host_out, stream=None) -> None:
+        if self.scene.grid is not None:
+            self.scene.grid.copy_(host_grid, non_blocking=True)
+        self.buf.zero_()
+        self.scene.trace(first, count, self.buf, accum=self.accum, frac_bits=self.frac_bits, precision=self.precision,
+                         stream=stream)
+        self.scene.reduce(self.buf, 1.0 / count, accum=self.accum, frac_bits=self.frac_bits, out=self.out,
+                          stream=stream)
+        host_out.copy_(self.out, non_blocking=True)

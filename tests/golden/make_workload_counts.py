@@ -1,0 +1,38 @@
+"""Writes workload_counts.json: algorithmic work per packet of the benchmark workloads,
+counted by the CPU oracle (grid cells visited by all walks of a packet), used as the
+per-unit figure of the roofline.  Calls only oracle/ and the scene generators.
+
+    python tests/golden/make_workload_counts.py
+"""
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+from oracle import oracle as O  # noqa: E402
+from paper_2406_15632_gb300 import scenes as S  # noqa: E402
+
+N = 1 << 18
+
+
+def main():
+    out = {}
+    prob = S.flared_disk_problem(n=256)
+    _, log = O.trace_single(prob, 1, N, log=True)
+    out["flared_disk_single_scattering"] = {
+        "cells_per_packet": float(log[:, 9].mean()),
+        "packets": N,
+        "contributing_fraction": float((log[:, 8] == 0).mean()),
+        "note": "256^3 flared disk, point source, Sobol indices 1..2^18, all three walks per packet",
+    }
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "workload_counts.json")
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+        f.write("\n")
+    print(json.dumps(out, indent=1))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,161 @@
+"""The C-ABI library builds, loads and exports every entry point the header declares;
+host-side argument validation rejects bad calls before any device work (these calls
+never reach the GPU, so they run without one)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2406_15632_gb300 import build as B
+from paper_2406_15632_gb300 import qmcrt as Q
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "qmcrt.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return Q.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(qmcrt_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_header_declares_the_four_path_calls():
+    names = declared_functions()
+    for n in ("qmcrt_generate_points", "qmcrt_trace_single", "qmcrt_trace_multiple", "qmcrt_image_reduce"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    assert sorted(Q.EXPORTED) == sorted(declared_functions())
+    assert lib.qmcrt_abi_version() == 1
+
+
+STRUCTS = ["qmcrt_points_desc", "qmcrt_medium", "qmcrt_source", "qmcrt_dust", "qmcrt_observer", "qmcrt_image",
+           "qmcrt_trace_opts"]
+
+
+def test_struct_layout_matches_the_c_compiler(tmp_path):
+    """Compile the header with the host C compiler and compare every struct's size and
+    field offsets with the ctypes mirrors used by the binding."""
+    import subprocess
+
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "qmcrt.h"', "int main(void) {"]
+    for sname in STRUCTS:
+        cls = getattr(Q, sname)
+        lines.append(f'printf("{sname} %zu\\n", sizeof({sname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{sname}.{fname} %zu\\n", offsetof({sname}, {fname}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)])
+    got = dict(line.split() for line in subprocess.check_output([str(exe)]).decode().splitlines())
+    for sname in STRUCTS:
+        cls = getattr(Q, sname)
+        assert int(got[sname]) == C.sizeof(cls), sname
+        for fname, _ in cls._fields_:
+            assert int(got[f"{sname}.{fname}"]) == getattr(cls, fname).offset, (sname, fname)
+
+
+def _expect(code, fn, *args):
+    with pytest.raises(Q.QmcrtError) as e:
+        fn(*args)
+    assert e.value.code == code, str(e.value)
+    return str(e.value)
+
+
+def test_points_validation(lib):
+    d = Q.points_desc("sobol", 3, 1, 16)
+    _expect(Q.ERR_INVALID_ARG, Q.qmcrt_generate_points, d, 0)  # NULL output
+    fake = 0x1000  # never dereferenced: validation fails first
+    for bad in (Q.points_desc("sobol", 0, 1, 16), Q.points_desc("sobol", 257, 1, 16),
+                Q.points_desc("sobol", 3, 0, 16), Q.points_desc("halton", 3, 1, 16, fmt="u32"),
+                Q.points_desc("sobol", 3, 2 ** 32 - 4, 16), Q.points_desc("hammersley", 2, 1, 16, total_n=8)):
+        _expect(Q.ERR_INVALID_ARG, Q.qmcrt_generate_points, bad, fake)
+    d = Q.points_desc("sobol", 3, 1, 16)
+    d.struct_size = 40
+    assert "ABI" in _expect(Q.ERR_INVALID_ARG, Q.qmcrt_generate_points, d, fake)
+    d = Q.points_desc("sobol", 3, 1, 16)
+    d.kind = 9
+    _expect(Q.ERR_INVALID_ARG, Q.qmcrt_generate_points, d, fake)
+
+
+def _descs(**over):
+    medium = Q._new(Q.qmcrt_medium, kind=Q.MEDIUM_SPHERE, kscale=1.0, sphere_r=1.0, sphere_k=0.1)
+    source = Q._new(Q.qmcrt_source, kind=Q.SOURCE_POINT)
+    dust = Q._new(Q.qmcrt_dust, albedo=1.0, g=0.0, p_l=0.0)
+    obs = Q._new(Q.qmcrt_observer, splat=0, theta=1.0, phi=0.0, half_width=1.0, nx=8, ny=8)
+    pts = Q.points_desc("sobol", 3, 1, 64)
+    opts = Q._new(Q.qmcrt_trace_opts, precision=0, tau_min=1e-12, max_orders=1, rr_survival=0.1)
+    img = Q._new(Q.qmcrt_image, accum=0, d_accum=0x1000, n_images=1, frac_bits=40)
+    d = dict(medium=medium, source=source, dust=dust, obs=obs, pts=pts, opts=opts, img=img)
+    for k, v in over.items():
+        obj, field = k.split("__")
+        setattr(d[obj], field, v)
+    return d
+
+
+BAD_TRACE = [
+    dict(dust__g=1.0), dict(dust__albedo=1.5), dict(dust__p_l=-0.1), dict(obs__nx=0), dict(obs__half_width=0.0),
+    dict(obs__splat=3), dict(pts__first_index=0), dict(pts__dims=2), dict(img__d_accum=None), dict(img__frac_bits=63),
+    dict(img__accum=5), dict(img__n_images=2), dict(opts__precision=7), dict(opts__block_size=48),
+    dict(medium__kind=0), dict(medium__kscale=0.0), dict(source__kind=1), dict(opts__tau_min=-1.0),
+]
+
+
+@pytest.mark.parametrize("over", BAD_TRACE)
+def test_trace_single_validation(lib, over):
+    d = _descs(**over)
+    _expect(Q.ERR_INVALID_ARG, Q.qmcrt_trace_single, d["medium"], d["source"], d["dust"], d["obs"], d["pts"],
+            d["opts"], d["img"], 0, 0)
+
+
+def test_trace_multiple_validation(lib):
+    d = _descs(opts__max_orders=3)
+    d["pts"].dims = 11  # needs 12
+    _expect(Q.ERR_INVALID_ARG, Q.qmcrt_trace_multiple, d["medium"], d["source"], d["dust"], d["obs"], d["pts"],
+            d["opts"], d["img"], 0)
+    d = _descs(opts__max_orders=3, opts__rr_survival=0.0)
+    d["pts"].dims = 12
+    _expect(Q.ERR_INVALID_ARG, Q.qmcrt_trace_multiple, d["medium"], d["source"], d["dust"], d["obs"], d["pts"],
+            d["opts"], d["img"], 0)
+    d = _descs(opts__max_orders=3, source__kind=1, source__radius=0.1)
+    d["pts"].dims = 12
+    _expect(Q.ERR_UNSUPPORTED, Q.qmcrt_trace_multiple, d["medium"], d["source"], d["dust"], d["obs"], d["pts"],
+            d["opts"], d["img"], 0)
+
+
+def test_image_reduce_validation(lib):
+    img = Q._new(Q.qmcrt_image, accum=0, d_accum=0x1000, n_images=1, frac_bits=40)
+    _expect(Q.ERR_INVALID_ARG, Q.qmcrt_image_reduce, img, 8, 8, 1, 1.0, 0)
+    _expect(Q.ERR_INVALID_ARG, Q.qmcrt_image_reduce, img, 0, 8, 1, 1.0, 0x2000)
+    _expect(Q.ERR_INVALID_ARG, Q.qmcrt_image_reduce, img, 8, 8, 0, 1.0, 0x2000)
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    with pytest.raises(Q.QmcrtError):
+        Q._lib_saved = Q._lib
+        Q._lib = None
+        try:
+            Q.load(str(tmp_path / "nope.so"))
+        finally:
+            Q._lib = Q._lib_saved
+
+
+def test_default_frac_bits_never_overflows():
+    from paper_2406_15632_gb300 import scenes as S
+
+    for prob, n in ((S.flared_disk_problem(n=8), 1 << 28), (S.homogeneous_sphere_problem(), 1 << 16),
+                    (S.clumpy_problem(n=8), 1 << 24)):
+        fb = Q.default_frac_bits(prob, n)
+        assert 0 <= fb <= 62
+        assert n * Q.contribution_bound(prob) * prob.max_orders * 2.0 ** fb < 2.0 ** 63

@@ -1,0 +1,239 @@
+"""GPU tracer through the C ABI against the CPU oracle on the same seeded inputs.
+
+Tolerances, derived from the arithmetic:
+  * FP64 path: images agree to relative L2 <= 1e-10.  Both sides do the same steps in
+    double; they differ only by rounding order (fused multiply-adds, incremental face
+    distances on the GPU) and by libm ulps, ~1e-15 per operation over a few hundred
+    operations per packet.  Pixel-boundary flips need a position error of ~1e-15 and
+    do not occur at these sizes.
+  * FP32 path: per packet, intensity and polarization within 1e-5 of the FP64 value
+    and the sky position within 1e-5 (units of the medium) for >= 99.9 % of packets;
+    the remaining packets scatter in cells of very low density, where the position is
+    ill-conditioned (an optical-depth rounding of 1e-7 moves it by 1e-7 / k).  Images
+    binned with the tent (bilinear) splat are continuous in position and agree to
+    relative L2 <= 1e-5; with nearest-pixel binning a packet near a pixel edge can
+    change pixels, so that image is compared through the packet log instead.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2406_15632_gb300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def Q():
+    from paper_2406_15632_gb300 import build as B
+    from paper_2406_15632_gb300 import qmcrt
+
+    B.build()
+    qmcrt.load()
+    return qmcrt
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def gpu_image(Q, prob, N, first=1, **kw):
+    import torch
+
+    out = Q.render(prob, N, first, scale=1.0, **kw)
+    torch.cuda.synchronize()
+    if isinstance(out, tuple):
+        return out[0].cpu().numpy(), out[1].cpu().numpy()
+    return out.cpu().numpy()
+
+
+def oracle_image(prob, N, first=1):
+    if prob.max_orders > 1:
+        return O.trace_multiple(prob, first, N)
+    return O.trace_single(prob, first, N)[None]
+
+
+DISK32 = S.flared_disk_problem(n=32, nx=64, ny=64)
+SINGLE_CASES = {
+    "sphere_c1": S.homogeneous_sphere_problem(),
+    "sphere_polarized": S.homogeneous_sphere_problem(g=0.5, p_l=0.5, sphere_k=1.0, theta_obs=0.7, phi_obs=0.3),
+    "disk_sobol": DISK32,
+    "disk_owen": DISK32.replace(generator="sobol_owen", seed=3),
+    "disk_halton": DISK32.replace(generator="halton"),
+    "disk_hammersley": DISK32.replace(generator="hammersley", total_n=1 << 14),
+    "disk_philox": DISK32.replace(generator="philox", seed=11),
+    "disk_bilinear": DISK32.replace(splat="bilinear"),
+    "disk_face_on": DISK32.replace(theta_obs=0.0),
+    "star_inverse": DISK32.replace(source="sphere", star_r=0.05, limb_u=0.6, emit_order="inverse"),
+    "star_direct": DISK32.replace(source="sphere", star_r=0.05, limb_u=0.6, emit_order="direct"),
+    "random_grid_kscale": S.Problem(grid=S.random_grid(7, seed=4), kscale=0.37, albedo=0.7, g=-0.3, p_l=0.8,
+                                    theta_obs=2.0, phi_obs=4.0, half_width=1.3, nx=33, ny=29),
+}
+
+
+@pytest.mark.parametrize("name", list(SINGLE_CASES))
+@pytest.mark.parametrize("accum", ["i64", "f64"])
+def test_trace_single_fp64_matches_oracle(Q, name, accum):
+    prob = SINGLE_CASES[name]
+    N = 1 << 14
+    got = gpu_image(Q, prob, N, precision="f64", accum=accum)
+    ref = oracle_image(prob, N)
+    assert rel_l2(got, ref) <= 1e-10
+
+
+def test_trace_single_fp64_packet_log(Q):
+    prob = DISK32.replace(source="sphere", star_r=0.05, limb_u=0.6)
+    N = 3000  # ragged: not a multiple of 32
+    _, lg = gpu_image(Q, prob, N, precision="f64", log=True)
+    _, ref = O.trace_single(prob, 1, N, log=True)
+    assert np.array_equal(lg[:, 8], ref[:, 8])
+    assert np.allclose(lg[:, :8], ref[:, :8], rtol=1e-11, atol=1e-13)
+
+
+def _fp32_packet_check(lg, ref, tol=1e-5, frac=0.999):
+    assert np.array_equal(lg[:, 8] == 0, ref[:, 8] == 0) or np.mean(lg[:, 8] != ref[:, 8]) < 1e-3
+    ok = (ref[:, 8] == 0) & (lg[:, 8] == 0)
+    I = ref[ok, 3]
+    good = (np.abs(lg[ok, 3] - I) <= tol * I)
+    good &= (np.abs(lg[ok, 4] - ref[ok, 4]) <= tol * I) & (np.abs(lg[ok, 5] - ref[ok, 5]) <= tol * I)
+    good &= (np.abs(lg[ok, 6] - ref[ok, 6]) <= tol) & (np.abs(lg[ok, 7] - ref[ok, 7]) <= tol)
+    assert good.mean() >= frac, good.mean()
+    # the rest stay close in intensity (their position is the ill-conditioned part)
+    assert np.all(np.abs(lg[ok, 3] - I) <= 1e-3 * I + 1e-12)
+    return good.mean()
+
+
+@pytest.mark.parametrize("name", ["disk_sobol", "disk_halton", "star_inverse", "star_direct", "random_grid_kscale",
+                                  "sphere_polarized"])
+def test_trace_single_fp32_packets_within_1e5(Q, name):
+    prob = SINGLE_CASES[name]
+    N = 1 << 14
+    _, lg = gpu_image(Q, prob, N, precision="f32", log=True)
+    _, ref = O.trace_single(prob, 1, N, log=True)
+    _fp32_packet_check(lg, ref)
+
+
+@pytest.mark.parametrize("name", ["disk_bilinear", "sphere_polarized"])
+def test_trace_single_fp32_bilinear_image_within_1e5(Q, name):
+    prob = SINGLE_CASES[name].replace(splat="bilinear")
+    N = 1 << 16
+    got = gpu_image(Q, prob, N, precision="f32")
+    ref = oracle_image(prob, N)
+    assert rel_l2(got, ref) <= 1e-5
+
+
+def test_trace_single_fp32_nearest_image_matches_binned_log(Q):
+    """Nearest-pixel FP32 image = the FP32 packet log binned on the host, exactly up to
+    the fixed-point quantum; and its total agrees with the oracle to 1e-5."""
+    prob = DISK32
+    N = 1 << 14
+    fb = 40
+    img, lg = gpu_image(Q, prob, N, precision="f32", log=True, frac_bits=fb)
+    ok = lg[:, 8] == 0
+    fx = np.floor((lg[ok, 6].astype(np.float32) + np.float32(1.0)) * np.float32(32.0))
+    fy = np.floor((lg[ok, 7].astype(np.float32) + np.float32(1.0)) * np.float32(32.0))
+    inside = (fx >= 0) & (fx < 64) & (fy >= 0) & (fy < 64)
+    ref = np.zeros((3, 64, 64))
+    for s in range(3):
+        np.add.at(ref[s], (fy[inside].astype(int), fx[inside].astype(int)), lg[ok, 3 + s][inside])
+    assert np.abs(img[0] - ref).max() <= N * 2.0 ** -fb
+    oref = O.trace_single(prob, 1, N)
+    assert img[0, 0].sum() == pytest.approx(oref[0].sum(), rel=1e-5)
+
+
+MULTI = S.clumpy_problem(n=32, max_orders=20, nx=64, ny=64, per_order=True)
+MULTI_CASES = {
+    "clumpy_force_all": MULTI,
+    "clumpy_force_first": MULTI.replace(force="first", rr_threshold=0.0),
+    "clumpy_owen_summed": MULTI.replace(per_order=False, generator="sobol_owen", seed=9),
+    "sphere_isotropic": S.homogeneous_sphere_problem(sphere_k=0.8, max_orders=12, g=0.0, p_l=0.3, per_order=True),
+}
+
+
+@pytest.mark.parametrize("name", list(MULTI_CASES))
+def test_trace_multiple_fp64_matches_oracle(Q, name):
+    prob = MULTI_CASES[name]
+    N = 1 << 13
+    got = gpu_image(Q, prob, N, precision="f64", accum="f64")
+    ref = oracle_image(prob, N)
+    assert rel_l2(got, ref) <= 1e-10
+    for k in range(got.shape[0]):
+        if np.linalg.norm(ref[k]) > 0:
+            assert rel_l2(got[k], ref[k]) <= 1e-9
+
+
+def test_trace_multiple_fp32_bilinear_first_orders(Q):
+    """FP32 multiple scattering: roulette and exit decisions are thresholds on float
+    values, so a few packets may end one order earlier or later than in FP64; the
+    low orders still agree closely and the whole image to the sampling error scale."""
+    prob = MULTI.replace(splat="bilinear")
+    N = 1 << 14
+    got = gpu_image(Q, prob, N, precision="f32")
+    ref = oracle_image(prob, N)
+    assert rel_l2(got[0], ref[0]) <= 1e-5
+    assert rel_l2(got[1], ref[1]) <= 1e-3
+    assert rel_l2(got.sum(0), ref.sum(0)) <= 1e-3
+
+
+def test_sharded_ranges_sum_bit_exactly(Q):
+    """Fixed-point accumulation is order-independent: two halves traced into one buffer
+    give exactly the unsharded image (the multi-rank path sums such buffers)."""
+    import torch
+
+    prob = DISK32
+    N = 1 << 15
+    sc = Q.Scene(prob)
+    fb = Q.default_frac_bits(prob, N)
+    whole = sc.accum_buffer()
+    sc.trace(1, N, whole, frac_bits=fb)
+    parts = sc.accum_buffer()
+    sc.trace(1, 12345, parts, frac_bits=fb)
+    sc.trace(12346, N - 12345, parts, frac_bits=fb)
+    torch.cuda.synchronize()
+    assert torch.equal(whole, parts)
+
+
+def test_edge_cases(Q):
+    import torch
+
+    # no packets: nothing is written
+    sc = Q.Scene(DISK32)
+    buf = sc.accum_buffer()
+    sc.trace(1, 0, buf, frac_bits=30)
+    # a single packet and a ragged warp
+    for N in (1, 33):
+        got = gpu_image(Q, DISK32, N, precision="f64")
+        assert rel_l2(got, oracle_image(DISK32, N)) <= 1e-10
+    # an empty medium scatters nothing
+    empty = DISK32.replace(grid=S.homogeneous_grid(8, 0.0))
+    assert np.all(gpu_image(Q, empty, 1000) == 0)
+    # tau_min above every optical depth
+    assert np.all(gpu_image(Q, DISK32.replace(tau_min=50.0), 1000) == 0)
+    # the Hammersley point i = N (u = 1) is valid
+    h = DISK32.replace(generator="hammersley", total_n=4096)
+    got = gpu_image(Q, h, 4096, precision="f64")
+    assert rel_l2(got, oracle_image(h, 4096)) <= 1e-10
+    torch.cuda.synchronize()
+    assert torch.all(buf == 0)
+
+
+def test_full_size_single_scattering_sampled(Q):
+    """The benchmark's single-scattering workload (256^3 disk, 256^2 I/Q/U, FP32 trace,
+    fixed-point accumulation) at 2^22 packets: sampled packets against the oracle one
+    by one, and the image total against the packet log."""
+    import torch
+
+    prob = S.flared_disk_problem(n=256)
+    N = 1 << 22
+    img, lg = gpu_image(Q, prob, N, precision="f32", log=True)
+    rng = np.random.default_rng(1)
+    sample = np.unique(rng.integers(0, N, 3000))
+    ref = np.concatenate([O.trace_single(prob, 1 + int(j), 1, log=True)[1] for j in sample])
+    _fp32_packet_check(lg[sample], ref, frac=0.995)
+    ok = lg[:, 8] == 0
+    sx, sy = lg[ok, 6], lg[ok, 7]
+    inside = (np.abs(sx) < 1) & (np.abs(sy) < 1)
+    assert img[0, 0].sum() == pytest.approx(lg[ok, 3][inside].sum(), rel=1e-9)
+    torch.cuda.synchronize()
