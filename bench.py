@@ -1,12 +1,12 @@
 #!/usr/bin/env python
 """Throughput benchmark of the quasi-Monte Carlo tracer on one GB300 (or N, weak scaling).
 
-Workload (one step): single scattering of 2^24 packets from a point source in the
+Workload (one step): single scattering of 2^26 packets from a point source in the
 flared disk (256^3 FP32 density grid over [-1, 1]^3, HG g = 0.5, albedo 0.6,
 p_l = 0.5, observer at 45 degrees), Sobol points, FP32 trace, fixed-point image
 accumulation into a 256x256 I/Q/U image, then the reduction to the FP64 image in
-units of the source luminosity.  Each step traces the next 2^24 points of the
-sequence.  With N ranks every rank traces its own 2^24-packet range per step and the
+units of the source luminosity.  Each step traces the next 2^26 points of the
+sequence.  With N ranks every rank traces its own 2^26-packet range per step and the
 fixed-point images are summed with one all-reduce before the reduction.
 
 Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle instead, on a
@@ -31,7 +31,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "packets/s and wall time to fixed image RMS error (QMC, learned vs plain), 1 GB300"
-PACKETS_PER_STEP = 1 << 24
+PACKETS_PER_STEP = 1 << 26
 OPS_PER_CELL = 10          # algorithmic ALU operations per grid-cell visit (see design notes)
 SMS, LANES_PER_SM = 152, 128
 KERNEL_SOURCES = ["paper_2406_15632_gb300/csrc/qmcrt_device.cuh", "paper_2406_15632_gb300/csrc/qmcrt_trace_single.cu"]
@@ -101,7 +101,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                          "-lms", "200", "-i", str(self.device)], stdout=subprocess.PIPE,
+                                          "-lms", "100", "-i", str(self.device)], stdout=subprocess.PIPE,
                                          stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()

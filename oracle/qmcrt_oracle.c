@@ -271,12 +271,33 @@ static void normalize3(double a[3])
     double n = sqrt(dot3(a, a));
     a[0] /= n; a[1] /= n; a[2] /= n;
 }
-/* Unit vector with polar angle theta (cos given) and azimuth phi (Sec. 3 convention). */
-static void from_angles(double cos_t, double phi, double n[3])
+/* sin and cos of the angle 2 pi u, exact at quarter turns: the turn splits into a
+ * quadrant (4u and its floor are exact in double) and an angle below pi/2, and
+ * sin/cos of the whole follow from the quadrant's symmetry.  (A direct cos(2 pi u)
+ * would give cos(pi/2) = 6e-17 instead of 0, tilting rays that start on a cell face
+ * into a neighbouring row of cells.) */
+static void sincos_2pi(double u, double *s, double *c)
+{
+    double x = 4.0 * u;
+    double q = floor(x);
+    double a = 0.5 * OR_PI * (x - q);
+    double s0 = sin(a), c0 = cos(a);
+    int quadrant = (int)(q - 4.0 * floor(q / 4.0));
+    if (quadrant == 0) { *s = s0; *c = c0; }
+    else if (quadrant == 1) { *s = c0; *c = -s0; }
+    else if (quadrant == 2) { *s = -s0; *c = -c0; }
+    else { *s = -c0; *c = s0; }
+}
+
+/* Unit vector with polar angle theta (cos given) and azimuth phi = 2 pi u (Sec. 3
+ * convention). */
+static void from_angles(double cos_t, double u, double n[3])
 {
     double sin_t = sqrt(fmax(0.0, 1.0 - cos_t * cos_t));
-    n[0] = sin_t * cos(phi);
-    n[1] = sin_t * sin(phi);
+    double sp, cp;
+    sincos_2pi(u, &sp, &cp);
+    n[0] = sin_t * cp;
+    n[1] = sin_t * sp;
     n[2] = cos_t;
 }
 /* The local basis e_theta, e_phi of a unit vector n (spherical-coordinate unit vectors). */
@@ -531,7 +552,7 @@ static double or_emit(const or_source *S, const or_points *P, uint64_t i, double
     if (S->kind == 0) {
         /* Eq. point_source_propagation_direction: phi = 2 pi u, theta = arccos(2v - 1). */
         double u = or_point_f64(P, i, 0), v = or_point_f64(P, i, 1);
-        from_angles(2.0 * v - 1.0, 2.0 * OR_PI * u, dir);
+        from_angles(2.0 * v - 1.0, u, dir);
         pos[0] = pos[1] = pos[2] = 0.0;
         sph_basis(dir, eref, ep);
         return or_point_f64(P, i, 2);
@@ -543,13 +564,14 @@ static double or_emit(const or_source *S, const or_points *P, uint64_t i, double
          * theta_l = sqrt(v4)) cos theta_l = sqrt(v4), the cosine-weighted outward
          * hemisphere of an isotropically radiating surface; v5 the depth. */
         double ne[3];
-        from_angles(2.0 * or_point_f64(P, i, 1) - 1.0, 2.0 * OR_PI * or_point_f64(P, i, 0), ne);
+        from_angles(2.0 * or_point_f64(P, i, 1) - 1.0, or_point_f64(P, i, 0), ne);
         for (int a = 0; a < 3; ++a) pos[a] = S->r * ne[a];
-        double phil = 2.0 * OR_PI * or_point_f64(P, i, 2);
+        double spl, cpl;
+        sincos_2pi(or_point_f64(P, i, 2), &spl, &cpl);
         mu = sqrt(or_point_f64(P, i, 3));
         double sl = sqrt(fmax(0.0, 1.0 - mu * mu));
         sph_basis(ne, et, ep);
-        for (int a = 0; a < 3; ++a) dir[a] = sl * cos(phil) * et[a] + sl * sin(phil) * ep[a] + mu * ne[a];
+        for (int a = 0; a < 3; ++a) dir[a] = sl * cpl * et[a] + sl * spl * ep[a] + mu * ne[a];
         normalize3(dir);
         sph_basis(dir, eref, ep);
         if (S->limb_u != 0) *weight = (1.0 - S->limb_u + S->limb_u * mu) / (1.0 - S->limb_u / 3.0);
@@ -560,13 +582,14 @@ static double or_emit(const or_source *S, const or_points *P, uint64_t i, double
      * the star's disk projected across the direction (radius R sqrt(v4), angle
      * 2 pi v5) lifted onto the hemisphere facing the direction, which gives the same
      * joint density of (point, direction) as the direct order. */
-    from_angles(2.0 * or_point_f64(P, i, 1) - 1.0, 2.0 * OR_PI * or_point_f64(P, i, 0), dir);
+    from_angles(2.0 * or_point_f64(P, i, 1) - 1.0, or_point_f64(P, i, 0), dir);
     double w = or_point_f64(P, i, 2);
     double v4 = or_point_f64(P, i, 3), v5 = or_point_f64(P, i, 4);
-    double rho = S->r * sqrt(v4), psi = 2.0 * OR_PI * v5;
+    double rho = S->r * sqrt(v4), sps, cps;
+    sincos_2pi(v5, &sps, &cps);
     double lift = sqrt(fmax(0.0, S->r * S->r - rho * rho));
     sph_basis(dir, et, ep);
-    for (int a = 0; a < 3; ++a) pos[a] = rho * cos(psi) * et[a] + rho * sin(psi) * ep[a] + lift * dir[a];
+    for (int a = 0; a < 3; ++a) pos[a] = rho * cps * et[a] + rho * sps * ep[a] + lift * dir[a];
     for (int a = 0; a < 3; ++a) eref[a] = et[a];
     mu = sqrt(fmax(0.0, 1.0 - v4));
     if (S->limb_u != 0) *weight = (1.0 - S->limb_u + S->limb_u * mu) / (1.0 - S->limb_u / 3.0);
@@ -699,10 +722,10 @@ static void or_scatter(const or_dust *D, double u, double v, double n[3], double
 {
     double ct = or_hg_cos(D->g, v);
     double st = sqrt(fmax(0.0, 1.0 - ct * ct));
-    double i1 = 2.0 * OR_PI * u;
     double b[3];
     cross3(n, a, b);
-    double ci = cos(i1), si = sin(i1);
+    double ci, si;
+    sincos_2pi(u, &si, &ci); /* i1 = 2 pi u */
     double nn[3], m[3];
     for (int k = 0; k < 3; ++k) {
         nn[k] = ct * n[k] + st * (ci * a[k] + si * b[k]);

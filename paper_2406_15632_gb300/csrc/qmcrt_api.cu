@@ -5,11 +5,17 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <utility>
 
 #include "qmcrt.h"
 #include "qmcrt_internal.h"
+#include "qmcrt_tables.h"
 
 namespace {
+
+// Host copy of the Sobol direction numbers (the same generated table the kernels
+// hold in constant memory), for building the net-order packet mapping.
+const uint32_t kSobolV[QMCRT_GEN_DIMS][32] = QMCRT_GEN_SOBOL_V_INIT;
 
 thread_local std::string g_last_error;
 
@@ -66,6 +72,87 @@ qmcrt::PointsP make_points(const qmcrt_points_desc *d)
     p.total_n = d->total_n;
     p.inv_total_n = d->total_n ? 1.0 / (double)d->total_n : 0.0;
     return p;
+}
+
+// Packet order of a launch (see OrderP): net order for Sobol point sets of at least
+// 2^7 packets, linear otherwise.  Solves y = L g over GF(2) once per call: L maps the
+// Gray code g of an index inside a 2^m block to the leading (a, b, c) bits of its
+// coordinates 0, 1, 2 (a + b + c = m - tt, balanced); tt is the smallest value for
+// which L has full row rank (the elementary boxes then hold 2^tt points each).
+void make_order(int kind, uint64_t first, uint64_t count, qmcrt::OrderP &O)
+{
+    memset(&O, 0, sizeof O);
+    O.threads = count;
+    if (count == 0 || (kind != QMCRT_SOBOL && kind != QMCRT_SOBOL_OWEN)) return;
+    int m = 0;
+    while (m < qmcrt::NET_MAX_M && (2ull << m) <= count) ++m;
+    if (m < 7) return;
+    for (int tt = 0; tt <= 3; ++tt) {
+        const int bits = m - tt;
+        const int a = (bits + 2) / 3, b = (bits + 1) / 3, c = bits / 3;
+        uint32_t Lr[qmcrt::NET_MAX_M], Er[qmcrt::NET_MAX_M];
+        for (int rho = 0; rho < bits; ++rho) {
+            int dim, bit;
+            if (rho < c) { dim = 2; bit = 32 - c + rho; }
+            else if (rho < c + b) { dim = 1; bit = 32 - b + (rho - c); }
+            else { dim = 0; bit = 32 - a + (rho - c - b); }
+            uint32_t row = 0;
+            for (int k = 0; k < m; ++k) row |= ((kSobolV[dim][k] >> bit) & 1u) << k;
+            Lr[rho] = row;
+            Er[rho] = 1u << rho;
+        }
+        int piv[qmcrt::NET_MAX_M], rank = 0;
+        for (int col = 0; col < m && rank < bits; ++col) {
+            int sel = -1;
+            for (int q = rank; q < bits; ++q)
+                if ((Lr[q] >> col) & 1u) { sel = q; break; }
+            if (sel < 0) continue;
+            std::swap(Lr[sel], Lr[rank]);
+            std::swap(Er[sel], Er[rank]);
+            for (int q = 0; q < bits; ++q)
+                if (q != rank && ((Lr[q] >> col) & 1u)) {
+                    Lr[q] ^= Lr[rank];
+                    Er[q] ^= Er[rank];
+                }
+            piv[rank++] = col;
+        }
+        if (rank < bits) continue;
+        O.net = 1;
+        O.m = m;
+        O.bits = bits;
+        O.tt = tt;
+        O.a = a;
+        O.b = b;
+        O.c = c;
+        for (int j = 0; j < bits; ++j) {
+            uint32_t col = 0;
+            for (int q = 0; q < bits; ++q) col |= ((Er[q] >> j) & 1u) << piv[q];
+            O.ry[j] = col;
+        }
+        int nk = 0;
+        for (int f = 0; f < m; ++f) {
+            bool is_piv = false;
+            for (int q = 0; q < bits; ++q) is_piv |= piv[q] == f;
+            if (is_piv) continue;
+            uint32_t kv = 1u << f;
+            for (int q = 0; q < bits; ++q) kv |= ((Lr[q] >> f) & 1u) << piv[q];
+            O.k[nk++] = kv;
+        }
+        // Morton order of the boxes: thread bits go round-robin to the finest
+        // remaining bit of coordinates 0, 1, 2.
+        int used[3] = {0, 0, 0};
+        const int nbits[3] = {a, b, c}, off[3] = {b + c, c, 0};
+        for (int j = 0; j < bits;) {
+            for (int comp = 0; comp < 3 && j < bits; ++comp) {
+                if (used[comp] >= nbits[comp]) continue;
+                O.rm[j++] = O.ry[off[comp] + used[comp]++];
+            }
+        }
+        O.block0 = first >> m;
+        const uint64_t nblocks = ((first + count - 1) >> m) - O.block0 + 1;
+        O.threads = nblocks << m;
+        return;
+    }
 }
 
 template <class T>
@@ -180,7 +267,7 @@ int fill_trace(const qmcrt_medium *md, const qmcrt_source *src, const qmcrt_dust
     P.pts = make_points(pts);
     P.first = pts->first_index;
     P.count = pts->count;
-    P.stride = (pts->count + 31) / 32;
+    make_order(pts->kind, pts->first_index, pts->count, P.ord);
     // image
     if (!im->d_accum) return fail(QMCRT_ERR_INVALID_ARG, "image->d_accum is NULL");
     if (im->accum != QMCRT_ACCUM_I64 && im->accum != QMCRT_ACCUM_F64)

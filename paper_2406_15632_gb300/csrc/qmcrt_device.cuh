@@ -203,24 +203,60 @@ __device__ __forceinline__ T point(const PointsP &P, uint64_t i, int d)
     return Mth<T>::from_f64(point_f64(P, i, d));
 }
 
+// Point index traced by thread tid (see OrderP); false if it lies outside the range.
+__device__ __forceinline__ uint32_t gray_inverse(uint32_t g)
+{
+    g ^= g >> 1;
+    g ^= g >> 2;
+    g ^= g >> 4;
+    g ^= g >> 8;
+    g ^= g >> 16;
+    return g;
+}
+
+__device__ __forceinline__ uint32_t lead_bits(uint32_t x, int n) { return n ? x >> (32 - n) : 0u; }
+
+__device__ __forceinline__ bool packet_index(const OrderP &O, uint64_t first, uint64_t count, uint64_t tid,
+                                             uint64_t &i)
+{
+    if (!O.net) {
+        i = first + tid;
+        return tid < count;
+    }
+    const uint64_t base = (O.block0 + (tid >> O.m)) << O.m;
+    const uint32_t tl = (uint32_t)(tid & ((1ull << O.m) - 1));
+    const uint32_t box = tl >> O.tt;
+    uint32_t g = 0;
+    for (int j = 0; j < O.bits; ++j) g ^= ((box >> j) & 1u) ? O.rm[j] : 0u;
+    for (int j = 0; j < O.tt; ++j) g ^= ((tl >> j) & 1u) ? O.k[j] : 0u;
+    const uint32_t y = (lead_bits(sobol_u32((uint32_t)base, 0), O.a) << (O.b + O.c)) |
+                       (lead_bits(sobol_u32((uint32_t)base, 1), O.b) << O.c) | lead_bits(sobol_u32((uint32_t)base, 2), O.c);
+    for (int j = 0; j < O.bits; ++j) g ^= ((y >> j) & 1u) ? O.ry[j] : 0u;
+    i = base + gray_inverse(g);
+    return i >= first && i < first + count;
+}
+
 // ------------------------------------------------------------------------------------
 // Optical depth along a ray (Sec. 3.4)
 // ------------------------------------------------------------------------------------
 
-// Cell of coordinate x; on a face, the cell the ray enters.
+// Cell of coordinate x; on a face, the cell the ray enters.  (x - lo) drops the low
+// digits of a coordinate much smaller than lo (in float a point 2e-8 below the face
+// through the origin becomes a point on it), so the estimate is settled against the
+// face coordinates themselves.
 template <class T>
 __device__ __forceinline__ int start_cell(T x, T lo, T h, T d)
 {
-    const T f = (x - lo) / h;
-    const T fl = Mth<T>::floor_(f);
-    int c = (int)fl;
-    if (f == fl && d < T(0)) c -= 1;
+    int c = (int)Mth<T>::floor_((x - lo) / h);
+    if (x < lo + T(c) * h) --c;
+    else if (x >= lo + T(c + 1) * h) ++c;
+    if (d < T(0) && x == lo + T(c) * h) --c;
     return c;
 }
 
 template <class T>
 struct AxisWalk {
-    T t_next, dt;
+    T s, dt;   // distance along the ray to this axis's next face; length of one cell crossing
     int step, left;
 };
 
@@ -229,19 +265,19 @@ __device__ __forceinline__ AxisWalk<T> axis_setup(T p, T d, int c, T lo, T h, in
 {
     AxisWalk<T> a;
     if (d > T(0)) {
-        a.t_next = (lo + T(c + 1) * h - p) / d;
+        a.s = (lo + T(c + 1) * h - p) / d;
         a.dt = h / d;
         a.step = stride;
         a.left = n - 1 - c;
     } else if (d < T(0)) {
-        a.t_next = (lo + T(c) * h - p) / d;
+        a.s = (lo + T(c) * h - p) / d;
         a.dt = -h / d;
         a.step = -stride;
         a.left = c;
     } else {
         // never the nearest face unless every axis is (a zero direction): then the
         // walk ends at once instead of stepping in place
-        a.t_next = Mth<T>::inf();
+        a.s = Mth<T>::inf();
         a.dt = T(0);
         a.step = 0;
         a.left = 0;
@@ -250,11 +286,15 @@ __device__ __forceinline__ AxisWalk<T> axis_setup(T p, T d, int c, T lo, T h, in
 }
 
 // Walk through the grid cells from p along unit d.
-//   TARGET = false: returns the optical depth to the grid edge in tau_out.
+//   TARGET = false: returns the optical depth to the grid edge in tau_raw.
 //   TARGET = true : stops where the optical depth reaches target (true, t_out = path
 //                   length), or leaves the grid first (false, t_out = far end of the
 //                   last segment with nonzero density).
-// Sums run over raw cell values (the caller scales by kscale) with Kahan compensation.
+// Each axis keeps the distance to its own next face, so a segment length is the
+// smallest of three cell-sized numbers rather than a difference of two path
+// lengths of order one: in float this keeps every segment, and hence every cell's
+// optical depth, to a few units in the last place.  Sums run over raw cell values
+// (the caller scales by kscale) with Kahan compensation.
 template <class T, bool TARGET>
 __device__ __forceinline__ bool grid_walk(const MediumP<T> &G, const T p[3], const T d[3], T target_raw, T &tau_raw,
                                           T &t_out)
@@ -273,8 +313,8 @@ __device__ __forceinline__ bool grid_walk(const MediumP<T> &G, const T p[3], con
     T t = T(0), acc = TARGET ? target_raw : T(0), comp = T(0), t_last = T(0);
     for (;;) {
         const T kc = (T)__ldg(K + idx);
-        const T tm = Mth<T>::min_(X.t_next, Mth<T>::min_(Y.t_next, Z.t_next));
-        const T dtau = (tm - t) * kc;
+        const T L = Mth<T>::min_(X.s, Mth<T>::min_(Y.s, Z.s));
+        const T dtau = L * kc;
         if (TARGET) {
             const T rem = acc - comp;
             if (kc > T(0) && dtau >= rem) {
@@ -286,26 +326,29 @@ __device__ __forceinline__ bool grid_walk(const MediumP<T> &G, const T p[3], con
             const T s = acc + y;
             comp = (s - acc) - y;
             acc = s;
-            if (kc > T(0) && tm > t) t_last = tm;
+            t += L;
+            if (kc > T(0) && L > T(0)) t_last = t;
         } else {
             const T y = dtau - comp;  // acc += dtau, compensated
             const T s = acc + y;
             comp = (s - acc) - y;
             acc = s;
         }
-        t = tm;
-        if (X.t_next == tm) {
+        X.s -= L;  // exact (zero) for the axis whose face is reached
+        Y.s -= L;
+        Z.s -= L;
+        if (X.s == T(0)) {  // ties step x, then y, then z
             if (X.left-- == 0) break;
             idx += X.step;
-            X.t_next += X.dt;
-        } else if (Y.t_next == tm) {
+            X.s = X.dt;
+        } else if (Y.s == T(0)) {
             if (Y.left-- == 0) break;
             idx += Y.step;
-            Y.t_next += Y.dt;
+            Y.s = Y.dt;
         } else {
             if (Z.left-- == 0) break;
             idx += Z.step;
-            Z.t_next += Z.dt;
+            Z.s = Z.dt;
         }
     }
     if (TARGET) {

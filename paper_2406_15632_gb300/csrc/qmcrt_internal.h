@@ -64,8 +64,31 @@ struct AccumP {
     size_t plane;      // nx * ny
 };
 
+// Packet order.  Linear: thread t traces point first + t.  Net order (Sobol kinds):
+// the index range is covered by aligned blocks of 2^m indices, and inside a block
+// thread t traces the point whose leading (a, b, c) bits of coordinates (0, 1, 2)
+// form the t-th elementary box in Morton order (2^tt points per box, tt = the
+// t-value of the chosen split).  With y(i) the vector of those leading bits and g the
+// Gray code of the index inside the block, y(i) = y(block start) ^ L g over GF(2);
+// the host inverts L: g = R (y ^ y(block start)) ^ K e, e selecting within the box.
+// Consecutive threads, hence a warp, receive points from adjacent boxes: packets that
+// start in nearly the same direction and scatter at nearly the same depth.
+constexpr int NET_MAX_M = 24;
+
+struct OrderP {
+    int net;            // 0 linear, 1 net order
+    int m, bits, tt;    // block 2^m, bits = m - tt Morton bits, tt kernel bits
+    int a, b, c;        // leading bits taken from coordinates 0, 1, 2
+    uint64_t block0;    // first block index
+    uint64_t threads;   // threads to launch (count when linear)
+    uint32_t rm[NET_MAX_M];  // R column for Morton bit j of the thread's box index
+    uint32_t ry[NET_MAX_M];  // R column for bit j of y
+    uint32_t k[4];           // kernel basis of L
+};
+
 template <class T>
 struct TraceP {
+    OrderP ord;
     MediumP<T> med;
     SourceP<T> src;
     DustP<T> dust;
@@ -75,7 +98,6 @@ struct TraceP {
     T tau_min;
     uint64_t first;    // first point index
     uint64_t count;    // packets
-    uint64_t stride;   // lane stride: ceil(count / 32); lane l of warp task w traces first + l*stride + w
     double *log;       // optional [count][9]
     int max_orders, force_all, per_order;
     T rr_threshold, rr_survival, inv_rr_survival;

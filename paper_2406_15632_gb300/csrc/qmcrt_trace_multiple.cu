@@ -11,12 +11,12 @@ namespace qmcrt {
 template <class T>
 __global__ void __launch_bounds__(256) k_trace_multiple(const __grid_constant__ TraceP<T> P)
 {
-    const int lane = threadIdx.x & 31;
-    const uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (w >= P.stride) return;  // uniform per warp
-    const uint64_t j = (uint64_t)lane * P.stride + w;
-    bool alive = j < P.count;
-    const uint64_t i = P.first + j;
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if ((tid & ~31ull) >= P.ord.threads) return;  // uniform per warp
+    uint64_t i;
+    const bool live_index = packet_index(P.ord, P.first, P.count, tid, i);
+    if (!__any_sync(FULL_MASK, live_index)) return;
+    bool alive = live_index;
     T pos[3] = {T(0), T(0), T(0)}, n[3] = {T(0), T(0), T(1)}, a[3] = {T(1), T(0), T(0)};
     T S[3] = {T(0), T(0), T(0)};
     T wd = T(0);
@@ -76,7 +76,7 @@ template <class T>
 static cudaError_t launch(const TraceP<T> &p, int block, cudaStream_t s)
 {
     if (p.count == 0) return cudaSuccess;
-    const uint64_t threads = p.stride * 32;
+    const uint64_t threads = (p.ord.threads + 31) & ~31ull;
     const uint64_t grid = (threads + block - 1) / block;
     k_trace_multiple<T><<<(unsigned)grid, block, 0, s>>>(p);
     return cudaGetLastError();

@@ -1,11 +1,10 @@
 // qmcrt_trace_single.cu -- single-scattering tracer kernel (Sec. 3.2-3.6).
 //
-// Packet mapping: warp task w (0 <= w < stride = ceil(count/32)) traces the packets
-// j = lane * stride + w.  The 32 packets of a warp differ only in the high bits of
-// their index, so for Sobol points (whose leading bits in every coordinate depend
-// only on the low bits of the index) they start in nearly the same direction, march
-// through the same cells and usually land in the same pixel: the warp stays coherent
-// and its deposits collapse to one atomic.
+// Packet mapping (OrderP): for Sobol point sets a warp receives 32 points from
+// adjacent elementary boxes of the first three coordinates, so its packets start in
+// nearly the same direction, scatter at nearly the same depth, walk the same cells
+// and usually land in the same pixel: the warp stays coherent and its deposits
+// collapse to one atomic per Stokes component.
 #include "qmcrt_device.cuh"
 
 namespace qmcrt {
@@ -13,17 +12,18 @@ namespace qmcrt {
 template <class T>
 __global__ void __launch_bounds__(256) k_trace_single(const __grid_constant__ TraceP<T> P)
 {
-    const int lane = threadIdx.x & 31;
-    const uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (w >= P.stride) return;  // uniform per warp
-    const uint64_t j = (uint64_t)lane * P.stride + w;
-    const bool live = j < P.count;
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if ((tid & ~31ull) >= P.ord.threads) return;  // uniform per warp
+    uint64_t i;
+    const bool live_index = packet_index(P.ord, P.first, P.count, tid, i);
+    if (!__any_sync(FULL_MASK, live_index)) return;
+    const uint64_t j = i - P.first;
+    const bool live = live_index;
     T S[3] = {T(0), T(0), T(0)};
     T x = T(0), y = T(0);
     int status = 1;
     T pos[3] = {T(0), T(0), T(0)};
     if (live) {
-        const uint64_t i = P.first + j;
         T d[3], a[3], wgt, W1;
         const T wd = emit(P, i, pos, d, a, wgt);
         if (forced_step(P, pos, d, wd, W1)) {
@@ -50,7 +50,7 @@ template <class T>
 static cudaError_t launch(const TraceP<T> &p, int block, cudaStream_t s)
 {
     if (p.count == 0) return cudaSuccess;
-    const uint64_t threads = p.stride * 32;
+    const uint64_t threads = (p.ord.threads + 31) & ~31ull;
     const uint64_t grid = (threads + block - 1) / block;
     k_trace_single<T><<<(unsigned)grid, block, 0, s>>>(p);
     return cudaGetLastError();

@@ -223,3 +223,15 @@ def test_occultation_by_the_star():
     assert ok
     ok, _ = O.peel_packet(prob, [0.5, 0.0, 0.0], [1, 0, 0], [0, 0, 1], [1, 0, 0])
     assert ok
+
+
+def test_quarter_turn_directions_are_exact():
+    """phi = 2 pi u at u = 1/4, 1/2, 3/4 (Sobol indices 3, 1, 2) gives directions with an
+    exactly zero x or y component, so rays from a source on a cell face stay on it."""
+    prob = S.Problem(**EMPTY, generator="sobol")
+    _, d1, _, _, _ = O.emit_packet(prob, 1)  # u = 1/2: phi = pi
+    _, d2, _, _, _ = O.emit_packet(prob, 2)  # u = 3/4: phi = 3 pi / 2
+    _, d3, _, _, _ = O.emit_packet(prob, 3)  # u = 1/4: phi = pi / 2
+    assert d1[1] == 0.0 and d1[0] < 0
+    assert d2[0] == 0.0 and d2[1] < 0
+    assert d3[0] == 0.0 and d3[1] > 0
