@@ -205,6 +205,32 @@ int qmcrt_trace_multiple(const qmcrt_medium *medium, const qmcrt_source *source,
 int qmcrt_image_reduce(const qmcrt_image *image, int32_t nx, int32_t ny, int32_t n_replicas, double scale,
                        double *d_out, void *stream);
 
+/*
+ * qmcrt_trace_single_noalloc -- qmcrt_trace_single followed by qmcrt_image_reduce for
+ * one image, for callers that cannot allocate device memory: code embedded in a host
+ * application that owns every device allocation through its own pool, or code that
+ * must not allocate once running (an allocation can synchronize the device, or fail
+ * under memory pressure at a bad moment).  The paper has no counterpart; this is a
+ * convenience of the library.
+ * The fixed-point accumulation scratch is a device array inside the library (3 x
+ * QMCRT_NOALLOC_MAX_PIXELS int64 values, 6 MiB, held on every GPU that loads the
+ * library until the process exits); nothing is allocated.  The caller passes the
+ * descriptors of qmcrt_trace_single, the fixed-point scale frac_bits (as in
+ * qmcrt_image), the final scale (normally 1/N) and d_image: device double
+ * [3][ny][nx], overwritten with the image.
+ * Every call clears the part of the scratch it uses, then traces and reduces on
+ * stream.  All calls share the one scratch array: calls whose work overlaps on the
+ * GPU (other streams, other host threads) race and corrupt each other's images.
+ * The first call on a device looks up the scratch address with that device current;
+ * make it before any stream capture.
+ * Errors: as qmcrt_trace_single; INVALID_ARG for NULL d_image or an image of more than
+ * QMCRT_NOALLOC_MAX_PIXELS pixels; CUDA if the scratch address cannot be found.
+ */
+#define QMCRT_NOALLOC_MAX_PIXELS (512 * 512)
+int qmcrt_trace_single_noalloc(const qmcrt_medium *medium, const qmcrt_source *source, const qmcrt_dust *dust,
+                               const qmcrt_observer *obs, const qmcrt_points_desc *pts, const qmcrt_trace_opts *opts,
+                               int32_t frac_bits, double scale, double *d_image, void *stream);
+
 /* Thread-local message describing the last error (empty if none). */
 const char *qmcrt_last_error(void);
 

@@ -316,6 +316,21 @@ int trace_common(const qmcrt_medium *md, const qmcrt_source *src, const qmcrt_du
 
 }  // namespace
 
+namespace qmcrt {
+
+int set_error(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+}  // namespace qmcrt
+
 extern "C" {
 
 int qmcrt_abi_version(void) { return QMCRT_ABI_VERSION; }

@@ -103,6 +103,9 @@ struct TraceP {
     T rr_threshold, rr_survival, inv_rr_survival;
 };
 
+// Records a message for qmcrt_last_error() on the calling thread; returns code.
+int set_error(int code, const char *fmt, ...);
+
 // Launchers (return a cudaError_t from the launch).
 cudaError_t launch_generate_points(const PointsP &p, uint64_t first, uint64_t count, int format, void *out,
                                    cudaStream_t s);

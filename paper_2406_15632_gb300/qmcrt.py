@@ -100,6 +100,9 @@ _SIGS = [
                                        _P(qmcrt_points_desc), _P(qmcrt_trace_opts), _P(qmcrt_image), C.c_void_p]),
     ("qmcrt_image_reduce", C.c_int, [_P(qmcrt_image), C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_void_p,
                                      C.c_void_p]),
+    ("qmcrt_trace_single_noalloc", C.c_int, [_P(qmcrt_medium), _P(qmcrt_source), _P(qmcrt_dust),
+                                             _P(qmcrt_observer), _P(qmcrt_points_desc), _P(qmcrt_trace_opts),
+                                             C.c_int32, C.c_double, C.c_void_p, C.c_void_p]),
 ]
 EXPORTED = [s[0] for s in _SIGS]
 
@@ -150,6 +153,16 @@ def qmcrt_trace_multiple(medium, source, dust, obs, pts, opts, image, stream: in
 def qmcrt_image_reduce(image, nx: int, ny: int, n_replicas: int, scale: float, d_out: int, stream: int = 0) -> None:
     _check(load().qmcrt_image_reduce(C.byref(image), nx, ny, n_replicas, scale, C.c_void_p(d_out),
                                      C.c_void_p(stream)))
+
+
+def qmcrt_trace_single_noalloc(medium, source, dust, obs, pts, opts, frac_bits: int, scale: float, d_image: int,
+                               stream: int = 0) -> None:
+    """Single scattering into the FP64 image at d_image ([3][ny][nx]) with the library's
+    own accumulation scratch: for callers that cannot allocate device memory.  Calls
+    share that scratch, so calls that overlap on the GPU must be avoided."""
+    _check(load().qmcrt_trace_single_noalloc(C.byref(medium), C.byref(source), C.byref(dust), C.byref(obs),
+                                             C.byref(pts), C.byref(opts), frac_bits, scale, C.c_void_p(d_image),
+                                             C.c_void_p(stream)))
 
 
 # --- marshalling helpers ------------------------------------------------------------------
