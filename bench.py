@@ -149,11 +149,12 @@ def run_cpu_baseline(target_seconds: float = 12.0):
 
     prob = workload_problem()
     threads = O.default_threads()
-    n0 = 1 << 14
-    t = time.perf_counter()
-    O.trace_single(prob, 1, n0, nthreads=threads)
-    rate0 = n0 / (time.perf_counter() - t)
-    n = int(min(max(rate0 * target_seconds, n0), 1 << 26))
+    n = 1 << 14
+    for _ in range(2):  # calibrate on growing samples (thread start-up dominates tiny ones)
+        t = time.perf_counter()
+        O.trace_single(prob, 1, n, nthreads=threads)
+        rate = n / (time.perf_counter() - t)
+        n = int(min(max(rate * (target_seconds if _ else 1.5), 1 << 14), 1 << 27))
     t = time.perf_counter()
     O.trace_single(prob, 1, n, nthreads=threads)
     dt = time.perf_counter() - t

@@ -78,12 +78,15 @@ int qmcrt_generate_points(const qmcrt_points_desc *d, void *d_out, void *stream)
 #define QMCRT_MEDIUM_GRID 0   /* Cartesian grid, constant kappa*rho per cell */
 #define QMCRT_MEDIUM_SPHERE 1 /* homogeneous sphere centred at the origin (analytic chords) */
 
+#define QMCRT_MIN_PAD 8 /* sentinel layers a padded grid needs (qmcrt_pad_grid) */
+
 typedef struct qmcrt_medium {
     uint32_t struct_size;
     int32_t kind;
-    const float *d_k;  /* grid: device [nz][ny][nx] extinction kappa*rho per unit length, x fastest */
-    int32_t nx, ny, nz;
-    int32_t reserved;
+    const float *d_k;  /* grid: device [nz][ny][nx] extinction kappa*rho per unit length, x fastest;
+                          with pad > 0 the [nz+2pad][ny+2pad][nx+2pad] array of qmcrt_pad_grid */
+    int32_t nx, ny, nz; /* cells of the grid proper (without padding) */
+    int32_t pad;        /* 0, or >= QMCRT_MIN_PAD sentinel layers (faster walk) */
     double lo[3], hi[3]; /* grid box; every packet starts inside it */
     double kscale;       /* multiplier on every cell (opacity at another wavelength) */
     double sphere_r;     /* sphere medium: radius */
@@ -193,6 +196,16 @@ int qmcrt_trace_single(const qmcrt_medium *medium, const qmcrt_source *source, c
 int qmcrt_trace_multiple(const qmcrt_medium *medium, const qmcrt_source *source, const qmcrt_dust *dust,
                          const qmcrt_observer *obs, const qmcrt_points_desc *pts, const qmcrt_trace_opts *opts,
                          const qmcrt_image *image, void *stream);
+
+/*
+ * qmcrt_pad_grid -- prepares a grid for the faster walk (Sec. 3.4 optical-depth
+ * integration, unchanged in result): writes d_padded, device float
+ * [nz+2pad][ny+2pad][nx+2pad], the cells of d_k ([nz][ny][nx]) surrounded by pad layers
+ * of the sentinel value -1.  Pass d_padded with qmcrt_medium.pad = pad.
+ * Errors: INVALID_ARG (NULL pointers, empty grid, pad < QMCRT_MIN_PAD, more than 2^31
+ * padded cells), CUDA.
+ */
+int qmcrt_pad_grid(const float *d_k, int32_t nx, int32_t ny, int32_t nz, int32_t pad, float *d_padded, void *stream);
 
 /*
  * qmcrt_image_reduce -- final image in units of the source luminosity (Sec. 3.6):

@@ -179,9 +179,14 @@ int fill_trace(const qmcrt_medium *md, const qmcrt_source *src, const qmcrt_dust
             P.med.hi[a] = (T)md->hi[a];
             P.med.h[a] = (T)((md->hi[a] - md->lo[a]) / n[a]);
         }
+        if (md->pad != 0 && md->pad < QMCRT_MIN_PAD)
+            return fail(QMCRT_ERR_INVALID_ARG, "pad %d: 0 or at least %d", md->pad, QMCRT_MIN_PAD);
+        const int px = md->nx + 2 * md->pad, py = md->ny + 2 * md->pad, pz = md->nz + 2 * md->pad;
+        if ((double)px * py * pz > 2147483647.0) return fail(QMCRT_ERR_INVALID_ARG, "padded grid larger than 2^31 cells");
+        P.med.pad = md->pad;
         P.med.stride[0] = 1;
-        P.med.stride[1] = md->nx;
-        P.med.stride[2] = md->nx * md->ny;
+        P.med.stride[1] = px;
+        P.med.stride[2] = px * py;
         P.med.k = md->d_k;
     } else if (md->kind == QMCRT_MEDIUM_SPHERE) {
         if (!(md->sphere_r > 0) || !(md->sphere_k >= 0)) return fail(QMCRT_ERR_INVALID_ARG, "sphere medium needs r > 0, k >= 0");
@@ -366,6 +371,17 @@ int qmcrt_trace_multiple(const qmcrt_medium *medium, const qmcrt_source *source,
 {
     g_last_error.clear();
     return trace_common(medium, source, dust, obs, pts, opts, image, nullptr, stream, 1);
+}
+
+int qmcrt_pad_grid(const float *d_k, int32_t nx, int32_t ny, int32_t nz, int32_t pad, float *d_padded, void *stream)
+{
+    g_last_error.clear();
+    if (!d_k || !d_padded) return fail(QMCRT_ERR_INVALID_ARG, "NULL grid pointer");
+    if (nx < 1 || ny < 1 || nz < 1) return fail(QMCRT_ERR_INVALID_ARG, "grid has zero cells");
+    if (pad < QMCRT_MIN_PAD) return fail(QMCRT_ERR_INVALID_ARG, "pad %d < %d", pad, QMCRT_MIN_PAD);
+    if ((double)(nx + 2 * pad) * (ny + 2 * pad) * (nz + 2 * pad) > 2147483647.0)
+        return fail(QMCRT_ERR_INVALID_ARG, "padded grid larger than 2^31 cells");
+    return cuda_status(qmcrt::launch_pad_grid(d_k, nx, ny, nz, pad, d_padded, (cudaStream_t)stream), "pad_grid launch");
 }
 
 int qmcrt_image_reduce(const qmcrt_image *image, int32_t nx, int32_t ny, int32_t n_replicas, double scale,

@@ -264,6 +264,10 @@ template <class T>
 __device__ __forceinline__ AxisWalk<T> axis_setup(T p, T d, int c, T lo, T h, int n, int stride)
 {
     AxisWalk<T> a;
+    a.s = Mth<T>::inf();
+    a.dt = T(0);
+    a.step = 0;
+    a.left = 0;
     if (d > T(0)) {
         a.s = (lo + T(c + 1) * h - p) / d;
         a.dt = h / d;
@@ -274,15 +278,28 @@ __device__ __forceinline__ AxisWalk<T> axis_setup(T p, T d, int c, T lo, T h, in
         a.dt = -h / d;
         a.step = -stride;
         a.left = c;
-    } else {
-        // never the nearest face unless every axis is (a zero direction): then the
-        // walk ends at once instead of stepping in place
+    }
+    if (!(d != T(0) && a.s < Mth<T>::inf() && a.dt < Mth<T>::inf())) {
+        // an axis the ray never crosses (zero component, or a face distance beyond
+        // float range): never the nearest face
         a.s = Mth<T>::inf();
         a.dt = T(0);
         a.step = 0;
         a.left = 0;
     }
     return a;
+}
+
+// A walk needs a finite start and direction and at least one axis it crosses; with
+// those every step reaches the nearest face of a crossed axis and moves one cell, so
+// both walks below end after at most nx + ny + nz steps (plus one batch).
+template <class T>
+__device__ __forceinline__ bool walkable(const T p[3], const T d[3])
+{
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) ok &= (p[a] - p[a] == T(0)) && (d[a] - d[a] == T(0));  // finite
+    return ok && (d[0] != T(0) || d[1] != T(0) || d[2] != T(0));
 }
 
 // Walk through the grid cells from p along unit d.
@@ -295,6 +312,15 @@ __device__ __forceinline__ AxisWalk<T> axis_setup(T p, T d, int c, T lo, T h, in
 // lengths of order one: in float this keeps every segment, and hence every cell's
 // optical depth, to a few units in the last place.  Sums run over raw cell values
 // (the caller scales by kscale) with Kahan compensation.
+//
+// The geometry of a walk does not depend on the densities, so it runs WALK_UNROLL
+// cells ahead: one batch computes the segments and cell indices of the next cells,
+// issues their density loads together (independent loads in flight at once instead
+// of one dependent load per cell), then accumulates their optical depths in order.
+// After the ray leaves the grid the rest of the batch repeats the last cell with
+// zero length, so no load leaves the grid.
+constexpr int WALK_UNROLL = 4;
+
 template <class T, bool TARGET>
 __device__ __forceinline__ bool grid_walk(const MediumP<T> &G, const T p[3], const T d[3], T target_raw, T &tau_raw,
                                           T &t_out)
@@ -304,52 +330,163 @@ __device__ __forceinline__ bool grid_walk(const MediumP<T> &G, const T p[3], con
     const int cz = start_cell(p[2], G.lo[2], G.h[2], d[2]);
     tau_raw = T(0);
     t_out = T(0);
+    if (!walkable(p, d)) return false;
     if (cx < 0 || cx >= G.n[0] || cy < 0 || cy >= G.n[1] || cz < 0 || cz >= G.n[2]) return false;
     AxisWalk<T> X = axis_setup(p[0], d[0], cx, G.lo[0], G.h[0], G.n[0], G.stride[0]);
     AxisWalk<T> Y = axis_setup(p[1], d[1], cy, G.lo[1], G.h[1], G.n[1], G.stride[1]);
     AxisWalk<T> Z = axis_setup(p[2], d[2], cz, G.lo[2], G.h[2], G.n[2], G.stride[2]);
+    if (X.step == 0 && Y.step == 0 && Z.step == 0) return false;
     int idx = cx * G.stride[0] + cy * G.stride[1] + cz * G.stride[2];
     const float *__restrict__ K = G.k;
     T t = T(0), acc = TARGET ? target_raw : T(0), comp = T(0), t_last = T(0);
+    bool done = false;
     for (;;) {
-        const T kc = (T)__ldg(K + idx);
-        const T L = Mth<T>::min_(X.s, Mth<T>::min_(Y.s, Z.s));
-        const T dtau = L * kc;
-        if (TARGET) {
-            const T rem = acc - comp;
-            if (kc > T(0) && dtau >= rem) {
-                t_out = t + rem / kc;
-                tau_raw = target_raw;
-                return true;
+        T L[WALK_UNROLL];
+        int cell[WALK_UNROLL];
+#pragma unroll
+        for (int u = 0; u < WALK_UNROLL; ++u) {
+            cell[u] = idx;
+            const T l = done ? T(0) : Mth<T>::min_(X.s, Mth<T>::min_(Y.s, Z.s));
+            L[u] = l;
+            X.s -= l;  // exact (zero) for the axis whose face is reached
+            Y.s -= l;
+            Z.s -= l;
+            if (!done) {
+                if (X.s == T(0)) {  // ties step x, then y, then z
+                    done = X.left-- == 0;
+                    if (!done) {
+                        idx += X.step;
+                        X.s = X.dt;
+                    }
+                } else if (Y.s == T(0)) {
+                    done = Y.left-- == 0;
+                    if (!done) {
+                        idx += Y.step;
+                        Y.s = Y.dt;
+                    }
+                } else {
+                    done = Z.left-- == 0;
+                    if (!done) {
+                        idx += Z.step;
+                        Z.s = Z.dt;
+                    }
+                }
             }
-            const T y = -dtau - comp;  // acc -= dtau, compensated
-            const T s = acc + y;
-            comp = (s - acc) - y;
-            acc = s;
-            t += L;
-            if (kc > T(0) && L > T(0)) t_last = t;
-        } else {
-            const T y = dtau - comp;  // acc += dtau, compensated
-            const T s = acc + y;
-            comp = (s - acc) - y;
-            acc = s;
         }
-        X.s -= L;  // exact (zero) for the axis whose face is reached
-        Y.s -= L;
-        Z.s -= L;
-        if (X.s == T(0)) {  // ties step x, then y, then z
-            if (X.left-- == 0) break;
-            idx += X.step;
-            X.s = X.dt;
-        } else if (Y.s == T(0)) {
-            if (Y.left-- == 0) break;
-            idx += Y.step;
-            Y.s = Y.dt;
-        } else {
-            if (Z.left-- == 0) break;
-            idx += Z.step;
-            Z.s = Z.dt;
+        T kc[WALK_UNROLL];
+#pragma unroll
+        for (int u = 0; u < WALK_UNROLL; ++u) kc[u] = (T)__ldg(K + cell[u]);
+#pragma unroll
+        for (int u = 0; u < WALK_UNROLL; ++u) {
+            const T dtau = L[u] * kc[u];
+            if (TARGET) {
+                const T rem = acc - comp;
+                if (kc[u] > T(0) && dtau >= rem) {
+                    t_out = t + rem / kc[u];
+                    tau_raw = target_raw;
+                    return true;
+                }
+                const T y = -dtau - comp;  // acc -= dtau, compensated
+                const T s = acc + y;
+                comp = (s - acc) - y;
+                acc = s;
+                t += L[u];
+                if (kc[u] > T(0) && L[u] > T(0)) t_last = t;
+            } else {
+                const T y = dtau - comp;  // acc += dtau, compensated
+                const T s = acc + y;
+                comp = (s - acc) - y;
+                acc = s;
+            }
         }
+        if (done) break;
+    }
+    if (TARGET) {
+        t_out = t_last;
+        tau_raw = target_raw - (acc - comp);
+    } else {
+        tau_raw = acc - comp;
+    }
+    return false;
+}
+
+// The same walk over a padded grid (QMCRT pad >= WALK_UNROLL): the grid is
+// surrounded by `pad` layers of sentinel cells (value -1).  The walk needs no per-axis
+// cell counters: a batch of WALK_UNROLL cells is stepped blindly (at most
+// WALK_UNROLL cells past the box, still inside the padding), sentinels contribute
+// nothing, and the walk ends after the first batch that loaded one.  The
+// box is convex and axis-aligned, so once a step leaves it along any axis every later
+// cell of the ray is outside too.
+template <class T, bool TARGET>
+__device__ __forceinline__ bool grid_walk_padded(const MediumP<T> &G, const T p[3], const T d[3], T target_raw,
+                                                 T &tau_raw, T &t_out)
+{
+    const int cx = start_cell(p[0], G.lo[0], G.h[0], d[0]);
+    const int cy = start_cell(p[1], G.lo[1], G.h[1], d[1]);
+    const int cz = start_cell(p[2], G.lo[2], G.h[2], d[2]);
+    tau_raw = T(0);
+    t_out = T(0);
+    if (!walkable(p, d)) return false;
+    if (cx < 0 || cx >= G.n[0] || cy < 0 || cy >= G.n[1] || cz < 0 || cz >= G.n[2]) return false;
+    AxisWalk<T> X = axis_setup(p[0], d[0], cx, G.lo[0], G.h[0], G.n[0], G.stride[0]);
+    AxisWalk<T> Y = axis_setup(p[1], d[1], cy, G.lo[1], G.h[1], G.n[1], G.stride[1]);
+    AxisWalk<T> Z = axis_setup(p[2], d[2], cz, G.lo[2], G.h[2], G.n[2], G.stride[2]);
+    if (X.step == 0 && Y.step == 0 && Z.step == 0) return false;
+    int idx = (cx + G.pad) * G.stride[0] + (cy + G.pad) * G.stride[1] + (cz + G.pad) * G.stride[2];
+    const float *__restrict__ K = G.k;
+    T t = T(0), acc = TARGET ? target_raw : T(0), comp = T(0), t_last = T(0);
+    for (;;) {
+        T L[WALK_UNROLL];
+        int cell[WALK_UNROLL];
+#pragma unroll
+        for (int u = 0; u < WALK_UNROLL; ++u) {
+            cell[u] = idx;
+            const T l = Mth<T>::min_(X.s, Mth<T>::min_(Y.s, Z.s));
+            L[u] = l;
+            X.s -= l;  // exact (zero) for the axis whose face is reached
+            Y.s -= l;
+            Z.s -= l;
+            if (X.s == T(0)) {  // ties step x, then y, then z
+                idx += X.step;
+                X.s = X.dt;
+            } else if (Y.s == T(0)) {
+                idx += Y.step;
+                Y.s = Y.dt;
+            } else {
+                idx += Z.step;
+                Z.s = Z.dt;
+            }
+        }
+        T kc[WALK_UNROLL];
+#pragma unroll
+        for (int u = 0; u < WALK_UNROLL; ++u) kc[u] = (T)__ldg(K + cell[u]);
+        T kmin = kc[0];
+#pragma unroll
+        for (int u = 0; u < WALK_UNROLL; ++u) {
+            const T k = Mth<T>::max_(kc[u], T(0));  // sentinels (outside the box) add nothing
+            kmin = Mth<T>::min_(kmin, kc[u]);
+            const T dtau = L[u] * k;
+            if (TARGET) {
+                const T rem = acc - comp;
+                if (k > T(0) && dtau >= rem) {
+                    t_out = t + rem / k;
+                    tau_raw = target_raw;
+                    return true;
+                }
+                const T y = -dtau - comp;  // acc -= dtau, compensated
+                const T s = acc + y;
+                comp = (s - acc) - y;
+                acc = s;
+                t += L[u];
+                if (k > T(0) && L[u] > T(0)) t_last = t;
+            } else {
+                const T y = dtau - comp;  // acc += dtau, compensated
+                const T s = acc + y;
+                comp = (s - acc) - y;
+                acc = s;
+            }
+        }
+        if (kmin < T(0)) break;
     }
     if (TARGET) {
         t_out = t_last;
@@ -379,7 +516,8 @@ __device__ __forceinline__ T tau_to_edge(const MediumP<T> &G, const T p[3], cons
         return G.sph_k * sphere_exit(p, d, G.sph_r);
     }
     T raw, t;
-    grid_walk<T, false>(G, p, d, T(0), raw, t);
+    if (G.pad) grid_walk_padded<T, false>(G, p, d, T(0), raw, t);
+    else grid_walk<T, false>(G, p, d, T(0), raw, t);
     return raw * G.kscale;
 }
 
@@ -396,7 +534,8 @@ __device__ __forceinline__ bool march(const MediumP<T> &G, T pos[3], const T d[3
         t = hit ? tau / G.sph_k : s;
     } else {
         T raw;
-        hit = grid_walk<T, true>(G, pos, d, tau * G.inv_kscale, raw, t);
+        hit = G.pad ? grid_walk_padded<T, true>(G, pos, d, tau * G.inv_kscale, raw, t)
+                    : grid_walk<T, true>(G, pos, d, tau * G.inv_kscale, raw, t);
     }
     pos[0] += t * d[0];
     pos[1] += t * d[1];

@@ -27,7 +27,8 @@ struct MediumP {
     const float *k;
     int kind;          // QMCRT_MEDIUM_GRID / QMCRT_MEDIUM_SPHERE
     int n[3];
-    int stride[3];     // linear index step of one cell along x, y, z
+    int pad;           // sentinel layers around the grid (0: plain grid, walked with cell counters)
+    int stride[3];     // linear index step of one cell along x, y, z (of the padded array if pad > 0)
     T lo[3], hi[3], h[3];
     T kscale, inv_kscale;
     T sph_r, sph_k;    // analytic sphere: radius, kscale * extinction
@@ -73,7 +74,7 @@ struct AccumP {
 // the host inverts L: g = R (y ^ y(block start)) ^ K e, e selecting within the box.
 // Consecutive threads, hence a warp, receive points from adjacent boxes: packets that
 // start in nearly the same direction and scatter at nearly the same depth.
-constexpr int NET_MAX_M = 24;
+constexpr int NET_MAX_M = 28;
 
 struct OrderP {
     int net;            // 0 linear, 1 net order
@@ -109,6 +110,7 @@ int set_error(int code, const char *fmt, ...);
 // Launchers (return a cudaError_t from the launch).
 cudaError_t launch_generate_points(const PointsP &p, uint64_t first, uint64_t count, int format, void *out,
                                    cudaStream_t s);
+cudaError_t launch_pad_grid(const float *k, int nx, int ny, int nz, int pad, float *out, cudaStream_t s);
 cudaError_t launch_image_reduce(const void *acc, int mode, double frac_scale, size_t elems, int replicas,
                                 double scale, double *out, cudaStream_t s);
 cudaError_t launch_trace_single_f32(const TraceP<float> &p, int block, cudaStream_t s);

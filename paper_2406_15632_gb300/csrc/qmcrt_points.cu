@@ -1,5 +1,6 @@
-// qmcrt_points.cu -- point-set generation (Sec. 3.1) and the final image reduction
-// (Sec. 3.6: sums of all replicas, in units of the source luminosity).
+// qmcrt_points.cu -- point-set generation (Sec. 3.1), the final image reduction
+// (Sec. 3.6: sums of all replicas, in units of the source luminosity) and the padded
+// copy of a density grid.
 #include "qmcrt_device.cuh"
 
 namespace qmcrt {
@@ -43,6 +44,21 @@ __global__ void __launch_bounds__(256) k_image_reduce(const void *acc, int mode,
     }
 }
 
+// Copy of a grid with `pad` layers of sentinel cells (-1) on every side.
+__global__ void __launch_bounds__(256) k_pad_grid(const float *__restrict__ k, int nx, int ny, int nz, int pad,
+                                                 float *__restrict__ out)
+{
+    const int px = nx + 2 * pad, py = ny + 2 * pad, pz = nz + 2 * pad;
+    const size_t total = (size_t)px * py * pz;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(e % px) - pad;
+        const int y = (int)((e / px) % py) - pad;
+        const int z = (int)(e / ((size_t)px * py)) - pad;
+        const bool in = x >= 0 && x < nx && y >= 0 && y < ny && z >= 0 && z < nz;
+        out[e] = in ? k[((size_t)z * ny + y) * nx + x] : -1.0f;
+    }
+}
+
 static unsigned grid_for(uint64_t n)
 {
     uint64_t g = (n + 255) / 256;
@@ -55,6 +71,13 @@ cudaError_t launch_generate_points(const PointsP &p, uint64_t first, uint64_t co
 {
     if (count == 0) return cudaSuccess;
     k_generate_points<<<grid_for(count * (uint64_t)p.dims), 256, 0, s>>>(p, first, count, format, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pad_grid(const float *k, int nx, int ny, int nz, int pad, float *out, cudaStream_t s)
+{
+    const uint64_t total = (uint64_t)(nx + 2 * pad) * (ny + 2 * pad) * (nz + 2 * pad);
+    k_pad_grid<<<grid_for(total), 256, 0, s>>>(k, nx, ny, nz, pad, out);
     return cudaGetLastError();
 }
 

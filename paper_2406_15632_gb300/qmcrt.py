@@ -31,6 +31,7 @@ ACCUM = {"i64": 0, "f64": 1}
 PREC = {"f32": 0, "f64": 1}
 FORCE = {"all": 0, "first": 1}
 MAX_DIMS = 256
+MIN_PAD = 8
 
 
 class QmcrtError(RuntimeError):
@@ -46,7 +47,7 @@ class qmcrt_points_desc(C.Structure):
 
 class qmcrt_medium(C.Structure):
     _fields_ = [("struct_size", C.c_uint32), ("kind", C.c_int32), ("d_k", C.c_void_p), ("nx", C.c_int32),
-                ("ny", C.c_int32), ("nz", C.c_int32), ("reserved", C.c_int32), ("lo", C.c_double * 3),
+                ("ny", C.c_int32), ("nz", C.c_int32), ("pad", C.c_int32), ("lo", C.c_double * 3),
                 ("hi", C.c_double * 3), ("kscale", C.c_double), ("sphere_r", C.c_double), ("sphere_k", C.c_double)]
 
 
@@ -100,6 +101,7 @@ _SIGS = [
                                        _P(qmcrt_points_desc), _P(qmcrt_trace_opts), _P(qmcrt_image), C.c_void_p]),
     ("qmcrt_image_reduce", C.c_int, [_P(qmcrt_image), C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_void_p,
                                      C.c_void_p]),
+    ("qmcrt_pad_grid", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
     ("qmcrt_trace_single_noalloc", C.c_int, [_P(qmcrt_medium), _P(qmcrt_source), _P(qmcrt_dust),
                                              _P(qmcrt_observer), _P(qmcrt_points_desc), _P(qmcrt_trace_opts),
                                              C.c_int32, C.c_double, C.c_void_p, C.c_void_p]),
@@ -148,6 +150,10 @@ def qmcrt_trace_single(medium, source, dust, obs, pts, opts, image, d_log: int =
 def qmcrt_trace_multiple(medium, source, dust, obs, pts, opts, image, stream: int = 0) -> None:
     _check(load().qmcrt_trace_multiple(C.byref(medium), C.byref(source), C.byref(dust), C.byref(obs), C.byref(pts),
                                        C.byref(opts), C.byref(image), C.c_void_p(stream)))
+
+
+def qmcrt_pad_grid(d_k: int, nx: int, ny: int, nz: int, pad: int, d_padded: int, stream: int = 0) -> None:
+    _check(load().qmcrt_pad_grid(C.c_void_p(d_k), nx, ny, nz, pad, C.c_void_p(d_padded), C.c_void_p(stream)))
 
 
 def qmcrt_image_reduce(image, nx: int, ny: int, n_replicas: int, scale: float, d_out: int, stream: int = 0) -> None:
@@ -218,15 +224,23 @@ def default_frac_bits(prob: scenes.Problem, n_contributions: int) -> int:
 class Scene:
     """The descriptor structs of one problem, with its grid resident on the device."""
 
-    def __init__(self, prob: scenes.Problem, grid_device=None, device="cuda"):
+    def __init__(self, prob: scenes.Problem, grid_device=None, device="cuda", pad: int = MIN_PAD):
         torch = _torch()
         self.prob = prob
+        self.pad = pad
+        self.padded = None
         if prob.grid is not None:
             if grid_device is None:
                 grid_device = torch.as_tensor(prob.grid, dtype=torch.float32).to(device).contiguous()
             self.grid = grid_device
             nz, ny, nx = self.grid.shape
-            self.medium = _new(qmcrt_medium, kind=MEDIUM_GRID, d_k=self.grid.data_ptr(), nx=nx, ny=ny, nz=nz,
+            d_k = self.grid.data_ptr()
+            if pad:
+                self.padded = torch.empty((nz + 2 * pad, ny + 2 * pad, nx + 2 * pad), dtype=torch.float32,
+                                          device=device)
+                self.repad()
+                d_k = self.padded.data_ptr()
+            self.medium = _new(qmcrt_medium, kind=MEDIUM_GRID, d_k=d_k, nx=nx, ny=ny, nz=nz, pad=pad,
                                kscale=prob.kscale)
         else:
             self.grid = None
@@ -241,6 +255,12 @@ class Scene:
         self.dust = _new(qmcrt_dust, albedo=prob.albedo, g=prob.g, p_l=prob.p_l)
         self.obs = _new(qmcrt_observer, splat=SPLAT[prob.splat], theta=prob.theta_obs, phi=prob.phi_obs,
                         half_width=prob.half_width, nx=prob.nx, ny=prob.ny)
+
+    def repad(self, stream=None) -> None:
+        """Refresh the padded copy after the grid changed."""
+        if self.padded is not None:
+            nz, ny, nx = self.grid.shape
+            qmcrt_pad_grid(self.grid.data_ptr(), nx, ny, nz, self.pad, self.padded.data_ptr(), _stream(stream))
 
     def opts(self, precision: str = "f32", block_size: int = 0) -> qmcrt_trace_opts:
         p = self.prob
@@ -283,11 +303,12 @@ class Scene:
 
 
 def render(prob: scenes.Problem, n_packets: int, first: int = 1, *, precision: str = "f32", accum: str = "i64",
-           frac_bits: int | None = None, log: bool = False, scale: float | None = None):
+           frac_bits: int | None = None, log: bool = False, scale: float | None = None, pad: int = MIN_PAD):
     """Trace packets first..first+n_packets-1 and return the image [n_images][3][ny][nx]
-    (float64, scaled by 1/n_packets unless scale is given), and the packet log if asked."""
+    (float64, scaled by 1/n_packets unless scale is given), and the packet log if asked.
+    pad = 0 walks the plain grid with cell counters instead of the padded grid."""
     torch = _torch()
-    sc = Scene(prob)
+    sc = Scene(prob, pad=pad)
     fb = default_frac_bits(prob, n_packets) if frac_bits is None else frac_bits
     buf = sc.accum_buffer(accum)
     lg = torch.zeros((n_packets, 9), dtype=torch.float64, device="cuda") if log else None
@@ -320,6 +341,7 @@ class HostRenderer:
     def __call__(self, host_grid, first: int, count: int, host_out, stream=None) -> None:
         if self.scene.grid is not None:
             self.scene.grid.copy_(host_grid, non_blocking=True)
+            self.scene.repad(stream)
         self.buf.zero_()
         self.scene.trace(first, count, self.buf, accum=self.accum, frac_bits=self.frac_bits, precision=self.precision,
                          stream=stream)
