@@ -197,6 +197,61 @@ int qmcrt_trace_multiple(const qmcrt_medium *medium, const qmcrt_source *source,
                          const qmcrt_observer *obs, const qmcrt_points_desc *pts, const qmcrt_trace_opts *opts,
                          const qmcrt_image *image, void *stream);
 
+/* ---- batches of problems in one launch ---- */
+typedef struct qmcrt_instance {  /* device-resident table entry, 64 bytes */
+    double theta, phi;       /* direction toward this instance's observer */
+    double albedo, g, p_l;   /* dust at this instance's wavelength (as qmcrt_dust) */
+    double kscale;           /* opacity multiplier (times qmcrt_medium.kscale) */
+    uint64_t first_index;    /* first point index (>= 1); aligned to count keeps chunks full */
+    uint64_t count;          /* packet budget */
+} qmcrt_instance;
+
+typedef struct qmcrt_batch_config {
+    uint32_t struct_size;
+    int32_t chunk_log2;          /* largest work chunk, 2^chunk_log2 indices (7..28); an instance
+                                    uses chunks of min(2^chunk_log2, largest power of 2 <= budget) */
+    int32_t block_size;          /* threads per CTA: 64, 128 or 256 */
+    int32_t ctas_per_sm;         /* resident CTAs per SM (0 = as many as fit) */
+    int32_t packets_per_thread;  /* packets a thread traces per work tile (1..16) */
+    int32_t reserved;
+} qmcrt_batch_config;
+
+/* Bytes of device workspace qmcrt_trace_batch needs for n_instances instances. */
+uint64_t qmcrt_batch_workspace_bytes(int32_t n_instances);
+
+/*
+ * qmcrt_trace_batch -- single scattering (as qmcrt_trace_single, Sec. 3.2-3.6) for
+ * n_instances problems that share the medium and the source but differ in observer,
+ * dust (wavelength), opacity and packet budget, in one persistent launch: a fixed grid
+ * of CTAs pulls work tiles (instance, aligned chunk of indices, tile) from a
+ * counter in d_workspace until every budget is traced.  The work order is derived on
+ * the device from d_instances, so the call can be captured in a CUDA graph and
+ * replayed.  obs gives the image geometry (nx, ny, half_width, splat; theta and phi
+ * are taken from the instances); pts gives the point kind, dims, seed (first_index,
+ * count and total_n come from the instances: a Hammersley instance uses N = its last
+ * index); opts gives precision and tau_min.
+ * d_instances: device qmcrt_instance[n_instances] (caller-owned, unchanged).
+ * image->d_accum: device [n_instances][3][ny][nx] (n_images must be 1); contributions
+ * are added.  d_workspace: device, >= qmcrt_batch_workspace_bytes(n_instances).
+ * The instance values are not checked (they live on the device): |g| < 1, albedo and
+ * p_l in [0, 1], kscale > 0 and index ranges below 2^32 are the caller's duty.
+ * Errors: INVALID_ARG (NULL pointers, bad sizes or config, small workspace),
+ * UNSUPPORTED (a multiple-scattering option), CUDA.
+ */
+int qmcrt_trace_batch(const qmcrt_medium *medium, const qmcrt_source *source, const qmcrt_observer *obs,
+                      const qmcrt_points_desc *pts, const qmcrt_trace_opts *opts, const qmcrt_instance *d_instances,
+                      int32_t n_instances, const qmcrt_batch_config *config, void *d_workspace,
+                      uint64_t workspace_bytes, const qmcrt_image *image, void *stream);
+
+/*
+ * qmcrt_batch_reduce -- d_out[i][s][y][x] = raw[i][s][y][x] * 2^-frac_bits / count_i for
+ * every instance i (fixed-point accumulation only): the batch's images in units of
+ * the source luminosity.  d_out: device double [n_instances][3][ny][nx].
+ * Errors: INVALID_ARG, CUDA.
+ */
+int qmcrt_batch_reduce(const qmcrt_image *image, const qmcrt_instance *d_instances, int32_t n_instances, int32_t nx,
+                       int32_t ny, double *d_out, void *stream);
+
 /*
  * qmcrt_pad_grid -- prepares a grid for the faster walk (Sec. 3.4 optical-depth
  * integration, unchanged in result): writes d_padded, device float

@@ -5,6 +5,8 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <algorithm>
+#include <mutex>
 #include <utility>
 
 #include "qmcrt.h"
@@ -371,6 +373,98 @@ int qmcrt_trace_multiple(const qmcrt_medium *medium, const qmcrt_source *source,
 {
     g_last_error.clear();
     return trace_common(medium, source, dust, obs, pts, opts, image, nullptr, stream, 1);
+}
+
+uint64_t qmcrt_batch_workspace_bytes(int32_t n_instances)
+{
+    if (n_instances < 0) return 0;
+    return ((uint64_t)(n_instances + 2) * 8 + 255) & ~255ull;
+}
+
+int qmcrt_trace_batch(const qmcrt_medium *medium, const qmcrt_source *source, const qmcrt_observer *obs,
+                      const qmcrt_points_desc *pts, const qmcrt_trace_opts *opts, const qmcrt_instance *d_instances,
+                      int32_t n_instances, const qmcrt_batch_config *config, void *d_workspace,
+                      uint64_t workspace_bytes, const qmcrt_image *image, void *stream)
+{
+    g_last_error.clear();
+    CHECK_STRUCT(medium, qmcrt_medium);
+    CHECK_STRUCT(source, qmcrt_source);
+    CHECK_STRUCT(obs, qmcrt_observer);
+    CHECK_STRUCT(pts, qmcrt_points_desc);
+    CHECK_STRUCT(opts, qmcrt_trace_opts);
+    CHECK_STRUCT(config, qmcrt_batch_config);
+    CHECK_STRUCT(image, qmcrt_image);
+    if (!d_instances || !d_workspace) return fail(QMCRT_ERR_INVALID_ARG, "NULL instance table or workspace");
+    if (n_instances < 1) return fail(QMCRT_ERR_INVALID_ARG, "n_instances must be >= 1");
+    if (workspace_bytes < qmcrt_batch_workspace_bytes(n_instances))
+        return fail(QMCRT_ERR_INVALID_ARG, "workspace of %llu bytes < %llu", (unsigned long long)workspace_bytes,
+                    (unsigned long long)qmcrt_batch_workspace_bytes(n_instances));
+    if (config->chunk_log2 < 7 || config->chunk_log2 > qmcrt::NET_MAX_M)
+        return fail(QMCRT_ERR_INVALID_ARG, "chunk_log2 outside 7..%d", qmcrt::NET_MAX_M);
+    if (config->block_size != 64 && config->block_size != 128 && config->block_size != 256)
+        return fail(QMCRT_ERR_INVALID_ARG, "block_size must be 64, 128 or 256");
+    if (config->packets_per_thread < 1 || config->packets_per_thread > 16)
+        return fail(QMCRT_ERR_INVALID_ARG, "packets_per_thread outside 1..16");
+    if (config->ctas_per_sm < 0) return fail(QMCRT_ERR_INVALID_ARG, "ctas_per_sm must be >= 0");
+    if (image->n_images != 1) return fail(QMCRT_ERR_INVALID_ARG, "a batch has one image per instance");
+    // the template problem: instance values replace observer angles, dust, opacity and range
+    qmcrt_dust dust;
+    memset(&dust, 0, sizeof dust);
+    dust.struct_size = sizeof dust;
+    dust.albedo = 1.0;
+    qmcrt_points_desc p = *pts;
+    p.first_index = 1;
+    p.count = 1ull << config->chunk_log2;
+    p.total_n = p.count;
+    qmcrt_trace_opts o = *opts;
+    o.max_orders = 1;
+    o.per_order = 0;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_status(e, "device query");
+    const int occ = qmcrt::batch_occupancy(config->block_size, opts->precision);
+    const int per_sm = config->ctas_per_sm ? std::min(config->ctas_per_sm, std::max(occ, 1)) : std::max(occ, 1);
+    const int ctas = per_sm * sms;
+    cudaStream_t s = (cudaStream_t)stream;
+    auto *ws = (unsigned long long *)d_workspace;
+    static qmcrt::NetTables tabs[QMCRT_PHILOX + 1];  // per point kind, built once (read-only after)
+    static std::once_flag once[QMCRT_PHILOX + 1];
+    std::call_once(once[pts->kind], [&] {
+        for (int m = qmcrt::NET_MIN_M; m <= qmcrt::NET_MAX_M; ++m)
+            make_order(pts->kind, 0, 1ull << m, tabs[pts->kind].ord[m - qmcrt::NET_MIN_M]);
+    });
+    qmcrt::NetTables tab = tabs[pts->kind];
+    tab.m_cap = config->chunk_log2;
+    if (opts->precision == QMCRT_PREC_F64) {
+        qmcrt::TraceP<double> P;
+        int rc = fill_trace<double>(medium, source, &dust, obs, &p, &o, image, 0, P);
+        if (rc) return rc;
+        return cuda_status(qmcrt::launch_trace_batch_f64(P, tab, d_instances, n_instances, ws, config->block_size,
+                                                         ctas, config->packets_per_thread, s),
+                           "trace_batch launch");
+    }
+    qmcrt::TraceP<float> P;
+    int rc = fill_trace<float>(medium, source, &dust, obs, &p, &o, image, 0, P);
+    if (rc) return rc;
+    return cuda_status(qmcrt::launch_trace_batch_f32(P, tab, d_instances, n_instances, ws, config->block_size, ctas,
+                                                     config->packets_per_thread, s),
+                       "trace_batch launch");
+}
+
+int qmcrt_batch_reduce(const qmcrt_image *image, const qmcrt_instance *d_instances, int32_t n_instances, int32_t nx,
+                       int32_t ny, double *d_out, void *stream)
+{
+    g_last_error.clear();
+    CHECK_STRUCT(image, qmcrt_image);
+    if (!image->d_accum || !d_instances || !d_out) return fail(QMCRT_ERR_INVALID_ARG, "NULL buffer");
+    if (n_instances < 1 || nx < 1 || ny < 1) return fail(QMCRT_ERR_INVALID_ARG, "sizes must be >= 1");
+    if (image->accum != QMCRT_ACCUM_I64 || image->frac_bits < 0 || image->frac_bits > 62)
+        return fail(QMCRT_ERR_INVALID_ARG, "batch images use fixed-point accumulation with frac_bits 0..62");
+    return cuda_status(qmcrt::launch_batch_reduce((const long long *)image->d_accum, d_instances, n_instances,
+                                                  (size_t)3 * nx * ny, std::ldexp(1.0, -image->frac_bits), d_out,
+                                                  (cudaStream_t)stream),
+                       "batch_reduce launch");
 }
 
 int qmcrt_pad_grid(const float *d_k, int32_t nx, int32_t ny, int32_t nz, int32_t pad, float *d_padded, void *stream)

@@ -8,6 +8,8 @@
 
 #include <cuda_runtime.h>
 
+#include "qmcrt.h"
+
 namespace qmcrt {
 
 // Point set of Sec. 3.1.  Indices are global point indices (>= 1).
@@ -87,6 +89,13 @@ struct OrderP {
     uint32_t k[4];           // kernel basis of L
 };
 
+// Net-order tables for every block size a batch may use (m = NET_MIN_M .. NET_MAX_M).
+constexpr int NET_MIN_M = 7;
+struct NetTables {
+    OrderP ord[NET_MAX_M - NET_MIN_M + 1];
+    int m_cap;           // largest chunk a batch uses: instance i takes min(floor(log2 count_i), m_cap)
+};
+
 template <class T>
 struct TraceP {
     OrderP ord;
@@ -108,6 +117,15 @@ struct TraceP {
 int set_error(int code, const char *fmt, ...);
 
 // Launchers (return a cudaError_t from the launch).
+cudaError_t launch_trace_batch_f32(const TraceP<float> &p, const NetTables &tab, const qmcrt_instance *inst,
+                                   int n_inst, unsigned long long *ws, int block, int ctas, int per_thread,
+                                   cudaStream_t s);
+cudaError_t launch_trace_batch_f64(const TraceP<double> &p, const NetTables &tab, const qmcrt_instance *inst,
+                                   int n_inst, unsigned long long *ws, int block, int ctas, int per_thread,
+                                   cudaStream_t s);
+cudaError_t launch_batch_reduce(const long long *acc, const qmcrt_instance *inst, int n_inst, size_t per_inst,
+                                double frac_scale, double *out, cudaStream_t s);
+int batch_occupancy(int block, int precision);
 cudaError_t launch_generate_points(const PointsP &p, uint64_t first, uint64_t count, int format, void *out,
                                    cudaStream_t s);
 cudaError_t launch_pad_grid(const float *k, int nx, int ny, int nz, int pad, float *out, cudaStream_t s);

@@ -77,6 +77,16 @@ class qmcrt_trace_opts(C.Structure):
                 ("rr_survival", C.c_double), ("per_order", C.c_int32), ("block_size", C.c_int32)]
 
 
+class qmcrt_instance(C.Structure):
+    _fields_ = [("theta", C.c_double), ("phi", C.c_double), ("albedo", C.c_double), ("g", C.c_double),
+                ("p_l", C.c_double), ("kscale", C.c_double), ("first_index", C.c_uint64), ("count", C.c_uint64)]
+
+
+class qmcrt_batch_config(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("chunk_log2", C.c_int32), ("block_size", C.c_int32),
+                ("ctas_per_sm", C.c_int32), ("packets_per_thread", C.c_int32), ("reserved", C.c_int32)]
+
+
 def _new(cls, **kw):
     s = cls()
     s.struct_size = C.sizeof(cls)
@@ -100,6 +110,12 @@ _SIGS = [
     ("qmcrt_trace_multiple", C.c_int, [_P(qmcrt_medium), _P(qmcrt_source), _P(qmcrt_dust), _P(qmcrt_observer),
                                        _P(qmcrt_points_desc), _P(qmcrt_trace_opts), _P(qmcrt_image), C.c_void_p]),
     ("qmcrt_image_reduce", C.c_int, [_P(qmcrt_image), C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_void_p,
+                                     C.c_void_p]),
+    ("qmcrt_batch_workspace_bytes", C.c_uint64, [C.c_int32]),
+    ("qmcrt_trace_batch", C.c_int, [_P(qmcrt_medium), _P(qmcrt_source), _P(qmcrt_observer), _P(qmcrt_points_desc),
+                                    _P(qmcrt_trace_opts), C.c_void_p, C.c_int32, _P(qmcrt_batch_config), C.c_void_p,
+                                    C.c_uint64, _P(qmcrt_image), C.c_void_p]),
+    ("qmcrt_batch_reduce", C.c_int, [_P(qmcrt_image), C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p,
                                      C.c_void_p]),
     ("qmcrt_pad_grid", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
     ("qmcrt_trace_single_noalloc", C.c_int, [_P(qmcrt_medium), _P(qmcrt_source), _P(qmcrt_dust),
@@ -150,6 +166,23 @@ def qmcrt_trace_single(medium, source, dust, obs, pts, opts, image, d_log: int =
 def qmcrt_trace_multiple(medium, source, dust, obs, pts, opts, image, stream: int = 0) -> None:
     _check(load().qmcrt_trace_multiple(C.byref(medium), C.byref(source), C.byref(dust), C.byref(obs), C.byref(pts),
                                        C.byref(opts), C.byref(image), C.c_void_p(stream)))
+
+
+def qmcrt_batch_workspace_bytes(n_instances: int) -> int:
+    return int(load().qmcrt_batch_workspace_bytes(n_instances))
+
+
+def qmcrt_trace_batch(medium, source, obs, pts, opts, d_instances: int, n_instances: int, config, d_workspace: int,
+                      workspace_bytes: int, image, stream: int = 0) -> None:
+    _check(load().qmcrt_trace_batch(C.byref(medium), C.byref(source), C.byref(obs), C.byref(pts), C.byref(opts),
+                                    C.c_void_p(d_instances), n_instances, C.byref(config), C.c_void_p(d_workspace),
+                                    workspace_bytes, C.byref(image), C.c_void_p(stream)))
+
+
+def qmcrt_batch_reduce(image, d_instances: int, n_instances: int, nx: int, ny: int, d_out: int,
+                       stream: int = 0) -> None:
+    _check(load().qmcrt_batch_reduce(C.byref(image), C.c_void_p(d_instances), n_instances, nx, ny, C.c_void_p(d_out),
+                                     C.c_void_p(stream)))
 
 
 def qmcrt_pad_grid(d_k: int, nx: int, ny: int, nz: int, pad: int, d_padded: int, stream: int = 0) -> None:
@@ -348,3 +381,94 @@ class HostRenderer:
         self.scene.reduce(self.buf, 1.0 / count, accum=self.accum, frac_bits=self.frac_bits, out=self.out,
                           stream=stream)
         host_out.copy_(self.out, non_blocking=True)
+
+
+class Batch:
+    """Many instances (observer, wavelength, budget) of one problem traced in one
+    persistent launch: the instance table, workspace and images live on the device;
+    run() enqueues plan + trace + reduce on the current stream, and capture() records
+    that sequence in a CUDA graph that replay() launches again."""
+
+    def __init__(self, prob: scenes.Problem, instances, *, precision: str = "f32", chunk_log2: int = 16,
+                 block_size: int = 256, ctas_per_sm: int = 0, packets_per_thread: int = 4,
+                 frac_bits: int | None = None, scene: "Scene | None" = None):
+        torch = _torch()
+        self.prob = prob
+        self.scene = scene or Scene(prob)
+        self.precision = precision
+        self.n = len(instances)
+        table = (qmcrt_instance * self.n)()
+        for t, I in zip(table, instances):
+            t.theta, t.phi, t.albedo, t.g = I.theta_obs, prob.phi_obs, I.albedo, I.g
+            t.p_l, t.kscale, t.first_index, t.count = prob.p_l, I.kscale, I.first_index, I.n_packets
+        raw = torch.frombuffer(bytearray(bytes(table)), dtype=torch.uint8)
+        self.d_inst = raw.to("cuda")
+        self.counts = [I.n_packets for I in instances]
+        self.instances = list(instances)
+        self.ws_bytes = qmcrt_batch_workspace_bytes(self.n)
+        self.ws = torch.zeros(self.ws_bytes // 8, dtype=torch.int64, device="cuda")
+        self.accum = torch.zeros((self.n, 3, prob.ny, prob.nx), dtype=torch.int64, device="cuda")
+        self.out = torch.zeros((self.n, 3, prob.ny, prob.nx), dtype=torch.float64, device="cuda")
+        bound_prob = prob.replace(g=max(abs(I.g) for I in instances))
+        self.frac_bits = default_frac_bits(bound_prob, max(self.counts)) if frac_bits is None else frac_bits
+        self.graph = None
+        self.set_config(chunk_log2, block_size, ctas_per_sm, packets_per_thread)
+
+    def set_config(self, chunk_log2: int, block_size: int, ctas_per_sm: int, packets_per_thread: int) -> None:
+        self.config = _new(qmcrt_batch_config, chunk_log2=chunk_log2, block_size=block_size, ctas_per_sm=ctas_per_sm,
+                           packets_per_thread=packets_per_thread)
+        self.graph = None
+
+    def packets(self) -> int:
+        return sum(self.counts)
+
+    def run(self, stream=None) -> None:
+        sc = self.scene
+        st = _stream(stream)
+        self.accum.zero_()
+        pts = points_desc(self.prob.generator, self.prob.dims, 1, 1, "f64", self.prob.seed, 0)
+        img = _new(qmcrt_image, accum=ACCUM["i64"], d_accum=self.accum.data_ptr(), n_images=1,
+                   frac_bits=self.frac_bits)
+        qmcrt_trace_batch(sc.medium, sc.source, sc.obs, pts, sc.opts(self.precision), self.d_inst.data_ptr(), self.n,
+                          self.config, self.ws.data_ptr(), self.ws_bytes, img, st)
+        qmcrt_batch_reduce(img, self.d_inst.data_ptr(), self.n, self.prob.nx, self.prob.ny, self.out.data_ptr(), st)
+
+    def run_each(self, stream=None) -> None:
+        """The same images by one regular qmcrt_trace_single launch per instance (the
+        un-batched way), for comparison."""
+        sc = self.scene
+        st = _stream(stream)
+        self.accum.zero_()
+        opts = sc.opts(self.precision)
+        for k, (I, n) in enumerate(zip(self.instances, self.counts)):
+            if n == 0:
+                continue
+            med = qmcrt_medium.from_buffer_copy(sc.medium)
+            med.kscale = sc.medium.kscale * I.kscale
+            dust = _new(qmcrt_dust, albedo=I.albedo, g=I.g, p_l=self.prob.p_l)
+            obs = qmcrt_observer.from_buffer_copy(sc.obs)
+            obs.theta = I.theta_obs
+            pts = points_desc(self.prob.generator, self.prob.dims, I.first_index, n, "f64", self.prob.seed,
+                              I.first_index + n - 1)
+            img = _new(qmcrt_image, accum=ACCUM["i64"], d_accum=self.accum[k].data_ptr(), n_images=1,
+                       frac_bits=self.frac_bits)
+            qmcrt_trace_single(med, sc.source, dust, obs, pts, opts, img, 0, st)
+        img = _new(qmcrt_image, accum=ACCUM["i64"], d_accum=self.accum.data_ptr(), n_images=1,
+                   frac_bits=self.frac_bits)
+        qmcrt_batch_reduce(img, self.d_inst.data_ptr(), self.n, self.prob.nx, self.prob.ny, self.out.data_ptr(), st)
+
+    def capture(self) -> None:
+        torch = _torch()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):  # warm-up outside the capture
+            self.run()
+        torch.cuda.current_stream().wait_stream(s)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.run()
+
+    def replay(self) -> None:
+        if self.graph is None:
+            self.capture()
+        self.graph.replay()

@@ -200,8 +200,10 @@ def batched_instances(n_incl: int = 32, n_wave: int = 8, seed: int = 4, min_log2
         th = math.radians(90.0 * j / max(1, n_incl - 1))
         for l in range(n_wave):
             t = l / max(1, n_wave - 1)
+            n = int(2 ** exps[j * n_wave + l])
+            # points n .. 2n-1: an aligned block of the sequence (a digitally shifted net)
             out.append(Instance(theta_obs=th, albedo=0.4 + 0.5 * t, g=0.2 + 0.5 * t,
-                                kscale=0.5 * 8.0 ** t, n_packets=int(2 ** exps[j * n_wave + l])))
+                                kscale=0.5 * 8.0 ** t, n_packets=n, first_index=n))
     return out
 
 

@@ -39,7 +39,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 STRUCTS = ["qmcrt_points_desc", "qmcrt_medium", "qmcrt_source", "qmcrt_dust", "qmcrt_observer", "qmcrt_image",
-           "qmcrt_trace_opts"]
+           "qmcrt_trace_opts", "qmcrt_instance", "qmcrt_batch_config"]
 
 
 def test_struct_layout_matches_the_c_compiler(tmp_path):
@@ -159,3 +159,25 @@ def test_default_frac_bits_never_overflows():
         fb = Q.default_frac_bits(prob, n)
         assert 0 <= fb <= 62
         assert n * Q.contribution_bound(prob) * prob.max_orders * 2.0 ** fb < 2.0 ** 63
+
+
+def test_batch_validation(lib):
+    d = _descs()
+    pts = Q.points_desc("sobol", 5, 1, 1)
+    cfg = Q._new(Q.qmcrt_batch_config, chunk_log2=16, block_size=256, ctas_per_sm=0, packets_per_thread=4)
+    img = Q._new(Q.qmcrt_image, accum=0, d_accum=0x1000, n_images=1, frac_bits=40)
+    ws = Q.qmcrt_batch_workspace_bytes(8)
+    assert ws >= 8 * 10 and ws % 256 == 0
+    args = [d["medium"], d["source"], d["obs"], pts, d["opts"], 0x3000, 8, cfg, 0x4000, ws, img, 0]
+    for i, bad in ((5, 0), (6, 0), (8, 0), (9, ws - 8)):
+        a = list(args)
+        a[i] = bad
+        _expect(Q.ERR_INVALID_ARG, Q.qmcrt_trace_batch, *a)
+    for field, v in (("chunk_log2", 3), ("block_size", 96), ("packets_per_thread", 0), ("ctas_per_sm", -1)):
+        c = Q._new(Q.qmcrt_batch_config, chunk_log2=16, block_size=256, ctas_per_sm=0, packets_per_thread=4)
+        setattr(c, field, v)
+        a = list(args)
+        a[7] = c
+        _expect(Q.ERR_INVALID_ARG, Q.qmcrt_trace_batch, *a)
+    img2 = Q._new(Q.qmcrt_image, accum=1, d_accum=0x1000, n_images=1, frac_bits=40)
+    _expect(Q.ERR_INVALID_ARG, Q.qmcrt_batch_reduce, img2, 0x3000, 8, 8, 8, 0x5000)
