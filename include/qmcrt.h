@@ -252,6 +252,31 @@ int qmcrt_trace_batch(const qmcrt_medium *medium, const qmcrt_source *source, co
 int qmcrt_batch_reduce(const qmcrt_image *image, const qmcrt_instance *d_instances, int32_t n_instances, int32_t nx,
                        int32_t ny, double *d_out, void *stream);
 
+/* ---- tensor-core GEMM (building block of the learned proposal) ---- */
+typedef struct qmcrt_gemm_epilogue {
+    uint32_t struct_size;
+    int32_t relu;            /* max(0, .) after the bias */
+    const float *d_bias;     /* [N] or NULL */
+    const void *d_mask;      /* bf16 [M][N] or NULL: zero where mask <= 0 (ReLU backward) */
+    float *d_out_f32;        /* [M][N] or NULL */
+    void *d_out_bf16;        /* bf16 [M][N] or NULL */
+    void *d_out_bf16_t;      /* bf16 [N][ldt] or NULL: the transpose of the result */
+    int32_t ldt;             /* row length of d_out_bf16_t, >= M */
+    int32_t k_splits;        /* > 1: split K over CTAs and add into d_out_f32 atomically (no bias) */
+    int32_t *d_error;        /* set to 1 if a tensor-core wait gives up (NULL: not reported) */
+} qmcrt_gemm_epilogue;
+
+/*
+ * qmcrt_gemm_bf16 -- D[M][N] = A[M][K] . B[N][K]^T on the tensor cores (BF16 inputs, FP32
+ * accumulation), then the epilogue (bias, ReLU, ReLU mask, FP32 / BF16 / transposed
+ * BF16 outputs).  A, B: device bf16, row-major, K contiguous, 16-byte aligned.  The
+ * paper has no counterpart; it is the building block of the learned warp's network.
+ * Errors: INVALID_ARG (NULL pointers, M < 1, N not 32/64/128, K not a positive multiple
+ * of 32, ldt < M, bias with k_splits > 1), CUDA.
+ */
+int qmcrt_gemm_bf16(const void *d_A, const void *d_B, int32_t M, int32_t N, int32_t K,
+                    const qmcrt_gemm_epilogue *epilogue, void *stream);
+
 /*
  * qmcrt_pad_grid -- prepares a grid for the faster walk (Sec. 3.4 optical-depth
  * integration, unchanged in result): writes d_padded, device float

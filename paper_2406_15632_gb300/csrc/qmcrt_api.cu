@@ -10,6 +10,7 @@
 #include <utility>
 
 #include "qmcrt.h"
+#include "qmcrt_gemm.cuh"
 #include "qmcrt_internal.h"
 #include "qmcrt_tables.h"
 
@@ -465,6 +466,38 @@ int qmcrt_batch_reduce(const qmcrt_image *image, const qmcrt_instance *d_instanc
                                                   (size_t)3 * nx * ny, std::ldexp(1.0, -image->frac_bits), d_out,
                                                   (cudaStream_t)stream),
                        "batch_reduce launch");
+}
+
+int qmcrt_gemm_bf16(const void *d_A, const void *d_B, int32_t M, int32_t N, int32_t K,
+                    const qmcrt_gemm_epilogue *epilogue, void *stream)
+{
+    g_last_error.clear();
+    CHECK_STRUCT(epilogue, qmcrt_gemm_epilogue);
+    if (!d_A || !d_B) return fail(QMCRT_ERR_INVALID_ARG, "NULL operand");
+    if (M < 1 || (N != 32 && N != 64 && N != 128) || K < 32 || K % 32)
+        return fail(QMCRT_ERR_INVALID_ARG, "shape M=%d N=%d K=%d: need M >= 1, N in {32, 64, 128}, K a multiple of 32",
+                    M, N, K);
+    if ((reinterpret_cast<uintptr_t>(d_A) | reinterpret_cast<uintptr_t>(d_B)) & 15)
+        return fail(QMCRT_ERR_INVALID_ARG, "operands must be 16-byte aligned");
+    const int splits = epilogue->k_splits > 1 ? epilogue->k_splits : 1;
+    if (splits > 1 && (epilogue->d_bias || epilogue->relu || epilogue->d_mask || epilogue->d_out_bf16 ||
+                       epilogue->d_out_bf16_t || !epilogue->d_out_f32))
+        return fail(QMCRT_ERR_INVALID_ARG, "a K split only adds into d_out_f32 (no bias, ReLU, mask or BF16 output)");
+    if (epilogue->d_out_bf16_t && epilogue->ldt < M) return fail(QMCRT_ERR_INVALID_ARG, "ldt < M");
+    qmcrt::GemmEpi ep;
+    ep.bias = epilogue->d_bias;
+    ep.relu = epilogue->relu;
+    ep.mask = static_cast<const __nv_bfloat16 *>(epilogue->d_mask);
+    ep.out_f32 = epilogue->d_out_f32;
+    ep.out_bf16 = static_cast<__nv_bfloat16 *>(epilogue->d_out_bf16);
+    ep.out_bf16_t = static_cast<__nv_bfloat16 *>(epilogue->d_out_bf16_t);
+    ep.ldt = epilogue->ldt;
+    ep.atomic_f32 = splits > 1;
+    ep.error = epilogue->d_error;
+    return cuda_status(qmcrt::launch_gemm_bf16(static_cast<const __nv_bfloat16 *>(d_A),
+                                               static_cast<const __nv_bfloat16 *>(d_B), M, N, K, splits, ep,
+                                               (cudaStream_t)stream),
+                       "gemm launch");
 }
 
 int qmcrt_pad_grid(const float *d_k, int32_t nx, int32_t ny, int32_t nz, int32_t pad, float *d_padded, void *stream)

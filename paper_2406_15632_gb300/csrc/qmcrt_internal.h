@@ -6,6 +6,7 @@
 #include <cstddef>
 #include <cstdint>
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "qmcrt.h"
@@ -112,6 +113,10 @@ struct TraceP {
     int max_orders, force_all, per_order;
     T rr_threshold, rr_survival, inv_rr_survival;
 };
+
+struct GemmEpi;
+cudaError_t launch_gemm_bf16(const __nv_bfloat16 *A, const __nv_bfloat16 *B, int M, int N, int K, int splits,
+                             const GemmEpi &ep, cudaStream_t s);
 
 // Records a message for qmcrt_last_error() on the calling thread; returns code.
 int set_error(int code, const char *fmt, ...);

@@ -87,6 +87,12 @@ class qmcrt_batch_config(C.Structure):
                 ("ctas_per_sm", C.c_int32), ("packets_per_thread", C.c_int32), ("reserved", C.c_int32)]
 
 
+class qmcrt_gemm_epilogue(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("relu", C.c_int32), ("d_bias", C.c_void_p), ("d_mask", C.c_void_p),
+                ("d_out_f32", C.c_void_p), ("d_out_bf16", C.c_void_p), ("d_out_bf16_t", C.c_void_p),
+                ("ldt", C.c_int32), ("k_splits", C.c_int32), ("d_error", C.c_void_p)]
+
+
 def _new(cls, **kw):
     s = cls()
     s.struct_size = C.sizeof(cls)
@@ -117,6 +123,8 @@ _SIGS = [
                                     C.c_uint64, _P(qmcrt_image), C.c_void_p]),
     ("qmcrt_batch_reduce", C.c_int, [_P(qmcrt_image), C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p,
                                      C.c_void_p]),
+    ("qmcrt_gemm_bf16", C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32,
+                                  _P(qmcrt_gemm_epilogue), C.c_void_p]),
     ("qmcrt_pad_grid", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
     ("qmcrt_trace_single_noalloc", C.c_int, [_P(qmcrt_medium), _P(qmcrt_source), _P(qmcrt_dust),
                                              _P(qmcrt_observer), _P(qmcrt_points_desc), _P(qmcrt_trace_opts),
@@ -183,6 +191,22 @@ def qmcrt_batch_reduce(image, d_instances: int, n_instances: int, nx: int, ny: i
                        stream: int = 0) -> None:
     _check(load().qmcrt_batch_reduce(C.byref(image), C.c_void_p(d_instances), n_instances, nx, ny, C.c_void_p(d_out),
                                      C.c_void_p(stream)))
+
+
+def qmcrt_gemm_bf16(d_A: int, d_B: int, M: int, N: int, K: int, epilogue, stream: int = 0) -> None:
+    _check(load().qmcrt_gemm_bf16(C.c_void_p(d_A), C.c_void_p(d_B), M, N, K, C.byref(epilogue), C.c_void_p(stream)))
+
+
+def gemm(A, B, *, bias=None, relu=False, mask=None, out_f32=None, out_bf16=None, out_bf16_t=None, k_splits=1,
+         error=None, stream=None):
+    """Device tensors: A [M][K] and B [N][K] bf16 -> epilogue outputs (see qmcrt_gemm_bf16)."""
+    M, K = A.shape
+    N = B.shape[0]
+    ptr = lambda t: t.data_ptr() if t is not None else None
+    ep = _new(qmcrt_gemm_epilogue, relu=1 if relu else 0, d_bias=ptr(bias), d_mask=ptr(mask), d_out_f32=ptr(out_f32),
+              d_out_bf16=ptr(out_bf16), d_out_bf16_t=ptr(out_bf16_t),
+              ldt=out_bf16_t.shape[1] if out_bf16_t is not None else 0, k_splits=k_splits, d_error=ptr(error))
+    qmcrt_gemm_bf16(A.data_ptr(), B.data_ptr(), M, N, K, ep, _stream(stream))
 
 
 def qmcrt_pad_grid(d_k: int, nx: int, ny: int, nz: int, pad: int, d_padded: int, stream: int = 0) -> None:

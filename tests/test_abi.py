@@ -39,7 +39,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 STRUCTS = ["qmcrt_points_desc", "qmcrt_medium", "qmcrt_source", "qmcrt_dust", "qmcrt_observer", "qmcrt_image",
-           "qmcrt_trace_opts", "qmcrt_instance", "qmcrt_batch_config"]
+           "qmcrt_trace_opts", "qmcrt_instance", "qmcrt_batch_config", "qmcrt_gemm_epilogue"]
 
 
 def test_struct_layout_matches_the_c_compiler(tmp_path):
