@@ -277,6 +277,68 @@ typedef struct qmcrt_gemm_epilogue {
 int qmcrt_gemm_bf16(const void *d_A, const void *d_B, int32_t M, int32_t N, int32_t K,
                     const qmcrt_gemm_epilogue *epilogue, void *stream);
 
+/* ---- learned proposal: a trained warp of the first-scattering coordinates ----
+ * The paper has no counterpart.  x = T(u) on the unit cube, autoregressive and
+ * piecewise linear with QMCRT_WARP_BINS bins per coordinate (after Mueller et al.,
+ * "Neural Importance Sampling", 2019): x0 follows the learned pdf softmax(theta0);
+ * x1 the pdf given by MLP0(one-blob(x0)); x2 the pdf given by MLP1(one-blob(x0),
+ * one-blob(x1)).  Each MLP has 4 layers of width 128 with ReLU (input 128 features:
+ * 32 one-blob bins per conditioning coordinate, zero padded; output 32 logits).
+ * Parameter vector (FP32, QMCRT_WARP_PARAMS): theta0[32], then for m = 0, 1 and layer
+ * l = 0..3 the weight W[m][l] (out x in row-major: 128x128, 128x128, 128x128, 32x128)
+ * followed by its bias b[m][l] (out).  The bf16 blobs hold the 8 weight matrices in the
+ * same order (QMCRT_WARP_BF16_WEIGHTS values), as is and transposed. */
+#define QMCRT_WARP_BINS 32
+#define QMCRT_WARP_WIDTH 128
+#define QMCRT_WARP_PARAMS 107360
+#define QMCRT_WARP_BF16_WEIGHTS 106496
+
+typedef struct qmcrt_warp {
+    uint32_t struct_size;
+    int32_t reserved;
+    float *d_params;     /* device FP32 [QMCRT_WARP_PARAMS] */
+    void *d_weights;     /* device bf16 [QMCRT_WARP_BF16_WEIGHTS] (refreshed by qmcrt_warp_sync) */
+    void *d_weights_t;   /* device bf16 [QMCRT_WARP_BF16_WEIGHTS], the transposes */
+    int32_t *d_error;    /* device int or NULL: set to 1 if a tensor-core wait gives up */
+} qmcrt_warp;
+
+typedef struct qmcrt_adam {
+    uint32_t struct_size;
+    int32_t step;        /* 1, 2, ... (bias correction) */
+    double lr, beta1, beta2, eps;
+} qmcrt_adam;
+
+/* Device workspace bytes for the warp calls processing up to `rows` samples per pass. */
+uint64_t qmcrt_warp_workspace_bytes(uint64_t rows);
+
+/* Refresh the bf16 weight copies (as is and transposed) from the FP32 parameters. */
+int qmcrt_warp_sync(const qmcrt_warp *warp, void *stream);
+
+/*
+ * qmcrt_warp_forward -- d_x[n][3] = T(d_u[n][3]) and d_logj[n] = log |det dx/du| =
+ * -log q(x), for points u in [0,1]^3 (FP32, row-major).  The MLPs run on the tensor
+ * cores (bf16 weights and activations, FP32 accumulation), in passes of as many rows as
+ * the workspace holds.  Errors: INVALID_ARG (NULL pointers, workspace below one pass of
+ * 128 rows), CUDA.
+ */
+int qmcrt_warp_forward(const qmcrt_warp *warp, const float *d_u, float *d_x, float *d_logj, uint64_t n,
+                       void *d_workspace, uint64_t workspace_bytes, void *stream);
+
+/*
+ * qmcrt_warp_grad -- gradient of the cross-entropy loss -sum_j w_j log q(x_j) / sum_j w_j
+ * over logged samples (d_x[n][3], weights d_w[n] >= 0: a packet's contribution divided
+ * by the density it was drawn from), ADDED into d_grad[QMCRT_WARP_PARAMS]; the loss is
+ * added into *d_loss.  Forward and backward passes on the tensor cores.
+ * Errors: as qmcrt_warp_forward.
+ */
+int qmcrt_warp_grad(const qmcrt_warp *warp, const float *d_x, const float *d_w, uint64_t n, float *d_grad,
+                    float *d_loss, void *d_workspace, uint64_t workspace_bytes, void *stream);
+
+/* One Adam step on warp->d_params from d_grad (moments d_m, d_v, FP32
+ * [QMCRT_WARP_PARAMS]), then qmcrt_warp_sync.  Errors: INVALID_ARG, CUDA. */
+int qmcrt_warp_adam(const qmcrt_warp *warp, const float *d_grad, float *d_m, float *d_v, const qmcrt_adam *opt,
+                    void *stream);
+
 /*
  * qmcrt_pad_grid -- prepares a grid for the faster walk (Sec. 3.4 optical-depth
  * integration, unchanged in result): writes d_padded, device float

@@ -1,0 +1,409 @@
+// qmcrt_flow.cu -- the learned proposal: a piecewise-linear autoregressive warp of the
+// first-scattering coordinates with two 4-layer MLP conditionals, its cross-entropy
+// gradient and Adam.  Dense layers run on the tensor cores (qmcrt_gemm.cuh); the
+// kernels here are the element-wise parts.  Every GEMM operand is produced by the
+// previous step already in the K-major form the tensor cores read (activations and
+// backward signals are written both as is and transposed), so no transposed
+// descriptor is needed:
+//   forward   H[l+1] = relu(H[l] . W[l]^T + b[l])         A = H[l],     B = W[l]
+//   backward  dH[l]  = (dP[l] . W[l]) * (H[l] > 0)        A = dP[l],    B = W[l]^T
+//             dW[l]  = dP[l]^T . H[l]                      A = dP[l]^T, B = H[l]^T (K = rows)
+#include <cmath>
+#include <cstring>
+
+#include "qmcrt.h"
+#include "qmcrt_gemm.cuh"
+#include "qmcrt_internal.h"
+
+namespace qmcrt {
+namespace {
+
+constexpr int KB = QMCRT_WARP_BINS;
+constexpr int WD = QMCRT_WARP_WIDTH;
+constexpr int BLOB = 32;
+constexpr int ROW_BYTES = 3328;  // workspace bytes per row (see carve)
+
+__host__ __device__ constexpr int out_dim(int l) { return l == 3 ? KB : WD; }
+__host__ __device__ constexpr int mlp_params() { return 3 * (WD * WD + WD) + (KB * WD + KB); }
+__host__ __device__ inline int param_w(int m, int l)
+{
+    int o = KB + m * mlp_params();
+    for (int j = 0; j < l; ++j) o += out_dim(j) * WD + out_dim(j);
+    return o;
+}
+__host__ __device__ inline int param_b(int m, int l) { return param_w(m, l) + out_dim(l) * WD; }
+__host__ __device__ inline int bf_w(int m, int l)
+{
+    int o = m * (3 * WD * WD + KB * WD);
+    for (int j = 0; j < l; ++j) o += out_dim(j) * WD;
+    return o;
+}
+static_assert(KB + 2 * mlp_params() == QMCRT_WARP_PARAMS, "parameter count");
+static_assert(2 * (3 * WD * WD + KB * WD) == QMCRT_WARP_BF16_WEIGHTS, "weight count");
+
+struct Work {
+    __nv_bfloat16 *F, *Ft, *H[3], *Ht[3], *dL, *dLt, *dP[2], *dPt[2];
+    float *L;
+    double *wsum;
+    int rows;
+};
+
+uint64_t round128(uint64_t r) { return (r + 127) & ~127ull; }
+
+Work carve(void *ws, int rows)
+{
+    Work w;
+    char *p = (char *)ws;
+    auto take = [&](size_t bytes) {
+        char *q = p;
+        p += (bytes + 255) & ~(size_t)255;
+        return q;
+    };
+    w.rows = rows;
+    w.wsum = (double *)take(256);
+    w.F = (__nv_bfloat16 *)take((size_t)rows * WD * 2);
+    w.Ft = (__nv_bfloat16 *)take((size_t)rows * WD * 2);
+    for (int i = 0; i < 3; ++i) {
+        w.H[i] = (__nv_bfloat16 *)take((size_t)rows * WD * 2);
+        w.Ht[i] = (__nv_bfloat16 *)take((size_t)rows * WD * 2);
+    }
+    w.L = (float *)take((size_t)rows * KB * 4);
+    w.dL = (__nv_bfloat16 *)take((size_t)rows * KB * 2);
+    w.dLt = (__nv_bfloat16 *)take((size_t)rows * KB * 2);
+    for (int i = 0; i < 2; ++i) {
+        w.dP[i] = (__nv_bfloat16 *)take((size_t)rows * WD * 2);
+        w.dPt[i] = (__nv_bfloat16 *)take((size_t)rows * WD * 2);
+    }
+    return w;
+}
+
+uint64_t bytes_for(uint64_t rows) { return (uint64_t)ROW_BYTES * rows + 8192; }
+
+int rows_for(uint64_t ws_bytes)
+{
+    if (ws_bytes < bytes_for(128)) return 0;
+    uint64_t r = (ws_bytes - 8192) / ROW_BYTES;
+    r &= ~127ull;
+    return (int)std::min<uint64_t>(r, 1u << 22);
+}
+
+__device__ __forceinline__ float blob(float v, int k) { const float d = (v - (k + 0.5f) / BLOB) * BLOB; return __expf(-0.5f * d * d); }
+
+// Input features of MLP m for rows [0, rows): one-blob(x0) [, one-blob(x1)], zero padded;
+// rows >= n use x = 0.5 (their loss weight is zero).
+__global__ void k_features(const float *__restrict__ x, int n, int rows, int m, __nv_bfloat16 *__restrict__ F,
+                           __nv_bfloat16 *__restrict__ Ft)
+{
+    const long long total = (long long)rows * WD;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(e / WD), f = (int)(e % WD);
+        float v = 0.0f;
+        if (f < BLOB) v = blob(j < n ? x[3ll * j] : 0.5f, f);
+        else if (m == 1 && f < 2 * BLOB) v = blob(j < n ? x[3ll * j + 1] : 0.5f, f - BLOB);
+        const __nv_bfloat16 b = __float2bfloat16_rn(v);
+        F[e] = b;
+        if (Ft) Ft[(long long)f * rows + j] = b;
+    }
+}
+
+__device__ __forceinline__ void softmax32(const float *z, float *q)
+{
+    float mx = z[0];
+    for (int k = 1; k < KB; ++k) mx = fmaxf(mx, z[k]);
+    float s = 0.0f;
+    for (int k = 0; k < KB; ++k) {
+        q[k] = expf(z[k] - mx);
+        s += q[k];
+    }
+    const float inv = 1.0f / s;
+    for (int k = 0; k < KB; ++k) q[k] *= inv;
+}
+
+// Sampling step of coordinate `layer`: x_l = F^-1(u_l) for the pdf 32 Q[b] on bin b;
+// log |dx/du| accumulates -log(32 Q[b]).
+__global__ void k_sample(int layer, const float *__restrict__ theta0, const float *__restrict__ L,
+                         const float *__restrict__ u, float *__restrict__ x, float *__restrict__ logj, int n)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    float z[KB], q[KB];
+    const float *src = layer == 0 ? theta0 : L + (long long)j * KB;
+    for (int k = 0; k < KB; ++k) z[k] = src[k];
+    softmax32(z, q);
+    const float uu = u[3ll * j + layer];
+    float c = 0.0f;
+    int b = KB - 1;
+    for (int k = 0; k < KB - 1; ++k) {
+        if (uu < c + q[k]) { b = k; break; }
+        c += q[k];
+    }
+    const float xv = fminf(fmaxf((b + (uu - c) / q[b]) / KB, 0.0f), 1.0f);
+    x[3ll * j + layer] = xv;
+    const float lq = logf(KB * q[b]);
+    logj[j] = layer == 0 ? -lq : logj[j] - lq;
+}
+
+__global__ void k_wsum(const float *__restrict__ w, int n, double *out)
+{
+    double s = 0.0;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) s += w[j];
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+
+// Loss and d loss / d logits of coordinate `layer` (0: theta0; 1, 2: MLP0, MLP1 logits
+// in L) for rows [0, rows); rows >= n have weight zero.
+__global__ void k_loss_grad(int layer, const float *__restrict__ theta0, const float *__restrict__ L,
+                            const float *__restrict__ x, const float *__restrict__ w, int n, int rows,
+                            const double *__restrict__ wsum, float *__restrict__ loss, float *__restrict__ dtheta,
+                            __nv_bfloat16 *__restrict__ dL, __nv_bfloat16 *__restrict__ dLt)
+{
+    __shared__ float s_dt[KB];
+    __shared__ float s_loss;
+    if (threadIdx.x < KB) s_dt[threadIdx.x] = 0.0f;
+    if (threadIdx.x == 0) s_loss = 0.0f;
+    __syncthreads();
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < rows) {
+        const float ww = j < n ? (float)(w[j] / *wsum) : 0.0f;
+        float z[KB], q[KB];
+        const float *src = layer == 0 ? theta0 : L + (long long)j * KB;
+        for (int k = 0; k < KB; ++k) z[k] = src[k];
+        softmax32(z, q);
+        const float xv = j < n ? x[3ll * j + layer] : 0.5f;
+        const int b = min((int)(xv * KB), KB - 1);
+        if (ww != 0.0f) atomicAdd(&s_loss, -ww * logf(KB * q[b]));
+        for (int k = 0; k < KB; ++k) {
+            const float g = -ww * ((k == b ? 1.0f : 0.0f) - q[k]);
+            if (layer == 0) {
+                if (ww != 0.0f) atomicAdd(&s_dt[k], g);
+            } else {
+                const __nv_bfloat16 gb = __float2bfloat16_rn(g);
+                dL[(long long)j * KB + k] = gb;
+                dLt[(long long)k * rows + j] = gb;
+            }
+        }
+    }
+    __syncthreads();
+    if (layer == 0 && threadIdx.x < KB) atomicAdd(dtheta + threadIdx.x, s_dt[threadIdx.x]);
+    if (threadIdx.x == 0) atomicAdd(loss, s_loss);
+}
+
+// out[r] += sum_j At[r][j] (bias gradient from a transposed backward signal), one warp per row.
+__global__ void k_rowsum(const __nv_bfloat16 *__restrict__ At, int nrows, int rows, float *__restrict__ out)
+{
+    const int r = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (r >= nrows) return;
+    float s = 0.0f;
+    for (int j = threadIdx.x & 31; j < rows; j += 32) s += __bfloat162float(At[(long long)r * rows + j]);
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) out[r] += s;
+}
+
+__global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m, float *__restrict__ v,
+                       int n, float lr, float b1, float b2, float eps, float bc1, float bc2)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+    }
+}
+
+__global__ void k_sync(const float *__restrict__ p, __nv_bfloat16 *__restrict__ wb, __nv_bfloat16 *__restrict__ wt)
+{
+    const int total = QMCRT_WARP_BF16_WEIGHTS;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        int m = e / (3 * WD * WD + KB * WD), r = e % (3 * WD * WD + KB * WD), l = 0;
+        while (r >= out_dim(l) * WD) {
+            r -= out_dim(l) * WD;
+            ++l;
+        }
+        const int o = r / WD, i = r % WD;
+        const __nv_bfloat16 b = __float2bfloat16_rn(p[param_w(m, l) + r]);
+        wb[e] = b;
+        wt[bf_w(m, l) + i * out_dim(l) + o] = b;
+    }
+}
+
+unsigned blocks(long long n, int t = 256)
+{
+    long long b = (n + t - 1) / t;
+    return (unsigned)std::max(1ll, std::min(b, 152ll * 32));
+}
+
+int gemm(const __nv_bfloat16 *A, const __nv_bfloat16 *B, int M, int N, int K, int splits, GemmEpi ep, cudaStream_t s)
+{
+    cudaError_t e = launch_gemm_bf16(A, B, M, N, K, splits, ep, s);
+    return e == cudaSuccess ? QMCRT_OK : set_error(QMCRT_ERR_CUDA, "flow gemm: %s", cudaGetErrorString(e));
+}
+
+GemmEpi epi(int *err)
+{
+    GemmEpi e;
+    memset(&e, 0, sizeof e);
+    e.error = err;
+    return e;
+}
+
+// Forward of MLP m on the features in W.F; keeps activations (and their transposes when
+// `keep_t`), logits in W.L.
+int mlp_forward(const qmcrt_warp *wp, const Work &W, int m, bool keep_t, cudaStream_t s)
+{
+    const auto *wb = (const __nv_bfloat16 *)wp->d_weights;
+    const __nv_bfloat16 *in = W.F;
+    for (int l = 0; l < 3; ++l) {
+        GemmEpi e = epi(wp->d_error);
+        e.bias = wp->d_params + param_b(m, l);
+        e.relu = 1;
+        e.out_bf16 = W.H[l];
+        if (keep_t) {
+            e.out_bf16_t = W.Ht[l];
+            e.ldt = W.rows;
+        }
+        int rc = gemm(in, wb + bf_w(m, l), W.rows, WD, WD, 1, e, s);
+        if (rc) return rc;
+        in = W.H[l];
+    }
+    GemmEpi e = epi(wp->d_error);
+    e.bias = wp->d_params + param_b(m, 3);
+    e.out_f32 = W.L;
+    return gemm(in, wb + bf_w(m, 3), W.rows, KB, WD, 1, e, s);
+}
+
+int check_warp(const qmcrt_warp *w)
+{
+    if (!w || w->struct_size != sizeof(qmcrt_warp)) return set_error(QMCRT_ERR_INVALID_ARG, "warp descriptor");
+    if (!w->d_params || !w->d_weights || !w->d_weights_t) return set_error(QMCRT_ERR_INVALID_ARG, "NULL warp buffers");
+    if (((uintptr_t)w->d_weights | (uintptr_t)w->d_weights_t) & 15)
+        return set_error(QMCRT_ERR_INVALID_ARG, "warp weights must be 16-byte aligned");
+    return QMCRT_OK;
+}
+
+int launch_status(const char *what)
+{
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? QMCRT_OK : set_error(QMCRT_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+}  // namespace
+}  // namespace qmcrt
+
+using namespace qmcrt;
+
+extern "C" {
+
+uint64_t qmcrt_warp_workspace_bytes(uint64_t rows) { return bytes_for(round128(rows ? rows : 1)); }
+
+int qmcrt_warp_sync(const qmcrt_warp *warp, void *stream)
+{
+    int rc = check_warp(warp);
+    if (rc) return rc;
+    k_sync<<<blocks(QMCRT_WARP_BF16_WEIGHTS), 256, 0, (cudaStream_t)stream>>>(
+        warp->d_params, (__nv_bfloat16 *)warp->d_weights, (__nv_bfloat16 *)warp->d_weights_t);
+    return launch_status("warp sync");
+}
+
+int qmcrt_warp_forward(const qmcrt_warp *warp, const float *d_u, float *d_x, float *d_logj, uint64_t n,
+                       void *d_workspace, uint64_t workspace_bytes, void *stream)
+{
+    int rc = check_warp(warp);
+    if (rc) return rc;
+    if (!d_u || !d_x || !d_logj || !d_workspace) return set_error(QMCRT_ERR_INVALID_ARG, "NULL buffer");
+    const int R = rows_for(workspace_bytes);
+    if (R < 128) return set_error(QMCRT_ERR_INVALID_ARG, "workspace below one pass of 128 rows");
+    cudaStream_t s = (cudaStream_t)stream;
+    const Work W0 = carve(d_workspace, R);
+    for (uint64_t base = 0; base < n; base += (uint64_t)R) {
+        const int cnt = (int)std::min<uint64_t>((uint64_t)R, n - base);
+        Work W = W0;
+        W.rows = (int)round128(cnt);
+        const float *u = d_u + 3 * base;
+        float *x = d_x + 3 * base, *lj = d_logj + base;
+        k_sample<<<blocks(cnt), 256, 0, s>>>(0, warp->d_params, nullptr, u, x, lj, cnt);
+        for (int m = 0; m < 2; ++m) {
+            k_features<<<blocks((long long)W.rows * WD), 256, 0, s>>>(x, cnt, W.rows, m, W.F, nullptr);
+            if ((rc = launch_status("warp features"))) return rc;
+            if ((rc = mlp_forward(warp, W, m, false, s))) return rc;
+            k_sample<<<blocks(cnt), 256, 0, s>>>(m + 1, warp->d_params, W.L, u, x, lj, cnt);
+            if ((rc = launch_status("warp sample"))) return rc;
+        }
+    }
+    return QMCRT_OK;
+}
+
+int qmcrt_warp_grad(const qmcrt_warp *warp, const float *d_x, const float *d_w, uint64_t n, float *d_grad,
+                    float *d_loss, void *d_workspace, uint64_t workspace_bytes, void *stream)
+{
+    int rc = check_warp(warp);
+    if (rc) return rc;
+    if (!d_x || !d_w || !d_grad || !d_loss || !d_workspace) return set_error(QMCRT_ERR_INVALID_ARG, "NULL buffer");
+    const int R = rows_for(workspace_bytes);
+    if (R < 128) return set_error(QMCRT_ERR_INVALID_ARG, "workspace below one pass of 128 rows");
+    cudaStream_t s = (cudaStream_t)stream;
+    const Work W0 = carve(d_workspace, R);
+    const auto *wt = (const __nv_bfloat16 *)warp->d_weights_t;
+    cudaError_t e = cudaMemsetAsync(W0.wsum, 0, sizeof(double), s);
+    if (e != cudaSuccess) return set_error(QMCRT_ERR_CUDA, "warp grad: %s", cudaGetErrorString(e));
+    if (n) k_wsum<<<blocks((long long)n), 256, 0, s>>>(d_w, (int)n, W0.wsum);
+    for (uint64_t base = 0; base < n; base += (uint64_t)R) {
+        const int cnt = (int)std::min<uint64_t>((uint64_t)R, n - base);
+        Work W = W0;
+        W.rows = (int)round128(cnt);
+        const float *x = d_x + 3 * base, *w = d_w + base;
+        k_loss_grad<<<(W.rows + 255) / 256, 256, 0, s>>>(0, warp->d_params, nullptr, x, w, cnt, W.rows, W.wsum, d_loss,
+                                                          d_grad, nullptr, nullptr);
+        for (int m = 0; m < 2; ++m) {
+            k_features<<<blocks((long long)W.rows * WD), 256, 0, s>>>(x, cnt, W.rows, m, W.F, W.Ft);
+            if ((rc = mlp_forward(warp, W, m, true, s))) return rc;
+            k_loss_grad<<<(W.rows + 255) / 256, 256, 0, s>>>(m + 1, warp->d_params, W.L, x, w, cnt, W.rows, W.wsum,
+                                                              d_loss, d_grad, W.dL, W.dLt);
+            if ((rc = launch_status("warp loss"))) return rc;
+            const int splits = std::max(1, W.rows / 2048);
+            // layer 3: signal dL [rows x 32]
+            const __nv_bfloat16 *dP = W.dL, *dPt = W.dLt;
+            for (int l = 3; l >= 0; --l) {
+                const int N_out = out_dim(l);
+                const __nv_bfloat16 *Xt = l == 0 ? W.Ft : W.Ht[l - 1];
+                GemmEpi gw = epi(warp->d_error);  // dW[l] = dP^T . X  (M = out, N = in, K = rows)
+                gw.out_f32 = d_grad + param_w(m, l);
+                gw.atomic_f32 = splits > 1;
+                if (gw.atomic_f32 == 0) gw.atomic_f32 = 1;  // accumulate into the caller's gradient
+                if ((rc = gemm(dPt, Xt, N_out, WD, W.rows, splits, gw, s))) return rc;
+                k_rowsum<<<(N_out + 7) / 8, 256, 0, s>>>(dPt, N_out, W.rows, d_grad + param_b(m, l));
+                if ((rc = launch_status("warp bias grad"))) return rc;
+                if (l == 0) break;
+                GemmEpi gx = epi(warp->d_error);  // dH[l-1] = (dP . W[l]) * (H[l-1] > 0)
+                gx.mask = W.H[l - 1];
+                gx.out_bf16 = W.dP[l & 1];
+                gx.out_bf16_t = W.dPt[l & 1];
+                gx.ldt = W.rows;
+                if ((rc = gemm(dP, wt + bf_w(m, l), W.rows, WD, N_out, 1, gx, s))) return rc;
+                dP = W.dP[l & 1];
+                dPt = W.dPt[l & 1];
+            }
+        }
+    }
+    return launch_status("warp grad");
+}
+
+int qmcrt_warp_adam(const qmcrt_warp *warp, const float *d_grad, float *d_m, float *d_v, const qmcrt_adam *opt,
+                    void *stream)
+{
+    int rc = check_warp(warp);
+    if (rc) return rc;
+    if (!d_grad || !d_m || !d_v || !opt || opt->struct_size != sizeof(qmcrt_adam) || opt->step < 1)
+        return set_error(QMCRT_ERR_INVALID_ARG, "adam arguments");
+    const float bc1 = (float)(1.0 - std::pow(opt->beta1, opt->step));
+    const float bc2 = (float)(1.0 - std::pow(opt->beta2, opt->step));
+    k_adam<<<blocks(QMCRT_WARP_PARAMS), 256, 0, (cudaStream_t)stream>>>(
+        warp->d_params, d_grad, d_m, d_v, QMCRT_WARP_PARAMS, (float)opt->lr, (float)opt->beta1, (float)opt->beta2,
+        (float)opt->eps, bc1, bc2);
+    if ((rc = launch_status("warp adam"))) return rc;
+    return qmcrt_warp_sync(warp, stream);
+}
+
+}  // extern "C"

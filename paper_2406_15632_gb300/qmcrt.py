@@ -93,6 +93,16 @@ class qmcrt_gemm_epilogue(C.Structure):
                 ("ldt", C.c_int32), ("k_splits", C.c_int32), ("d_error", C.c_void_p)]
 
 
+class qmcrt_warp(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("reserved", C.c_int32), ("d_params", C.c_void_p),
+                ("d_weights", C.c_void_p), ("d_weights_t", C.c_void_p), ("d_error", C.c_void_p)]
+
+
+class qmcrt_adam(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("step", C.c_int32), ("lr", C.c_double), ("beta1", C.c_double),
+                ("beta2", C.c_double), ("eps", C.c_double)]
+
+
 def _new(cls, **kw):
     s = cls()
     s.struct_size = C.sizeof(cls)
@@ -125,6 +135,13 @@ _SIGS = [
                                      C.c_void_p]),
     ("qmcrt_gemm_bf16", C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32,
                                   _P(qmcrt_gemm_epilogue), C.c_void_p]),
+    ("qmcrt_warp_workspace_bytes", C.c_uint64, [C.c_uint64]),
+    ("qmcrt_warp_sync", C.c_int, [_P(qmcrt_warp), C.c_void_p]),
+    ("qmcrt_warp_forward", C.c_int, [_P(qmcrt_warp), C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p,
+                                     C.c_uint64, C.c_void_p]),
+    ("qmcrt_warp_grad", C.c_int, [_P(qmcrt_warp), C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p,
+                                  C.c_void_p, C.c_uint64, C.c_void_p]),
+    ("qmcrt_warp_adam", C.c_int, [_P(qmcrt_warp), C.c_void_p, C.c_void_p, C.c_void_p, _P(qmcrt_adam), C.c_void_p]),
     ("qmcrt_pad_grid", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
     ("qmcrt_trace_single_noalloc", C.c_int, [_P(qmcrt_medium), _P(qmcrt_source), _P(qmcrt_dust),
                                              _P(qmcrt_observer), _P(qmcrt_points_desc), _P(qmcrt_trace_opts),
@@ -207,6 +224,110 @@ def gemm(A, B, *, bias=None, relu=False, mask=None, out_f32=None, out_bf16=None,
               d_out_bf16=ptr(out_bf16), d_out_bf16_t=ptr(out_bf16_t),
               ldt=out_bf16_t.shape[1] if out_bf16_t is not None else 0, k_splits=k_splits, d_error=ptr(error))
     qmcrt_gemm_bf16(A.data_ptr(), B.data_ptr(), M, N, K, ep, _stream(stream))
+
+
+WARP_BINS, WARP_WIDTH, WARP_PARAMS, WARP_BF16_WEIGHTS = 32, 128, 107360, 106496
+
+
+def qmcrt_warp_workspace_bytes(rows: int) -> int:
+    return int(load().qmcrt_warp_workspace_bytes(rows))
+
+
+def qmcrt_warp_sync(warp, stream: int = 0) -> None:
+    _check(load().qmcrt_warp_sync(C.byref(warp), C.c_void_p(stream)))
+
+
+def qmcrt_warp_forward(warp, d_u: int, d_x: int, d_logj: int, n: int, d_ws: int, ws_bytes: int,
+                       stream: int = 0) -> None:
+    _check(load().qmcrt_warp_forward(C.byref(warp), C.c_void_p(d_u), C.c_void_p(d_x), C.c_void_p(d_logj), n,
+                                     C.c_void_p(d_ws), ws_bytes, C.c_void_p(stream)))
+
+
+def qmcrt_warp_grad(warp, d_x: int, d_w: int, n: int, d_grad: int, d_loss: int, d_ws: int, ws_bytes: int,
+                    stream: int = 0) -> None:
+    _check(load().qmcrt_warp_grad(C.byref(warp), C.c_void_p(d_x), C.c_void_p(d_w), n, C.c_void_p(d_grad),
+                                  C.c_void_p(d_loss), C.c_void_p(d_ws), ws_bytes, C.c_void_p(stream)))
+
+
+def qmcrt_warp_adam(warp, d_grad: int, d_m: int, d_v: int, opt, stream: int = 0) -> None:
+    _check(load().qmcrt_warp_adam(C.byref(warp), C.c_void_p(d_grad), C.c_void_p(d_m), C.c_void_p(d_v),
+                                  C.byref(opt), C.c_void_p(stream)))
+
+
+class Warp:
+    """Device state of the learned warp: FP32 parameters, their bf16 copies, Adam
+    moments, a workspace for `rows` samples per pass, and an error word."""
+
+    def __init__(self, params=None, *, rows: int = 1 << 16, seed: int = 0):
+        torch = _torch()
+        if params is None:
+            params = self.initial(seed)
+        self.params = torch.as_tensor(params, dtype=torch.float32).to("cuda").contiguous()
+        assert self.params.numel() == WARP_PARAMS
+        self.wb = torch.zeros(WARP_BF16_WEIGHTS, dtype=torch.bfloat16, device="cuda")
+        self.wt = torch.zeros(WARP_BF16_WEIGHTS, dtype=torch.bfloat16, device="cuda")
+        self.error = torch.zeros(1, dtype=torch.int32, device="cuda")
+        self.desc = _new(qmcrt_warp, d_params=self.params.data_ptr(), d_weights=self.wb.data_ptr(),
+                         d_weights_t=self.wt.data_ptr(), d_error=self.error.data_ptr())
+        self.ws_bytes = qmcrt_warp_workspace_bytes(rows)
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device="cuda")
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.grad = torch.zeros_like(self.params)
+        self.loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        self.step = 0
+        qmcrt_warp_sync(self.desc, _stream(None))
+
+    @staticmethod
+    def initial(seed: int = 0):
+        """He-initialised hidden layers, small output layers, uniform x0 density: the
+        initial warp is close to the identity."""
+        torch = _torch()
+        g = torch.Generator().manual_seed(seed)
+        parts = [torch.zeros(WARP_BINS)]
+        for m in range(2):
+            for l, (o, i) in enumerate([(128, 128), (128, 128), (128, 128), (32, 128)]):
+                std = (2.0 / i) ** 0.5 * (0.1 if l == 3 else 1.0)
+                parts += [torch.randn((o, i), generator=g).reshape(-1) * std, torch.zeros(o)]
+        return torch.cat(parts)
+
+    def forward(self, u, stream=None):
+        """x = T(u), log|dx/du| for u [n][3] float32 on the device."""
+        torch = _torch()
+        n = u.shape[0]
+        x = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+        lj = torch.empty(n, dtype=torch.float32, device="cuda")
+        qmcrt_warp_forward(self.desc, u.data_ptr(), x.data_ptr(), lj.data_ptr(), n, self.ws.data_ptr(), self.ws_bytes,
+                           _stream(stream))
+        return x, lj
+
+    def gradient(self, x, w, stream=None):
+        """(loss, gradient) of the cross-entropy on samples x [n][3] with weights w [n]."""
+        self.grad.zero_()
+        self.loss.zero_()
+        qmcrt_warp_grad(self.desc, x.data_ptr(), w.data_ptr(), x.shape[0], self.grad.data_ptr(), self.loss.data_ptr(),
+                        self.ws.data_ptr(), self.ws_bytes, _stream(stream))
+        return self.loss, self.grad
+
+    def adam_step(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None) -> None:
+        self.step += 1
+        opt = _new(qmcrt_adam, step=self.step, lr=lr, beta1=beta1, beta2=beta2, eps=eps)
+        qmcrt_warp_adam(self.desc, self.grad.data_ptr(), self.m.data_ptr(), self.v.data_ptr(), opt, _stream(stream))
+
+    def train(self, x, w, *, epochs: int = 4, batch: int = 1 << 16, lr: float = 2e-3, seed: int = 0):
+        """Minibatch Adam over the logged samples; returns the loss per step."""
+        torch = _torch()
+        g = torch.Generator(device="cuda").manual_seed(seed)
+        n = x.shape[0]
+        losses = []
+        for _ in range(epochs):
+            perm = torch.randperm(n, generator=g, device="cuda")
+            for b0 in range(0, n - batch + 1, batch):
+                idx = perm[b0:b0 + batch]
+                loss, _ = self.gradient(x[idx].contiguous(), w[idx].contiguous())
+                losses.append(loss.clone())
+                self.adam_step(lr=lr)
+        return torch.cat(losses).cpu().tolist() if losses else []
 
 
 def qmcrt_pad_grid(d_k: int, nx: int, ny: int, nz: int, pad: int, d_padded: int, stream: int = 0) -> None:

@@ -39,7 +39,8 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 STRUCTS = ["qmcrt_points_desc", "qmcrt_medium", "qmcrt_source", "qmcrt_dust", "qmcrt_observer", "qmcrt_image",
-           "qmcrt_trace_opts", "qmcrt_instance", "qmcrt_batch_config", "qmcrt_gemm_epilogue"]
+           "qmcrt_trace_opts", "qmcrt_instance", "qmcrt_batch_config", "qmcrt_gemm_epilogue",
+           "qmcrt_warp", "qmcrt_adam"]
 
 
 def test_struct_layout_matches_the_c_compiler(tmp_path):
@@ -181,3 +182,12 @@ def test_batch_validation(lib):
         _expect(Q.ERR_INVALID_ARG, Q.qmcrt_trace_batch, *a)
     img2 = Q._new(Q.qmcrt_image, accum=1, d_accum=0x1000, n_images=1, frac_bits=40)
     _expect(Q.ERR_INVALID_ARG, Q.qmcrt_batch_reduce, img2, 0x3000, 8, 8, 8, 0x5000)
+
+
+def test_warp_constants_match_the_oracle_layout():
+    from oracle import flow as F
+
+    assert Q.WARP_PARAMS == F.N_PARAMS
+    assert Q.WARP_BF16_WEIGHTS == sum(F.LAYOUT[f"W{m}{l}"][1][0] * F.LAYOUT[f"W{m}{l}"][1][1]
+                                      for m in range(2) for l in range(4))
+    assert Q.Warp.initial(0).numel() == F.N_PARAMS
