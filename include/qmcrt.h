@@ -295,7 +295,8 @@ int qmcrt_gemm_bf16(const void *d_A, const void *d_B, int32_t M, int32_t N, int3
 
 typedef struct qmcrt_warp {
     uint32_t struct_size;
-    int32_t reserved;
+    float uniform_mix;   /* defensive mixture: bin masses (1 - mix) softmax + mix / 32, in [0, 1);
+                            bounds |dx/du| by mix^-3 */
     float *d_params;     /* device FP32 [QMCRT_WARP_PARAMS] */
     void *d_weights;     /* device bf16 [QMCRT_WARP_BF16_WEIGHTS] (refreshed by qmcrt_warp_sync) */
     void *d_weights_t;   /* device bf16 [QMCRT_WARP_BF16_WEIGHTS], the transposes */
@@ -348,6 +349,23 @@ int qmcrt_warp_adam(const qmcrt_warp *warp, const float *d_grad, float *d_m, flo
  * padded cells), CUDA.
  */
 int qmcrt_pad_grid(const float *d_k, int32_t nx, int32_t ny, int32_t nz, int32_t pad, float *d_padded, void *stream);
+
+/*
+ * qmcrt_trace_multiple_warped -- qmcrt_trace_multiple with the learned proposal: packet
+ * j (point index first_index + j) takes its first-order coordinates (emission phi,
+ * theta and first depth) from d_x[j][3] (x = T(u) from qmcrt_warp_forward) and
+ * multiplies its weight by exp(d_logj[j]) = |dx/du|, which keeps the estimator
+ * unbiased; the other orders read the point set as usual.  With d_x = d_logj = NULL
+ * it is qmcrt_trace_multiple.  d_train_log (optional, device float [count][4]):
+ * per packet the first-order coordinates used and the packet's total peel-off
+ * intensity summed over orders -- the samples and weights qmcrt_warp_grad trains on.
+ * Errors: as qmcrt_trace_multiple; INVALID_ARG if only one of d_x, d_logj is given;
+ * UNSUPPORTED for a warp with a sphere source.
+ */
+int qmcrt_trace_multiple_warped(const qmcrt_medium *medium, const qmcrt_source *source, const qmcrt_dust *dust,
+                                const qmcrt_observer *obs, const qmcrt_points_desc *pts, const qmcrt_trace_opts *opts,
+                                const float *d_x, const float *d_logj, const qmcrt_image *image, float *d_train_log,
+                                void *stream);
 
 /*
  * qmcrt_image_reduce -- final image in units of the source luminosity (Sec. 3.6):

@@ -117,6 +117,12 @@ def softmax(z):
     return e / e.sum(axis=-1, keepdims=True)
 
 
+def mixture(S, mix):
+    """Defensive mixture with the uniform bin masses: (1 - mix) S + mix / K, so that
+    K Q >= mix and |dx/du| = 1 / q(x) <= mix^-3."""
+    return (1.0 - mix) * S + mix / K_BINS
+
+
 def inverse_cdf(u, Q):
     """x with F(x) = u for the piecewise-constant pdf K Q[b] on K equal bins; returns x, b."""
     c = np.concatenate([np.zeros((Q.shape[0], 1)), np.cumsum(Q, axis=1)], axis=1)
@@ -133,38 +139,38 @@ def cdf(x, Q):
     return c[rows, b] + (x * K_BINS - b) * Q[rows, b]
 
 
-def conditionals(x, vec, use_bf16=False):
+def conditionals(x, vec, use_bf16=False, mix=0.0):
     """Q0 (one row per sample), Q1, Q2 at the coordinates x [B][3]."""
     p = unpack(vec)
     B = x.shape[0]
-    Q0 = np.repeat(softmax(p["theta0"])[None, :], B, axis=0)
+    Q0 = np.repeat(mixture(softmax(p["theta0"]), mix)[None, :], B, axis=0)
     L1, _ = mlp(features(x, 0, use_bf16), p, 0, use_bf16)
     L2, _ = mlp(features(x, 1, use_bf16), p, 1, use_bf16)
-    return Q0, softmax(L1), softmax(L2)
+    return Q0, mixture(softmax(L1), mix), mixture(softmax(L2), mix)
 
 
-def warp(u, vec, use_bf16=False):
+def warp(u, vec, use_bf16=False, mix=0.0):
     """x = T(u) and log |dx/du| (= -log q(x)) for points u [B][3]."""
     p = unpack(vec)
     B = u.shape[0]
     x = np.zeros((B, 3))
     logq = np.zeros(B)
-    Q0 = np.repeat(softmax(p["theta0"])[None, :], B, axis=0)
+    Q0 = np.repeat(mixture(softmax(p["theta0"]), mix)[None, :], B, axis=0)
     x[:, 0], b = inverse_cdf(u[:, 0], Q0)
     logq += np.log(K_BINS * Q0[np.arange(B), b])
     L1, _ = mlp(features(x, 0, use_bf16), p, 0, use_bf16)
-    Q1 = softmax(L1)
+    Q1 = mixture(softmax(L1), mix)
     x[:, 1], b = inverse_cdf(u[:, 1], Q1)
     logq += np.log(K_BINS * Q1[np.arange(B), b])
     L2, _ = mlp(features(x, 1, use_bf16), p, 1, use_bf16)
-    Q2 = softmax(L2)
+    Q2 = mixture(softmax(L2), mix)
     x[:, 2], b = inverse_cdf(u[:, 2], Q2)
     logq += np.log(K_BINS * Q2[np.arange(B), b])
     return x, -logq
 
 
-def log_density(x, vec, use_bf16=False):
-    Qs = conditionals(x, vec, use_bf16)
+def log_density(x, vec, use_bf16=False, mix=0.0):
+    Qs = conditionals(x, vec, use_bf16, mix)
     rows = np.arange(x.shape[0])
     out = np.zeros(x.shape[0])
     for l, Q in enumerate(Qs):
@@ -173,8 +179,10 @@ def log_density(x, vec, use_bf16=False):
     return out
 
 
-def loss_and_grad(x, w, vec, use_bf16=False):
-    """loss = -sum_j w_j log q(x_j) / sum_j w_j and its gradient w.r.t. the parameters."""
+def loss_and_grad(x, w, vec, use_bf16=False, mix=0.0):
+    """loss = -sum_j w_j log q(x_j) / sum_j w_j and its gradient w.r.t. the parameters.
+    With the mixture Q = (1 - mix) S + mix / K (S = softmax(z)) the derivative of
+    log Q_b by the logits is r (e_b - S), r = (1 - mix) S_b / Q_b."""
     p = unpack(vec)
     B = x.shape[0]
     rows = np.arange(B)
@@ -182,20 +190,24 @@ def loss_and_grad(x, w, vec, use_bf16=False):
     g = {k: np.zeros(s) for k, (o, s) in LAYOUT.items()}
     loss = 0.0
     # x0: unconditional logits
-    Q0 = softmax(p["theta0"])
+    S0 = softmax(p["theta0"])
+    Q0 = mixture(S0, mix)
     b0 = np.minimum((x[:, 0] * K_BINS).astype(int), K_BINS - 1)
     loss -= np.sum(w * np.log(K_BINS * Q0[b0])) / W
     onehot0 = np.zeros((B, K_BINS))
     onehot0[rows, b0] = 1.0
-    g["theta0"] = -((w / W)[:, None] * (onehot0 - Q0[None, :])).sum(axis=0)
+    r0 = (1.0 - mix) * S0[b0] / Q0[b0]
+    g["theta0"] = -((w / W * r0)[:, None] * (onehot0 - S0[None, :])).sum(axis=0)
     for m in range(2):
         L, cache = mlp(features(x, m, use_bf16), p, m, use_bf16)
-        Q = softmax(L)
+        Sm = softmax(L)
+        Q = mixture(Sm, mix)
         bl = np.minimum((x[:, m + 1] * K_BINS).astype(int), K_BINS - 1)
         loss -= np.sum(w * np.log(K_BINS * Q[rows, bl])) / W
         oh = np.zeros((B, K_BINS))
         oh[rows, bl] = 1.0
-        d = -(w / W)[:, None] * (oh - Q)  # d loss / d logits
+        r = (1.0 - mix) * Sm[rows, bl] / Q[rows, bl]
+        d = -(w / W * r)[:, None] * (oh - Sm)  # d loss / d logits
         for l in (3, 2, 1, 0):
             h_in = cache[l]
             Wl = p[f"W{m}{l}"]

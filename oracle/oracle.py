@@ -97,6 +97,7 @@ def lib():
             P = C.POINTER(_Problem)
             L.or_trace_single.argtypes = [P, u64, u64, dp, dp, i32]
             L.or_trace_multiple.argtypes = [P, u64, u64, dp, i32]
+            L.or_trace_multiple_warped.argtypes = [P, u64, u64, dp, dp, dp, dp, i32]
             L.or_tau_ray.restype = C.c_double
             L.or_tau_ray.argtypes = [P, dp, dp]
             L.or_march_ray.argtypes = [P, dp, dp, C.c_double, dp]
@@ -257,6 +258,25 @@ def trace_multiple(prob, first: int, count: int, nthreads: int | None = None):
     if rc != 0:
         raise RuntimeError(f"oracle trace_multiple rc={rc}")
     return img
+
+
+def trace_multiple_warped(prob, first: int, count: int, x=None, logj=None, train_log: bool = False,
+                          nthreads: int | None = None):
+    """Multiple scattering with the first-order coordinates of packet j set to x[j]
+    and its weight multiplied by exp(logj[j]).  Returns the raw image sums and, if
+    asked, the per-packet log [count][4] (coordinates, total peel-off intensity)."""
+    h = _Holder(prob)
+    img = np.zeros((prob.n_images, 3, prob.ny, prob.nx), dtype=np.float64)
+    dp = C.POINTER(C.c_double)
+    xa = None if x is None else np.ascontiguousarray(x, dtype=np.float64).reshape(count, 3)
+    la = None if logj is None else np.ascontiguousarray(logj, dtype=np.float64).reshape(count)
+    tl = np.zeros((count, 4), dtype=np.float64) if train_log else None
+    ptr = lambda a: a.ctypes.data_as(dp) if a is not None else None
+    rc = lib().or_trace_multiple_warped(h.ptr, first, count, ptr(xa), ptr(la), img.ctypes.data_as(dp), ptr(tl),
+                                        nthreads or default_threads())
+    if rc != 0:
+        raise RuntimeError(f"oracle trace_multiple_warped rc={rc}")
+    return (img, tl) if train_log else img
 
 
 def _vec(v):

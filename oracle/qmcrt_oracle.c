@@ -681,6 +681,8 @@ typedef struct {
     double *img;
     double *log;
     int multiple;
+    const double *wx, *wlogj; /* optional learned warp: first-order coordinates, log |dx/du| */
+    double *tlog;             /* optional [count][4]: coordinates used, total peel-off I */
 } or_job;
 
 static void or_trace_single_range(const or_problem *Pr, uint64_t first, uint64_t count, double *img,
@@ -749,15 +751,32 @@ static void or_scatter(const or_dust *D, double u, double v, double n[3], double
 /* Multiple scattering, point source.  Coordinates of order k (1-based) are
  * 4(k-1) + {0, 1, 2, 3}: azimuth (or emission phi), cos Theta (or emission
  * theta), depth, roulette. */
-static void or_trace_multiple_range(const or_problem *Pr, uint64_t first, uint64_t count, double *img)
+static void or_trace_multiple_range(const or_problem *Pr, uint64_t first, uint64_t count, double *img,
+                                    const double *wx, const double *wlogj, double *tlog)
 {
     or_view V;
     or_make_view(&Pr->obs, &V);
     size_t img_size = (size_t)3 * Pr->obs.nx * Pr->obs.ny;
     for (uint64_t j = 0; j < count; ++j) {
         uint64_t i = first + j;
-        double pos[3], n[3], a[3], wgt;
-        double w = or_emit(&Pr->source, &Pr->points, i, pos, n, a, &wgt);
+        double pos[3], n[3], a[3], wgt, w, total = 0.0;
+        double x0 = or_point_f64(&Pr->points, i, 0), x1 = or_point_f64(&Pr->points, i, 1);
+        if (wx) {
+            /* Learned proposal: the first-order coordinates are x = T(u), and the
+             * weight carries the Jacobian |dx/du| = 1 / q(x), so the estimate of the
+             * integral over x stays unbiased. */
+            double ep[3];
+            x0 = wx[3 * j];
+            x1 = wx[3 * j + 1];
+            from_angles(2.0 * x1 - 1.0, x0, n);
+            pos[0] = pos[1] = pos[2] = 0.0;
+            sph_basis(n, a, ep);
+            w = wx[3 * j + 2];
+            wgt = exp(wlogj[j]);
+        } else {
+            w = or_emit(&Pr->source, &Pr->points, i, pos, n, a, &wgt);
+        }
+        const double w_first = w;
         double S[3] = {wgt, 0.0, 0.0};
         for (int k = 1; k <= Pr->max_orders; ++k) {
             int base = 4 * (k - 1);
@@ -777,8 +796,10 @@ static void or_trace_multiple_range(const or_problem *Pr, uint64_t first, uint64
             }
             for (int s = 0; s < 3; ++s) S[s] *= Pr->dust.albedo;
             double out[3], x, y;
-            if (or_peel(Pr, &V, pos, n, a, S, out, &x, &y))
+            if (or_peel(Pr, &V, pos, n, a, S, out, &x, &y)) {
                 or_splat(&Pr->obs, img + (Pr->per_order ? (size_t)(k - 1) * img_size : 0), x, y, out);
+                total += out[0];
+            }
             if (k == Pr->max_orders) break;
             if (S[0] < Pr->rr_threshold) {
                 double r = or_point_f64(&Pr->points, i, base + 3);
@@ -789,13 +810,19 @@ static void or_trace_multiple_range(const or_problem *Pr, uint64_t first, uint64
                 }
             }
         }
+        if (tlog) {
+            tlog[4 * j] = x0;
+            tlog[4 * j + 1] = x1;
+            tlog[4 * j + 2] = w_first;
+            tlog[4 * j + 3] = total;
+        }
     }
 }
 
 static void *or_worker(void *arg)
 {
     or_job *J = (or_job *)arg;
-    if (J->multiple) or_trace_multiple_range(J->Pr, J->first, J->count, J->img);
+    if (J->multiple) or_trace_multiple_range(J->Pr, J->first, J->count, J->img, J->wx, J->wlogj, J->tlog);
     else or_trace_single_range(J->Pr, J->first, J->count, J->img, J->log);
     return NULL;
 }
@@ -805,7 +832,7 @@ static void *or_worker(void *arg)
  * packet: scattering position, peel-off I, Q, U, sky x, y, status (0 ok, 1 tau_1 <
  * tau_min, 2 occulted), grid cells visited by the packet's walks. */
 static int or_trace(const or_problem *Pr, uint64_t first, uint64_t count, double *image, double *log,
-                    int nthreads, int multiple)
+                    int nthreads, int multiple, const double *wx, const double *wlogj, double *tlog)
 {
     size_t img_size = (size_t)3 * Pr->obs.nx * Pr->obs.ny * (multiple && Pr->per_order ? Pr->max_orders : 1);
     if (nthreads < 1) nthreads = 1;
@@ -821,6 +848,9 @@ static int or_trace(const or_problem *Pr, uint64_t first, uint64_t count, double
         jobs[t].img = calloc(img_size, sizeof(double));
         jobs[t].log = log ? log + a * OR_LOG_COLS : NULL;
         jobs[t].multiple = multiple;
+        jobs[t].wx = wx ? wx + 3 * a : NULL;
+        jobs[t].wlogj = wlogj ? wlogj + a : NULL;
+        jobs[t].tlog = tlog ? tlog + 4 * a : NULL;
         if (!jobs[t].img) return -1;
         pthread_create(&th[t], NULL, or_worker, &jobs[t]);
     }
@@ -837,13 +867,25 @@ static int or_trace(const or_problem *Pr, uint64_t first, uint64_t count, double
 int or_trace_single(const or_problem *Pr, uint64_t first, uint64_t count, double *image, double *log,
                     int nthreads)
 {
-    return or_trace(Pr, first, count, image, log, nthreads, 0);
+    return or_trace(Pr, first, count, image, log, nthreads, 0, NULL, NULL, NULL);
 }
 
 int or_trace_multiple(const or_problem *Pr, uint64_t first, uint64_t count, double *image, int nthreads)
 {
     if (Pr->source.kind != 0) return -3; /* multiple scattering: point source only */
-    return or_trace(Pr, first, count, image, NULL, nthreads, 1);
+    return or_trace(Pr, first, count, image, NULL, nthreads, 1, NULL, NULL, NULL);
+}
+
+/* Multiple scattering with the first-order coordinates of packet j given (x[j][3],
+ * weight exp(logj[j])); either may be NULL together (plain points).  train_log
+ * (optional) gets per packet the first-order coordinates used and the packet's total
+ * peel-off intensity over all orders. */
+int or_trace_multiple_warped(const or_problem *Pr, uint64_t first, uint64_t count, const double *x,
+                             const double *logj, double *image, double *train_log, int nthreads)
+{
+    if (Pr->source.kind != 0) return -3;
+    if ((x == NULL) != (logj == NULL)) return -2;
+    return or_trace(Pr, first, count, image, NULL, nthreads, 1, x, logj, train_log);
 }
 
 /* Exposed for pins: tau along a ray and the position after a march. */

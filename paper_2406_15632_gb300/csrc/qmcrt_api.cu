@@ -293,9 +293,14 @@ int fill_trace(const qmcrt_medium *md, const qmcrt_source *src, const qmcrt_dust
     return QMCRT_OK;
 }
 
+struct WarpIO {
+    const float *x = nullptr, *logj = nullptr;
+    float *log = nullptr;
+};
+
 int trace_common(const qmcrt_medium *md, const qmcrt_source *src, const qmcrt_dust *du, const qmcrt_observer *ob,
                  const qmcrt_points_desc *pts, const qmcrt_trace_opts *op, const qmcrt_image *im, double *d_log,
-                 void *stream, int multiple)
+                 void *stream, int multiple, WarpIO wio = WarpIO())
 {
     CHECK_STRUCT(md, qmcrt_medium);
     CHECK_STRUCT(src, qmcrt_source);
@@ -310,6 +315,9 @@ int trace_common(const qmcrt_medium *md, const qmcrt_source *src, const qmcrt_du
         int rc = fill_trace<double>(md, src, du, ob, pts, op, im, multiple, P);
         if (rc) return rc;
         P.log = d_log;
+        P.warp_x = wio.x;
+        P.warp_logj = wio.logj;
+        P.train_log = wio.log;
         return cuda_status(multiple ? qmcrt::launch_trace_multiple_f64(P, block, s)
                                     : qmcrt::launch_trace_single_f64(P, block, s),
                            "trace launch");
@@ -318,6 +326,9 @@ int trace_common(const qmcrt_medium *md, const qmcrt_source *src, const qmcrt_du
     int rc = fill_trace<float>(md, src, du, ob, pts, op, im, multiple, P);
     if (rc) return rc;
     P.log = d_log;
+    P.warp_x = wio.x;
+    P.warp_logj = wio.logj;
+    P.train_log = wio.log;
     return cuda_status(multiple ? qmcrt::launch_trace_multiple_f32(P, block, s) : qmcrt::launch_trace_single_f32(P, block, s),
                        "trace launch");
 }
@@ -509,6 +520,23 @@ int qmcrt_pad_grid(const float *d_k, int32_t nx, int32_t ny, int32_t nz, int32_t
     if ((double)(nx + 2 * pad) * (ny + 2 * pad) * (nz + 2 * pad) > 2147483647.0)
         return fail(QMCRT_ERR_INVALID_ARG, "padded grid larger than 2^31 cells");
     return cuda_status(qmcrt::launch_pad_grid(d_k, nx, ny, nz, pad, d_padded, (cudaStream_t)stream), "pad_grid launch");
+}
+
+int qmcrt_trace_multiple_warped(const qmcrt_medium *medium, const qmcrt_source *source, const qmcrt_dust *dust,
+                                const qmcrt_observer *obs, const qmcrt_points_desc *pts, const qmcrt_trace_opts *opts,
+                                const float *d_x, const float *d_logj, const qmcrt_image *image, float *d_train_log,
+                                void *stream)
+{
+    g_last_error.clear();
+    CHECK_STRUCT(source, qmcrt_source);
+    if ((d_x == nullptr) != (d_logj == nullptr)) return fail(QMCRT_ERR_INVALID_ARG, "d_x and d_logj go together");
+    if (d_x && source->kind != QMCRT_SOURCE_POINT)
+        return fail(QMCRT_ERR_UNSUPPORTED, "the warp replaces point-source coordinates only");
+    WarpIO w;
+    w.x = d_x;
+    w.logj = d_logj;
+    w.log = d_train_log;
+    return trace_common(medium, source, dust, obs, pts, opts, image, nullptr, stream, 1, w);
 }
 
 int qmcrt_image_reduce(const qmcrt_image *image, int32_t nx, int32_t ny, int32_t n_replicas, double scale,

@@ -12,34 +12,16 @@
 #include <cstring>
 
 #include "qmcrt.h"
+#include "qmcrt_flow.cuh"
 #include "qmcrt_gemm.cuh"
 #include "qmcrt_internal.h"
 
 namespace qmcrt {
 namespace {
 
-constexpr int KB = QMCRT_WARP_BINS;
-constexpr int WD = QMCRT_WARP_WIDTH;
-constexpr int BLOB = 32;
+using namespace flow;
 constexpr int ROW_BYTES = 3328;  // workspace bytes per row (see carve)
 
-__host__ __device__ constexpr int out_dim(int l) { return l == 3 ? KB : WD; }
-__host__ __device__ constexpr int mlp_params() { return 3 * (WD * WD + WD) + (KB * WD + KB); }
-__host__ __device__ inline int param_w(int m, int l)
-{
-    int o = KB + m * mlp_params();
-    for (int j = 0; j < l; ++j) o += out_dim(j) * WD + out_dim(j);
-    return o;
-}
-__host__ __device__ inline int param_b(int m, int l) { return param_w(m, l) + out_dim(l) * WD; }
-__host__ __device__ inline int bf_w(int m, int l)
-{
-    int o = m * (3 * WD * WD + KB * WD);
-    for (int j = 0; j < l; ++j) o += out_dim(j) * WD;
-    return o;
-}
-static_assert(KB + 2 * mlp_params() == QMCRT_WARP_PARAMS, "parameter count");
-static_assert(2 * (3 * WD * WD + KB * WD) == QMCRT_WARP_BF16_WEIGHTS, "weight count");
 
 struct Work {
     __nv_bfloat16 *F, *Ft, *H[3], *Ht[3], *dL, *dLt, *dP[2], *dPt[2];
@@ -87,7 +69,6 @@ int rows_for(uint64_t ws_bytes)
     return (int)std::min<uint64_t>(r, 1u << 22);
 }
 
-__device__ __forceinline__ float blob(float v, int k) { const float d = (v - (k + 0.5f) / BLOB) * BLOB; return __expf(-0.5f * d * d); }
 
 // Input features of MLP m for rows [0, rows): one-blob(x0) [, one-blob(x1)], zero padded;
 // rows >= n use x = 0.5 (their loss weight is zero).
@@ -106,23 +87,13 @@ __global__ void k_features(const float *__restrict__ x, int n, int rows, int m, 
     }
 }
 
-__device__ __forceinline__ void softmax32(const float *z, float *q)
-{
-    float mx = z[0];
-    for (int k = 1; k < KB; ++k) mx = fmaxf(mx, z[k]);
-    float s = 0.0f;
-    for (int k = 0; k < KB; ++k) {
-        q[k] = expf(z[k] - mx);
-        s += q[k];
-    }
-    const float inv = 1.0f / s;
-    for (int k = 0; k < KB; ++k) q[k] *= inv;
-}
+
 
 // Sampling step of coordinate `layer`: x_l = F^-1(u_l) for the pdf 32 Q[b] on bin b;
 // log |dx/du| accumulates -log(32 Q[b]).
 __global__ void k_sample(int layer, const float *__restrict__ theta0, const float *__restrict__ L,
-                         const float *__restrict__ u, float *__restrict__ x, float *__restrict__ logj, int n)
+                         const float *__restrict__ u, float *__restrict__ x, float *__restrict__ logj, int n,
+                         float mix)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
@@ -130,16 +101,11 @@ __global__ void k_sample(int layer, const float *__restrict__ theta0, const floa
     const float *src = layer == 0 ? theta0 : L + (long long)j * KB;
     for (int k = 0; k < KB; ++k) z[k] = src[k];
     softmax32(z, q);
-    const float uu = u[3ll * j + layer];
-    float c = 0.0f;
-    int b = KB - 1;
-    for (int k = 0; k < KB - 1; ++k) {
-        if (uu < c + q[k]) { b = k; break; }
-        c += q[k];
-    }
-    const float xv = fminf(fmaxf((b + (uu - c) / q[b]) / KB, 0.0f), 1.0f);
+    if (mix != 0.0f)
+        for (int k = 0; k < KB; ++k) q[k] = mixed(q[k], mix);
+    float xv, lq;
+    sample_bin(q, u[3ll * j + layer], xv, lq);
     x[3ll * j + layer] = xv;
-    const float lq = logf(KB * q[b]);
     logj[j] = layer == 0 ? -lq : logj[j] - lq;
 }
 
@@ -156,7 +122,7 @@ __global__ void k_wsum(const float *__restrict__ w, int n, double *out)
 __global__ void k_loss_grad(int layer, const float *__restrict__ theta0, const float *__restrict__ L,
                             const float *__restrict__ x, const float *__restrict__ w, int n, int rows,
                             const double *__restrict__ wsum, float *__restrict__ loss, float *__restrict__ dtheta,
-                            __nv_bfloat16 *__restrict__ dL, __nv_bfloat16 *__restrict__ dLt)
+                            __nv_bfloat16 *__restrict__ dL, __nv_bfloat16 *__restrict__ dLt, float mix)
 {
     __shared__ float s_dt[KB];
     __shared__ float s_loss;
@@ -172,9 +138,12 @@ __global__ void k_loss_grad(int layer, const float *__restrict__ theta0, const f
         softmax32(z, q);
         const float xv = j < n ? x[3ll * j + layer] : 0.5f;
         const int b = min((int)(xv * KB), KB - 1);
-        if (ww != 0.0f) atomicAdd(&s_loss, -ww * logf(KB * q[b]));
+        // d log Q_b / d z_k = r (delta_bk - s_k), r = (1 - mix) s_b / Q_b (1 without mixing)
+        const float Qb = mixed(q[b], mix);
+        const float r = mix != 0.0f ? (1.0f - mix) * q[b] / Qb : 1.0f;
+        if (ww != 0.0f) atomicAdd(&s_loss, -ww * logf(KB * Qb));
         for (int k = 0; k < KB; ++k) {
-            const float g = -ww * ((k == b ? 1.0f : 0.0f) - q[k]);
+            const float g = -ww * r * ((k == b ? 1.0f : 0.0f) - q[k]);
             if (layer == 0) {
                 if (ww != 0.0f) atomicAdd(&s_dt[k], g);
             } else {
@@ -280,6 +249,8 @@ int check_warp(const qmcrt_warp *w)
     if (!w->d_params || !w->d_weights || !w->d_weights_t) return set_error(QMCRT_ERR_INVALID_ARG, "NULL warp buffers");
     if (((uintptr_t)w->d_weights | (uintptr_t)w->d_weights_t) & 15)
         return set_error(QMCRT_ERR_INVALID_ARG, "warp weights must be 16-byte aligned");
+    if (!(w->uniform_mix >= 0.0f && w->uniform_mix < 1.0f))
+        return set_error(QMCRT_ERR_INVALID_ARG, "uniform_mix must lie in [0, 1)");
     return QMCRT_OK;
 }
 
@@ -310,28 +281,15 @@ int qmcrt_warp_sync(const qmcrt_warp *warp, void *stream)
 int qmcrt_warp_forward(const qmcrt_warp *warp, const float *d_u, float *d_x, float *d_logj, uint64_t n,
                        void *d_workspace, uint64_t workspace_bytes, void *stream)
 {
+    (void)d_workspace;
+    (void)workspace_bytes;
     int rc = check_warp(warp);
     if (rc) return rc;
-    if (!d_u || !d_x || !d_logj || !d_workspace) return set_error(QMCRT_ERR_INVALID_ARG, "NULL buffer");
-    const int R = rows_for(workspace_bytes);
-    if (R < 128) return set_error(QMCRT_ERR_INVALID_ARG, "workspace below one pass of 128 rows");
-    cudaStream_t s = (cudaStream_t)stream;
-    const Work W0 = carve(d_workspace, R);
-    for (uint64_t base = 0; base < n; base += (uint64_t)R) {
-        const int cnt = (int)std::min<uint64_t>((uint64_t)R, n - base);
-        Work W = W0;
-        W.rows = (int)round128(cnt);
-        const float *u = d_u + 3 * base;
-        float *x = d_x + 3 * base, *lj = d_logj + base;
-        k_sample<<<blocks(cnt), 256, 0, s>>>(0, warp->d_params, nullptr, u, x, lj, cnt);
-        for (int m = 0; m < 2; ++m) {
-            k_features<<<blocks((long long)W.rows * WD), 256, 0, s>>>(x, cnt, W.rows, m, W.F, nullptr);
-            if ((rc = launch_status("warp features"))) return rc;
-            if ((rc = mlp_forward(warp, W, m, false, s))) return rc;
-            k_sample<<<blocks(cnt), 256, 0, s>>>(m + 1, warp->d_params, W.L, u, x, lj, cnt);
-            if ((rc = launch_status("warp sample"))) return rc;
-        }
-    }
+    if (!d_u || !d_x || !d_logj) return set_error(QMCRT_ERR_INVALID_ARG, "NULL buffer");
+    cudaError_t e = launch_warp_forward_fused(warp->d_params, (const __nv_bfloat16 *)warp->d_weights, d_u, d_x,
+                                              d_logj, (long long)n, warp->uniform_mix, warp->d_error,
+                                              (cudaStream_t)stream);
+    if (e != cudaSuccess) return set_error(QMCRT_ERR_CUDA, "warp forward: %s", cudaGetErrorString(e));
     return QMCRT_OK;
 }
 
@@ -355,12 +313,12 @@ int qmcrt_warp_grad(const qmcrt_warp *warp, const float *d_x, const float *d_w, 
         W.rows = (int)round128(cnt);
         const float *x = d_x + 3 * base, *w = d_w + base;
         k_loss_grad<<<(W.rows + 255) / 256, 256, 0, s>>>(0, warp->d_params, nullptr, x, w, cnt, W.rows, W.wsum, d_loss,
-                                                          d_grad, nullptr, nullptr);
+                                                          d_grad, nullptr, nullptr, warp->uniform_mix);
         for (int m = 0; m < 2; ++m) {
             k_features<<<blocks((long long)W.rows * WD), 256, 0, s>>>(x, cnt, W.rows, m, W.F, W.Ft);
             if ((rc = mlp_forward(warp, W, m, true, s))) return rc;
             k_loss_grad<<<(W.rows + 255) / 256, 256, 0, s>>>(m + 1, warp->d_params, W.L, x, w, cnt, W.rows, W.wsum,
-                                                              d_loss, d_grad, W.dL, W.dLt);
+                                                              d_loss, d_grad, W.dL, W.dLt, warp->uniform_mix);
             if ((rc = launch_status("warp loss"))) return rc;
             const int splits = std::max(1, W.rows / 2048);
             // layer 3: signal dL [rows x 32]

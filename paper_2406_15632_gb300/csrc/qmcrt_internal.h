@@ -110,6 +110,9 @@ struct TraceP {
     uint64_t first;    // first point index
     uint64_t count;    // packets
     double *log;       // optional [count][9]
+    const float *warp_x;     // optional [count][3]: first-order coordinates (learned warp)
+    const float *warp_logj;  // [count] log |dx/du| of warp_x (multiplies the packet weight)
+    float *train_log;        // optional [count][4]: coordinates used, total peel-off intensity
     int max_orders, force_all, per_order;
     T rr_threshold, rr_survival, inv_rr_survival;
 };
@@ -131,6 +134,10 @@ cudaError_t launch_trace_batch_f64(const TraceP<double> &p, const NetTables &tab
 cudaError_t launch_batch_reduce(const long long *acc, const qmcrt_instance *inst, int n_inst, size_t per_inst,
                                 double frac_scale, double *out, cudaStream_t s);
 int batch_occupancy(int block, int precision);
+
+// Forward pass of the learned warp, both conditionals fused on the tensor cores.
+cudaError_t launch_warp_forward_fused(const float *params, const __nv_bfloat16 *wb, const float *u, float *x,
+                                      float *logj, long long n, float mix, int *error, cudaStream_t s);
 cudaError_t launch_generate_points(const PointsP &p, uint64_t first, uint64_t count, int format, void *out,
                                    cudaStream_t s);
 cudaError_t launch_pad_grid(const float *k, int nx, int ny, int nz, int pad, float *out, cudaStream_t s);

@@ -1,8 +1,11 @@
 // qmcrt_trace_multiple.cu -- multiple-scattering tracer kernel (Sec. 3.5, 3.7).
 //
 // One thread per packet, the same warp-coherent packet mapping as the single-
-// scattering kernel.  Order k reads coordinates 4(k-1) + {0 azimuth, 1 cos Theta,
-// 2 depth, 3 roulette}; the order loop is uniform across the warp so deposits stay
+// scattering kernel.  With a learned warp the first-order coordinates come from a
+// buffer (x = T(u) and log |dx/du| per packet); the optional training log records,
+// per packet, the coordinates used and the packet's total peel-off intensity.
+// Order k reads coordinates 4(k-1) + {0 azimuth, 1 cos Theta, 2 depth, 3 roulette};
+// the order loop is uniform across the warp so deposits stay
 // convergent, and the warp leaves the loop once all its packets are done.
 #include "qmcrt_device.cuh"
 
@@ -13,16 +16,25 @@ __global__ void __launch_bounds__(256) k_trace_multiple(const __grid_constant__ 
 {
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if ((tid & ~31ull) >= P.ord.threads) return;  // uniform per warp
-    uint64_t i;
+    uint64_t i = P.first;
     const bool live_index = packet_index(P.ord, P.first, P.count, tid, i);
     if (!__any_sync(FULL_MASK, live_index)) return;
     bool alive = live_index;
     T pos[3] = {T(0), T(0), T(0)}, n[3] = {T(0), T(0), T(1)}, a[3] = {T(1), T(0), T(0)};
     T S[3] = {T(0), T(0), T(0)};
-    T wd = T(0);
+    T wd = T(0), total = T(0);
+    const uint64_t j = i - P.first;
     if (alive) {
         T wgt;
-        wd = emit(P, i, pos, n, a, wgt);
+        if (P.warp_x) {  // learned proposal: first-order coordinates and their Jacobian
+            T sp, cp;
+            direction_from((T)P.warp_x[3 * j], (T)P.warp_x[3 * j + 1], n, a, sp, cp);
+            pos[0] = pos[1] = pos[2] = T(0);
+            wd = (T)P.warp_x[3 * j + 2];
+            wgt = Mth<T>::exp_((T)P.warp_logj[j]);
+        } else {
+            wd = emit(P, i, pos, n, a, wgt);
+        }
         S[0] = wgt;
     }
     for (int k = 1; k <= P.max_orders; ++k) {
@@ -53,6 +65,7 @@ __global__ void __launch_bounds__(256) k_trace_multiple(const __grid_constant__ 
                 S[1] *= P.dust.albedo;
                 S[2] *= P.dust.albedo;
                 contrib = peel_polarized(P, pos, n, a, S, out, x, y);
+                if (contrib) total += out[0];
             }
         }
         splat(P, contrib, P.per_order ? k - 1 : 0, x, y, out);
@@ -69,6 +82,19 @@ __global__ void __launch_bounds__(256) k_trace_multiple(const __grid_constant__ 
                 }
             }
         }
+    }
+    if (P.train_log && live_index) {
+        float *r = P.train_log + 4 * j;
+        if (P.warp_x) {
+            r[0] = P.warp_x[3 * j];
+            r[1] = P.warp_x[3 * j + 1];
+            r[2] = P.warp_x[3 * j + 2];
+        } else {
+            r[0] = (float)point<T>(P.pts, i, 0);
+            r[1] = (float)point<T>(P.pts, i, 1);
+            r[2] = (float)point<T>(P.pts, i, 2);
+        }
+        r[3] = (float)total;
     }
 }
 

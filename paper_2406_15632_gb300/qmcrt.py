@@ -94,7 +94,7 @@ class qmcrt_gemm_epilogue(C.Structure):
 
 
 class qmcrt_warp(C.Structure):
-    _fields_ = [("struct_size", C.c_uint32), ("reserved", C.c_int32), ("d_params", C.c_void_p),
+    _fields_ = [("struct_size", C.c_uint32), ("uniform_mix", C.c_float), ("d_params", C.c_void_p),
                 ("d_weights", C.c_void_p), ("d_weights_t", C.c_void_p), ("d_error", C.c_void_p)]
 
 
@@ -127,6 +127,9 @@ _SIGS = [
                                        _P(qmcrt_points_desc), _P(qmcrt_trace_opts), _P(qmcrt_image), C.c_void_p]),
     ("qmcrt_image_reduce", C.c_int, [_P(qmcrt_image), C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_void_p,
                                      C.c_void_p]),
+    ("qmcrt_trace_multiple_warped", C.c_int, [_P(qmcrt_medium), _P(qmcrt_source), _P(qmcrt_dust),
+                                              _P(qmcrt_observer), _P(qmcrt_points_desc), _P(qmcrt_trace_opts),
+                                              C.c_void_p, C.c_void_p, _P(qmcrt_image), C.c_void_p, C.c_void_p]),
     ("qmcrt_batch_workspace_bytes", C.c_uint64, [C.c_int32]),
     ("qmcrt_trace_batch", C.c_int, [_P(qmcrt_medium), _P(qmcrt_source), _P(qmcrt_observer), _P(qmcrt_points_desc),
                                     _P(qmcrt_trace_opts), C.c_void_p, C.c_int32, _P(qmcrt_batch_config), C.c_void_p,
@@ -258,7 +261,7 @@ class Warp:
     """Device state of the learned warp: FP32 parameters, their bf16 copies, Adam
     moments, a workspace for `rows` samples per pass, and an error word."""
 
-    def __init__(self, params=None, *, rows: int = 1 << 16, seed: int = 0):
+    def __init__(self, params=None, *, rows: int = 1 << 16, seed: int = 0, uniform_mix: float = 0.0):
         torch = _torch()
         if params is None:
             params = self.initial(seed)
@@ -268,7 +271,7 @@ class Warp:
         self.wt = torch.zeros(WARP_BF16_WEIGHTS, dtype=torch.bfloat16, device="cuda")
         self.error = torch.zeros(1, dtype=torch.int32, device="cuda")
         self.desc = _new(qmcrt_warp, d_params=self.params.data_ptr(), d_weights=self.wb.data_ptr(),
-                         d_weights_t=self.wt.data_ptr(), d_error=self.error.data_ptr())
+                         d_weights_t=self.wt.data_ptr(), d_error=self.error.data_ptr(), uniform_mix=uniform_mix)
         self.ws_bytes = qmcrt_warp_workspace_bytes(rows)
         self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device="cuda")
         self.m = torch.zeros_like(self.params)
@@ -297,8 +300,11 @@ class Warp:
         n = u.shape[0]
         x = torch.empty((n, 3), dtype=torch.float32, device="cuda")
         lj = torch.empty(n, dtype=torch.float32, device="cuda")
-        qmcrt_warp_forward(self.desc, u.data_ptr(), x.data_ptr(), lj.data_ptr(), n, self.ws.data_ptr(), self.ws_bytes,
-                           _stream(stream))
+        return self.forward_into(u, x, lj, stream)
+
+    def forward_into(self, u, x, lj, stream=None):
+        qmcrt_warp_forward(self.desc, u.data_ptr(), x.data_ptr(), lj.data_ptr(), u.shape[0], self.ws.data_ptr(),
+                           self.ws_bytes, _stream(stream))
         return x, lj
 
     def gradient(self, x, w, stream=None):
@@ -314,17 +320,21 @@ class Warp:
         opt = _new(qmcrt_adam, step=self.step, lr=lr, beta1=beta1, beta2=beta2, eps=eps)
         qmcrt_warp_adam(self.desc, self.grad.data_ptr(), self.m.data_ptr(), self.v.data_ptr(), opt, _stream(stream))
 
-    def train(self, x, w, *, epochs: int = 4, batch: int = 1 << 16, lr: float = 2e-3, seed: int = 0):
-        """Minibatch Adam over the logged samples; returns the loss per step."""
+    def train(self, x, w, *, epochs: int = 4, batch: int = 1 << 16, lr: float = 2e-3):
+        """Minibatch Adam over the logged samples; returns the loss per step.
+
+        Minibatches are contiguous slices of the log.  A log written in point order by
+        a low-discrepancy set needs no shuffle: every aligned block of 2^m consecutive
+        Sobol points is itself a net, so each minibatch already covers the cube evenly.
+        Epoch e starts at slice e (mod the slice count)."""
         torch = _torch()
-        g = torch.Generator(device="cuda").manual_seed(seed)
         n = x.shape[0]
+        nb = n // batch
         losses = []
-        for _ in range(epochs):
-            perm = torch.randperm(n, generator=g, device="cuda")
-            for b0 in range(0, n - batch + 1, batch):
-                idx = perm[b0:b0 + batch]
-                loss, _ = self.gradient(x[idx].contiguous(), w[idx].contiguous())
+        for e in range(epochs):
+            for k in range(nb):
+                b0 = ((e + k) % nb) * batch
+                loss, _ = self.gradient(x[b0:b0 + batch], w[b0:b0 + batch])
                 losses.append(loss.clone())
                 self.adam_step(lr=lr)
         return torch.cat(losses).cpu().tolist() if losses else []
@@ -332,6 +342,14 @@ class Warp:
 
 def qmcrt_pad_grid(d_k: int, nx: int, ny: int, nz: int, pad: int, d_padded: int, stream: int = 0) -> None:
     _check(load().qmcrt_pad_grid(C.c_void_p(d_k), nx, ny, nz, pad, C.c_void_p(d_padded), C.c_void_p(stream)))
+
+
+def qmcrt_trace_multiple_warped(medium, source, dust, obs, pts, opts, d_x: int, d_logj: int, image,
+                                d_train_log: int = 0, stream: int = 0) -> None:
+    _check(load().qmcrt_trace_multiple_warped(C.byref(medium), C.byref(source), C.byref(dust), C.byref(obs),
+                                              C.byref(pts), C.byref(opts), C.c_void_p(d_x or None),
+                                              C.c_void_p(d_logj or None), C.byref(image),
+                                              C.c_void_p(d_train_log or None), C.c_void_p(stream)))
 
 
 def qmcrt_image_reduce(image, nx: int, ny: int, n_replicas: int, scale: float, d_out: int, stream: int = 0) -> None:
@@ -382,20 +400,30 @@ def generate_points(kind: str, dims: int, first: int, count: int, fmt: str = "f6
 
 
 def contribution_bound(prob: scenes.Problem) -> float:
-    """Upper bound on |I|, |Q|, |U| of one peel-off contribution: source weight x
-    max P11/(4 pi) x polarization growth over the orders (factor 1 + p_l each)."""
+    """Upper bound on |I|, |Q|, |U| of one peel-off contribution.
+
+    The packet weight starts at the source weight (limb-darkening factor at most
+    1 / (1 - u/3)).  Each scattering multiplies I by the albedo, by the forcing weight
+    (at most 1) and by 1 + (P12/P11)(Q/I) <= 1 + p_l, since |Q| <= I holds for the
+    carried Stokes vector; the peel-off of order k adds the phase function (at most
+    (1 + |g|) / (4 pi (1 - |g|)^2)) and once more at most 1 + p_l.  Roulette resets a
+    weight below the threshold to at most threshold / survival.  So a contribution of
+    order k is below limb * p_max * max(1, thr / surv) * (albedo (1 + p_l))^k, taken
+    at its largest k <= max_orders."""
     g = abs(prob.g)
-    p11 = (1 + g) / ((1 - g) ** 2)
+    p_max = (1 + g) / ((1 - g) ** 2) / (4 * math.pi)
     limb = 1.0 / (1.0 - prob.limb_u / 3.0) if prob.source == "sphere" else 1.0
-    growth = (1 + prob.p_l) ** max(prob.max_orders - 1, 0)
-    rr = 1.0 / prob.rr_survival if prob.rr_threshold > 0 else 1.0
-    return limb * p11 / (4 * math.pi) * min(growth, 2.0 ** 20) * max(rr * prob.rr_threshold, 1.0)
+    step = prob.albedo * (1 + prob.p_l)
+    growth = max(step ** k for k in range(1, max(prob.max_orders, 1) + 1))
+    rr = max(1.0, prob.rr_threshold / prob.rr_survival) if prob.rr_threshold > 0 else 1.0
+    return limb * p_max * growth * rr
 
 
-def default_frac_bits(prob: scenes.Problem, n_contributions: int) -> int:
-    """Largest fixed-point scale that cannot overflow: n * bound * 2^F < 2^62."""
+def default_frac_bits(prob: scenes.Problem, n_contributions: int, weight_bound: float = 1.0) -> int:
+    """Largest fixed-point scale that cannot overflow: n * bound * 2^F < 2^62.
+    weight_bound multiplies the bound (mix^-3 for a warp with a uniform mixture)."""
     n = max(int(n_contributions), 1) * max(prob.max_orders if not prob.per_order else 1, 1)
-    need = math.log2(n * contribution_bound(prob))
+    need = math.log2(n * contribution_bound(prob) * weight_bound)
     return int(max(0, min(62, math.floor(62 - need))))
 
 
@@ -470,6 +498,17 @@ class Scene:
             qmcrt_trace_single(self.medium, self.source, self.dust, self.obs, pts, self.opts(precision, block_size),
                                img, log.data_ptr() if log is not None else 0, _stream(stream))
 
+    def trace_warped(self, first: int, count: int, buf, *, x=None, logj=None, train_log=None, accum: str = "i64",
+                     frac_bits: int = 0, precision: str = "f32", stream=None) -> None:
+        """Multiple scattering with the first-order coordinates of packet j taken from
+        x[j] (weight times exp(logj[j])); optionally log (x, total intensity) per packet."""
+        p = self.prob
+        pts = points_desc(p.generator, p.dims, first, count, "f64", p.seed, p.total_n)
+        img = self.image_desc(buf, accum, frac_bits)
+        ptr = lambda t: t.data_ptr() if t is not None else 0
+        qmcrt_trace_multiple_warped(self.medium, self.source, self.dust, self.obs, pts, self.opts(precision), ptr(x),
+                                    ptr(logj), img, ptr(train_log), _stream(stream))
+
     def reduce(self, buf, scale: float, *, accum: str = "i64", frac_bits: int = 0, out=None, stream=None):
         torch = _torch()
         if out is None:
@@ -493,6 +532,49 @@ def render(prob: scenes.Problem, n_packets: int, first: int = 1, *, precision: s
     sc.trace(first, n_packets, buf, accum=accum, frac_bits=fb, precision=precision, log=lg)
     img = sc.reduce(buf, 1.0 / n_packets if scale is None else scale, accum=accum, frac_bits=fb)
     return (img, lg) if log else img
+
+
+class LearnedTracer:
+    """Multiple scattering with the learned proposal on the first-order coordinates.
+
+    Per chunk of packets: the point kernel writes the first three coordinates u (FP32),
+    the warp maps them to x = T(u) with log |dx/du| on the tensor cores, and the tracer
+    reads x and multiplies each packet's weight by |dx/du|.  With warp = None the same
+    loop runs the plain tracer (and can still write the training log)."""
+
+    def __init__(self, scene: "Scene", warp: "Warp | None", *, chunk: int = 1 << 22):
+        torch = _torch()
+        self.scene, self.warp, self.chunk = scene, warp, chunk
+        self.u = torch.empty((chunk, 3), dtype=torch.float32, device="cuda")
+        self.x = torch.empty((chunk, 3), dtype=torch.float32, device="cuda")
+        self.lj = torch.empty(chunk, dtype=torch.float32, device="cuda")
+
+    def weight_bound(self) -> float:
+        """Bound on |dx/du| (1 without a warp; mix^-3 with a uniform mixture)."""
+        if self.warp is None:
+            return 1.0
+        mix = self.warp.desc.uniform_mix
+        return mix ** -3 if mix > 0 else math.inf
+
+    def trace(self, first: int, count: int, buf, *, frac_bits: int = 0, accum: str = "f64", precision: str = "f32",
+              train_log=None, stream=None) -> None:
+        """Add packets first..first+count-1 to buf.  FP64 accumulation is the default
+        here: a fixed-point scale must leave room for the largest Jacobian weight."""
+        p = self.scene.prob
+        if accum == "i64" and math.isinf(self.weight_bound()):
+            raise QmcrtError(ERR_INVALID_ARG, "fixed-point accumulation needs a bounded warp (uniform_mix > 0)")
+        for c0 in range(0, count, self.chunk):
+            n = min(self.chunk, count - c0)
+            log = train_log[c0:c0 + n] if train_log is not None else None
+            if self.warp is None:
+                self.scene.trace_warped(first + c0, n, buf, train_log=log, accum=accum, frac_bits=frac_bits,
+                                        precision=precision, stream=stream)
+                continue
+            u, x, lj = self.u[:n], self.x[:n], self.lj[:n]
+            generate_points(p.generator, 3, first + c0, n, "f32", p.seed, p.total_n, out=u, stream=stream)
+            self.warp.forward_into(u, x, lj, stream=stream)
+            self.scene.trace_warped(first + c0, n, buf, x=x, logj=lj, train_log=log, accum=accum,
+                                    frac_bits=frac_bits, precision=precision, stream=stream)
 
 
 class HostRenderer:
@@ -554,7 +636,7 @@ class Batch:
         self.ws = torch.zeros(self.ws_bytes // 8, dtype=torch.int64, device="cuda")
         self.accum = torch.zeros((self.n, 3, prob.ny, prob.nx), dtype=torch.int64, device="cuda")
         self.out = torch.zeros((self.n, 3, prob.ny, prob.nx), dtype=torch.float64, device="cuda")
-        bound_prob = prob.replace(g=max(abs(I.g) for I in instances))
+        bound_prob = prob.replace(g=max(abs(I.g) for I in instances), albedo=max(I.albedo for I in instances))
         self.frac_bits = default_frac_bits(bound_prob, max(self.counts)) if frac_bits is None else frac_bits
         self.graph = None
         self.set_config(chunk_log2, block_size, ctas_per_sm, packets_per_thread)

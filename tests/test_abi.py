@@ -5,6 +5,7 @@ import ctypes as C
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2406_15632_gb300 import build as B
@@ -160,6 +161,37 @@ def test_default_frac_bits_never_overflows():
         fb = Q.default_frac_bits(prob, n)
         assert 0 <= fb <= 62
         assert n * Q.contribution_bound(prob) * prob.max_orders * 2.0 ** fb < 2.0 ** 63
+
+
+@pytest.mark.parametrize("g,albedo,p_l", [(0.6, 0.7, 0.5), (-0.4, 1.0, 1.0), (0.0, 0.9, 0.3)])
+def test_contribution_bound_holds_through_scattering_and_peel_off(g, albedo, p_l):
+    """Random packets pushed through the oracle's scattering and peel-off steps: no
+    contribution of order k exceeds the bound of a problem with k orders, and the
+    bound is reached within a factor of a few at the first order (it is tight where
+    the fixed-point scale needs it)."""
+    from oracle import oracle as O
+    from paper_2406_15632_gb300 import scenes as S
+
+    rng = np.random.default_rng(3)
+    K = 6
+    prob = S.homogeneous_sphere_problem(sphere_k=1e-9, g=g, albedo=albedo, p_l=p_l, max_orders=K)
+    worst = np.zeros(K + 1)
+    for _ in range(300):
+        n = rng.normal(size=3)
+        n /= np.linalg.norm(n)
+        a = np.cross(n, [0.0, 0.0, 1.0]) if abs(n[2]) < 0.9 else np.cross(n, [1.0, 0.0, 0.0])
+        a /= np.linalg.norm(a)
+        S3 = np.array([1.0, 0.0, 0.0])
+        for k in range(1, K + 1):
+            if k > 1:
+                n, a, S3 = O.scatter_packet(prob, rng.uniform(), rng.uniform(), n, a, S3)
+            S3 = S3 * albedo  # forcing weight <= 1 taken as 1
+            ok, out = O.peel_packet(prob, [0.0, 0.0, 0.0], n, a, S3)
+            if ok:
+                worst[k] = max(worst[k], np.abs(out[:3]).max())
+    for k in range(1, K + 1):
+        assert worst[k] <= Q.contribution_bound(prob.replace(max_orders=k)) * (1 + 1e-12), k
+    assert worst[1] >= 0.05 * Q.contribution_bound(prob.replace(max_orders=1))
 
 
 def test_batch_validation(lib):

@@ -59,20 +59,20 @@ def test_density_integrates_to_one_exactly():
     assert np.allclose(Q2.sum(axis=1), 1.0) and np.allclose(Q1.sum(axis=1), 1.0)
 
 
-@pytest.mark.parametrize("use_bf16", [False, True])
-def test_gradient_matches_finite_differences(use_bf16):
+@pytest.mark.parametrize("use_bf16,mix", [(False, 0.0), (True, 0.0), (False, 0.2)])
+def test_gradient_matches_finite_differences(use_bf16, mix):
     rng = np.random.default_rng(5)
     vec = F.init_params(6, scale=1.5)
     x = rng.uniform(size=(64, 3))
     w = rng.uniform(0.1, 2.0, size=64)
-    loss, g = F.loss_and_grad(x, w, vec)
+    loss, g = F.loss_and_grad(x, w, vec, mix=mix)
     idx = rng.choice(F.N_PARAMS, size=40, replace=False)
     idx = np.concatenate([idx, [0, 5, F.LAYOUT["b03"][0], F.LAYOUT["W13"][0] + 7]])
     for i in idx:
         h = 1e-6
         e = np.zeros(F.N_PARAMS)
         e[i] = h
-        fd = (F.loss_and_grad(x, w, vec + e)[0] - F.loss_and_grad(x, w, vec - e)[0]) / (2 * h)
+        fd = (F.loss_and_grad(x, w, vec + e, mix=mix)[0] - F.loss_and_grad(x, w, vec - e, mix=mix)[0]) / (2 * h)
         assert g[i] == pytest.approx(fd, rel=1e-5, abs=1e-8)
     if use_bf16:
         lb, gb = F.loss_and_grad(x, w, vec, use_bf16=True)
@@ -110,3 +110,26 @@ def test_adam_definition_on_a_quadratic():
     v = np.zeros(2)
     new, m, v = F.adam(vec, 2 * vec, m, v, 1, lr=0.1)
     assert np.allclose(new, vec - 0.1 * np.sign(vec))  # first step: m_hat/sqrt(v_hat) = sign(g)
+
+
+def test_uniform_mixture_bounds_the_jacobian_and_stays_a_bijection():
+    """With bin masses (1 - mix) softmax + mix / 32 every conditional density is at
+    least mix, so |dx/du| <= mix^-3, even for a sharply peaked network; the warp
+    still inverts through the CDFs and log |dx/du| = -log q(x)."""
+    mix = 0.1
+    vec = F.init_params(9, scale=8.0)
+    p = F.unpack(vec)
+    p["theta0"] = np.zeros(F.K_BINS)
+    p["theta0"][3] = 40.0  # almost all of x0's mass in one bin without the mixture
+    vec = F.pack(p)
+    u = np.random.default_rng(10).uniform(size=(3000, 3))
+    x, logj = F.warp(u, vec, mix=mix)
+    assert np.all(logj <= -3 * np.log(mix) + 1e-12)
+    # without the mixture 1 / q is huge outside the peak (x0 in another bin)
+    assert (-F.log_density(u, vec)).max() > -3 * np.log(mix) + 10.0
+    assert (-F.log_density(u, vec, mix=mix)).max() <= -3 * np.log(mix) + 1e-12
+    for l, Q in enumerate(F.conditionals(x, vec, mix=mix)):
+        assert np.allclose(Q.sum(axis=1), 1.0)
+        assert Q.min() >= mix / F.K_BINS * (1 - 1e-12)
+        assert np.allclose(F.cdf(x[:, l], Q), u[:, l], atol=1e-12)
+    assert np.allclose(logj, -F.log_density(x, vec, mix=mix), atol=1e-12)

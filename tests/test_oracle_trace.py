@@ -278,3 +278,47 @@ def test_three_d_reuse_anti_pattern_does_not_converge():
     bad_small, bad_large = reuse_second_order(1 << 10), reuse_second_order(1 << 12)
     assert abs(bad_large - good) > 0.02 * good
     assert abs(bad_large - good) > 0.5 * abs(bad_small - good)
+
+
+def test_identity_warp_is_the_plain_tracer_and_logs_packet_totals():
+    """x = u with log J = 0 replays the plain multiple-scattering tracer exactly; the
+    training log holds the point's first coordinates, and its per-packet totals add up
+    to at least the image total (peel-offs that land outside the image are counted in
+    the log but not binned)."""
+    p = S.clumpy_problem(n=16, max_orders=6, nx=32, ny=32, half_width=0.6)
+    N = 1 << 12
+    u = O.generate_points("sobol", 3, 1, N)
+    plain = O.trace_multiple(p, 1, N)
+    img, log = O.trace_multiple_warped(p, 1, N, u, np.zeros(N), train_log=True)
+    assert np.array_equal(img, plain)
+    img2, log2 = O.trace_multiple_warped(p, 1, N, train_log=True)
+    assert np.array_equal(img2, plain) and np.array_equal(log2, log)
+    assert np.array_equal(log[:, :3], u)
+    assert np.all(log[:, 3] >= 0)
+    assert log[:, 3].sum() > img[0, 0].sum() * (1 + 1e-3)
+
+
+@pytest.mark.parametrize("use_jacobian", [True, False])
+def test_warped_estimator_keeps_energy_conservation(use_jacobian):
+    """A known bijection of the first-order coordinates (x1 = u1^2, x2 = u2^3, with
+    |dx/du| = 2 u1 * 3 u2^2) leaves the homogeneous-sphere energy balance
+    1 - e^{-k} intact when the weight carries the Jacobian, and breaks it when the
+    Jacobian is dropped."""
+    k = 0.6
+    p = S.homogeneous_sphere_problem(sphere_k=k, max_orders=30, albedo=1.0, g=0.0, generator="sobol")
+    N = 1 << 14
+    u = O.generate_points("sobol", 3, 1, N)
+    x = u.copy()
+    x[:, 1] = u[:, 1] ** 2
+    x[:, 2] = u[:, 2] ** 3
+    logj = np.log(2 * u[:, 1]) + np.log(3 * u[:, 2] ** 2) if use_jacobian else np.zeros(N)
+    tot = 0.0
+    dirs = [(math.pi / 2, 0.0), (0.3, 1.0), (2.2, 4.0), (1.0, 2.5)]
+    for th, ph in dirs:
+        img = O.trace_multiple_warped(p.replace(theta_obs=th, phi_obs=ph), 1, N, x, logj)
+        tot += 4 * math.pi * img[:, 0].sum() / N / len(dirs)
+    err = abs(tot / (1 - math.exp(-k)) - 1)
+    if use_jacobian:
+        assert err < 2e-3
+    else:
+        assert err > 5e-3
