@@ -197,6 +197,201 @@ def run_batched():
             "identical_images": same, "config": cfg, "tuned_over": best.get("tried")}
 
 
+def _timed(fn):
+    import torch
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    out = fn()
+    e1.record()
+    e1.synchronize()
+    return out, e0.elapsed_time(e1)
+
+
+def _norms(img, ref):
+    """(RMS relative = ||A - B||_2 / ||B||_2, L1 relative = sum |A - B| / sum |B|) of the I images."""
+    d = img - ref
+    return float(d.norm() / ref.norm()), float(d.abs().sum() / ref.abs().sum())
+
+
+def _time_at(points, target):
+    """Wall time at which an arm reaches `target` error: log-log interpolation between
+    the ladder points (time, error) that bracket it, else extrapolation along the last
+    two points (flagged)."""
+    pts = sorted(points)
+    for (t0, e0), (t1, e1) in zip(pts, pts[1:]):
+        if e0 >= target >= e1 and e0 > e1:
+            f = math.log(e0 / target) / math.log(e0 / e1)
+            return math.exp(math.log(t0) + f * math.log(t1 / t0)), False
+    (t0, e0), (t1, e1) = pts[-2], pts[-1]
+    if e1 >= e0:
+        return None, True
+    slope = math.log(t1 / t0) / math.log(e0 / e1)
+    return t1 * (e1 / target) ** slope, True
+
+
+def _reference_image(Q, prob, grid, render_log2, seeds, accum):
+    """Converged reference: mean of Owen-scrambled Sobol images with independent seeds,
+    and the estimated RMS error of that mean (sample variance across seeds / seeds)."""
+    import torch
+
+    imgs = []
+    for seed in seeds:
+        sc = Q.Scene(prob.replace(generator="sobol_owen", seed=seed), grid_device=grid)
+        n = 1 << render_log2
+        fb = Q.default_frac_bits(sc.prob, n) if accum == "i64" else 0
+        buf = sc.accum_buffer(accum)
+        sc.trace(1, n, buf, accum=accum, frac_bits=fb)
+        imgs.append(sc.reduce(buf, 1.0 / n, accum=accum, frac_bits=fb)[0, 0].clone())
+    stack = torch.stack(imgs)
+    ref = stack.mean(0)
+    var_of_mean = stack.var(0, unbiased=True).sum() / len(seeds)
+    return ref, float(var_of_mean.sqrt() / ref.norm()), len(seeds) << render_log2
+
+
+def _ladder(render, ladder, ref, ref_err):
+    rows = []
+    for lg in ladder:
+        img, ms = render(1 << lg)
+        rms, l1 = _norms(img, ref)
+        corr = math.sqrt(max(rms * rms - ref_err * ref_err, 0.0))
+        rows.append({"log2_n": lg, "ms": ms, "rms": rms, "rms_minus_reference": corr, "l1": l1})
+    return rows
+
+
+def _tte_summary(arms, targets, overhead_ms=None):
+    """Per target error and arm: render time at that error (log-log interpolation on the
+    ladder, or extrapolation along its last two points, flagged) plus the arm's fixed
+    overhead (training), in ms."""
+    overhead_ms = overhead_ms or {}
+    out = {}
+    for tgt in targets:
+        row = {}
+        for name, rows in arms.items():
+            pts = [(r["ms"], r["rms_minus_reference"]) for r in rows if r["rms_minus_reference"] > 0]
+            t, extrap = _time_at(pts, tgt) if len(pts) >= 2 else (None, True)
+            row[name] = {"ms": None if t is None else t + overhead_ms.get(name, 0.0), "extrapolated": extrap}
+        out[f"{tgt:g}"] = row
+    return out
+
+
+def run_time_to_error_learned(ladder=(20, 22, 24, 26), ref_log2=28, ref_seeds=(101, 102, 103, 104),
+                              n_log_log2=22, epochs=2, batch_log2=16, lr=3e-3, mix=0.1, weight="l2"):
+    """Clumpy envelope (128^3, total radial tau 5, 20 orders, roulette at 1e-4, 512x512
+    I/Q/U): wall time to a fixed RMS error of the I image for plain QMC (Sobol), the
+    learned proposal (warp trained on the tracer's own log of 2^22 plain packets, each
+    weighted by the L2 norm of its in-image contributions -- the density that minimises
+    the summed pixel variance is proportional to that norm; logging and training time
+    are added to every ladder point) and Philox MC.  All arms
+    accumulate in FP64.  The reference is the mean of four Owen-scrambled Sobol images
+    of 2^ref_log2 packets with independent seeds; its own estimated error is
+    subtracted in quadrature from each measured error."""
+    import torch
+
+    from paper_2406_15632_gb300 import qmcrt as Q
+    from paper_2406_15632_gb300 import scenes as S
+
+    prob = S.clumpy_problem(n=128)
+    sc = Q.Scene(prob)
+    ref, ref_err, ref_n = _reference_image(Q, prob, sc.grid, ref_log2, ref_seeds, "f64")
+    mc_sc = Q.Scene(prob.replace(generator="philox", seed=7), grid_device=sc.grid)
+    plain, mc = Q.LearnedTracer(sc, None), Q.LearnedTracer(mc_sc, None)
+
+    # training: log 2^22 plain packets (points 1 .. 2^22), minibatch Adam on the log
+    n_log = 1 << n_log_log2
+    log = torch.zeros((n_log, 5), dtype=torch.float32, device="cuda")
+    _, ms_log = _timed(lambda: plain.trace(1, n_log, sc.accum_buffer("f64"), train_log=log))
+    W = Q.Warp(seed=2, uniform_mix=mix)
+    xs, ws = log[:, :3].contiguous(), log[:, 4 if weight == "l2" else 3].contiguous()
+    losses, ms_train = _timed(lambda: W.train(xs, ws, epochs=epochs, batch=1 << batch_log2, lr=lr))
+    learned = Q.LearnedTracer(sc, W)
+
+    def renderer(tracer, s):
+        buf = s.accum_buffer("f64")
+        out = torch.empty((1, 3, prob.ny, prob.nx), dtype=torch.float64, device="cuda")
+
+        def render(n):
+            def go():
+                buf.zero_()
+                tracer.trace(n, n, buf)  # points n .. 2n-1: past the training log for n >= 2^22
+                s.reduce(buf, 1.0 / n, accum="f64", out=out)
+            _, ms = _timed(go)
+            return out[0, 0].clone(), ms
+        return render
+
+    for r in (renderer(plain, sc), renderer(learned, sc), renderer(mc, mc_sc)):
+        r(1 << 16)  # warm
+    arms = {"plain_qmc": _ladder(renderer(plain, sc), ladder, ref, ref_err),
+            "learned_qmc": _ladder(renderer(learned, sc), ladder, ref, ref_err),
+            "mc_philox": _ladder(renderer(mc, mc_sc), ladder, ref, ref_err)}
+    overhead = {"learned_qmc": ms_log + ms_train}
+    targets = (0.05, 0.03, 1e-2, 1e-3)
+    summary = _tte_summary(arms, targets, overhead)
+    for tgt, row in summary.items():
+        p, l, m = (row[k]["ms"] for k in ("plain_qmc", "learned_qmc", "mc_philox"))
+        row["learned_speedup_vs_plain"] = p / l if p and l else None
+        row["plain_qmc_speedup_vs_mc"] = m / p if p and m else None
+    return {"workload": "clumpy envelope 128^3 (radial tau 5, sigma 1 clumps), point source, 20 orders, forced, "
+                        "roulette 1e-4, g 0.6, albedo 0.7, 512x512 I/Q/U, FP32 trace, FP64 accumulate",
+            "error": "RMS relative of the I image (L1 relative also listed), against the reference",
+            "reference": {"packets": ref_n, "generator": "sobol_owen", "seeds": list(ref_seeds),
+                          "estimated_rms_error": ref_err},
+            "training": {"logged_packets": n_log, "log_ms": ms_log, "train_ms": ms_train, "epochs": epochs,
+                         "batch": 1 << batch_log2, "lr": lr, "uniform_mix": mix, "sample_weight": weight,
+                         "loss_first": losses[0], "loss_last": sum(losses[-8:]) / len(losses[-8:]),
+                         "warp_error_flag": int(W.error.item())},
+            "ladder": arms, "time_to_error_ms": summary}
+
+
+def run_time_to_error_disk(ladder=(20, 22, 24, 26), ref_log2=28, ref_seeds=(101, 102, 103, 104)):
+    """The paper's comparison on the single-scattering flared disk (256^3, 256x256
+    I/Q/U, 45 degrees): wall time to a fixed image error for Sobol, Owen-scrambled
+    Sobol, Halton, Hammersley (its own set of N points for every N) and Philox MC, all
+    through the same FP32 tracer with fixed-point accumulation."""
+    import torch
+
+    from paper_2406_15632_gb300 import qmcrt as Q
+
+    prob = workload_problem()
+    base = Q.Scene(prob)
+    ref, ref_err, ref_n = _reference_image(Q, prob, base.grid, ref_log2, ref_seeds, "i64")
+
+    def renderer(gen, seed=0):
+        out = torch.empty((1, 3, prob.ny, prob.nx), dtype=torch.float64, device="cuda")
+
+        def render(n):
+            p = prob.replace(generator=gen, seed=seed, total_n=n if gen == "hammersley" else 0)
+            s = Q.Scene(p, grid_device=base.grid)
+            fb = Q.default_frac_bits(p, n)
+            buf = s.accum_buffer("i64")
+            first = 1 if gen == "hammersley" else n
+
+            def go():
+                s.trace(first, n, buf, frac_bits=fb)
+                s.reduce(buf, 1.0 / n, frac_bits=fb, out=out)
+            _, ms = _timed(go)
+            return out[0, 0].clone(), ms
+        return render
+
+    gens = {"sobol": ("sobol", 0), "sobol_owen": ("sobol_owen", 1), "halton": ("halton", 0),
+            "hammersley": ("hammersley", 0), "mc_philox": ("philox", 7)}
+    for g, sd in gens.values():
+        renderer(g, sd)(1 << 16)
+    arms = {k: _ladder(renderer(g, sd), ladder, ref, ref_err) for k, (g, sd) in gens.items()}
+    summary = _tte_summary(arms, (0.05, 0.02, 1e-2, 3e-3))
+    for tgt, row in summary.items():
+        m = row["mc_philox"]["ms"]
+        for k in gens:
+            if k != "mc_philox" and row[k]["ms"] and m:
+                row[k]["speedup_vs_mc"] = m / row[k]["ms"]
+    return {"workload": "flared disk 256^3 single scattering, point source, 256x256 I/Q/U, FP32 trace, int64 accumulate",
+            "error": "RMS relative of the I image (L1 relative, the paper's norm, also listed)",
+            "reference": {"packets": ref_n, "generator": "sobol_owen", "seeds": list(ref_seeds),
+                          "estimated_rms_error": ref_err},
+            "ladder": arms, "time_to_error_ms": summary}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -352,6 +547,8 @@ def main():
     }
     if world == 1 and not args.no_extras:
         line["batched"] = run_batched()
+        line["time_to_error"] = {"learned_vs_plain": run_time_to_error_learned(),
+                                 "qmc_vs_mc_disk": run_time_to_error_disk()}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = run_cpu_baseline()
     print(json.dumps(line), flush=True)

@@ -356,9 +356,11 @@ int qmcrt_pad_grid(const float *d_k, int32_t nx, int32_t ny, int32_t nz, int32_t
  * theta and first depth) from d_x[j][3] (x = T(u) from qmcrt_warp_forward) and
  * multiplies its weight by exp(d_logj[j]) = |dx/du|, which keeps the estimator
  * unbiased; the other orders read the point set as usual.  With d_x = d_logj = NULL
- * it is qmcrt_trace_multiple.  d_train_log (optional, device float [count][4]):
- * per packet the first-order coordinates used and the packet's total peel-off
- * intensity summed over orders -- the samples and weights qmcrt_warp_grad trains on.
+ * it is qmcrt_trace_multiple.  d_train_log (optional, device float [count][5]): per
+ * packet the first-order coordinates used, then two norms of the Stokes-I
+ * contributions its peel-offs put into the image over all orders: their sum and the
+ * square root of their sum of squares -- the samples and weights qmcrt_warp_grad
+ * trains on (weights include |dx/du|, i.e. f / q of the proposal that drew them).
  * Errors: as qmcrt_trace_multiple; INVALID_ARG if only one of d_x, d_logj is given;
  * UNSUPPORTED for a warp with a sphere source.
  */

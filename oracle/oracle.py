@@ -264,13 +264,14 @@ def trace_multiple_warped(prob, first: int, count: int, x=None, logj=None, train
                           nthreads: int | None = None):
     """Multiple scattering with the first-order coordinates of packet j set to x[j]
     and its weight multiplied by exp(logj[j]).  Returns the raw image sums and, if
-    asked, the per-packet log [count][4] (coordinates, total peel-off intensity)."""
+    asked, the per-packet log [count][5] (coordinates; sum and L2 norm of the in-image
+    peel-off intensities)."""
     h = _Holder(prob)
     img = np.zeros((prob.n_images, 3, prob.ny, prob.nx), dtype=np.float64)
     dp = C.POINTER(C.c_double)
     xa = None if x is None else np.ascontiguousarray(x, dtype=np.float64).reshape(count, 3)
     la = None if logj is None else np.ascontiguousarray(logj, dtype=np.float64).reshape(count)
-    tl = np.zeros((count, 4), dtype=np.float64) if train_log else None
+    tl = np.zeros((count, 5), dtype=np.float64) if train_log else None
     ptr = lambda a: a.ctypes.data_as(dp) if a is not None else None
     rc = lib().or_trace_multiple_warped(h.ptr, first, count, ptr(xa), ptr(la), img.ctypes.data_as(dp), ptr(tl),
                                         nthreads or default_threads())

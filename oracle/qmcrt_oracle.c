@@ -682,7 +682,7 @@ typedef struct {
     double *log;
     int multiple;
     const double *wx, *wlogj; /* optional learned warp: first-order coordinates, log |dx/du| */
-    double *tlog;             /* optional [count][4]: coordinates used, total peel-off I */
+    double *tlog;             /* optional [count][5]: coordinates used, sum and L2 norm of in-image I */
 } or_job;
 
 static void or_trace_single_range(const or_problem *Pr, uint64_t first, uint64_t count, double *img,
@@ -759,7 +759,7 @@ static void or_trace_multiple_range(const or_problem *Pr, uint64_t first, uint64
     size_t img_size = (size_t)3 * Pr->obs.nx * Pr->obs.ny;
     for (uint64_t j = 0; j < count; ++j) {
         uint64_t i = first + j;
-        double pos[3], n[3], a[3], wgt, w, total = 0.0;
+        double pos[3], n[3], a[3], wgt, w, total = 0.0, total2 = 0.0;
         double x0 = or_point_f64(&Pr->points, i, 0), x1 = or_point_f64(&Pr->points, i, 1);
         if (wx) {
             /* Learned proposal: the first-order coordinates are x = T(u), and the
@@ -798,7 +798,11 @@ static void or_trace_multiple_range(const or_problem *Pr, uint64_t first, uint64
             double out[3], x, y;
             if (or_peel(Pr, &V, pos, n, a, S, out, &x, &y)) {
                 or_splat(&Pr->obs, img + (Pr->per_order ? (size_t)(k - 1) * img_size : 0), x, y, out);
-                total += out[0];
+                double hw = Pr->obs.half_width;
+                if (x >= -hw && x < hw && y >= -hw && y < hw) {
+                    total += out[0];
+                    total2 += out[0] * out[0];
+                }
             }
             if (k == Pr->max_orders) break;
             if (S[0] < Pr->rr_threshold) {
@@ -811,10 +815,11 @@ static void or_trace_multiple_range(const or_problem *Pr, uint64_t first, uint64
             }
         }
         if (tlog) {
-            tlog[4 * j] = x0;
-            tlog[4 * j + 1] = x1;
-            tlog[4 * j + 2] = w_first;
-            tlog[4 * j + 3] = total;
+            tlog[5 * j] = x0;
+            tlog[5 * j + 1] = x1;
+            tlog[5 * j + 2] = w_first;
+            tlog[5 * j + 3] = total;
+            tlog[5 * j + 4] = sqrt(total2);
         }
     }
 }
@@ -850,7 +855,7 @@ static int or_trace(const or_problem *Pr, uint64_t first, uint64_t count, double
         jobs[t].multiple = multiple;
         jobs[t].wx = wx ? wx + 3 * a : NULL;
         jobs[t].wlogj = wlogj ? wlogj + a : NULL;
-        jobs[t].tlog = tlog ? tlog + 4 * a : NULL;
+        jobs[t].tlog = tlog ? tlog + 5 * a : NULL;
         if (!jobs[t].img) return -1;
         pthread_create(&th[t], NULL, or_worker, &jobs[t]);
     }
@@ -878,8 +883,9 @@ int or_trace_multiple(const or_problem *Pr, uint64_t first, uint64_t count, doub
 
 /* Multiple scattering with the first-order coordinates of packet j given (x[j][3],
  * weight exp(logj[j])); either may be NULL together (plain points).  train_log
- * (optional) gets per packet the first-order coordinates used and the packet's total
- * peel-off intensity over all orders. */
+ * (optional) gets per packet the first-order coordinates used, the sum of the
+ * intensities its peel-offs put into the image (all orders) and the square root of
+ * their sum of squares. */
 int or_trace_multiple_warped(const or_problem *Pr, uint64_t first, uint64_t count, const double *x,
                              const double *logj, double *image, double *train_log, int nthreads)
 {

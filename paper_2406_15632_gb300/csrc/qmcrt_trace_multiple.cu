@@ -3,7 +3,8 @@
 // One thread per packet, the same warp-coherent packet mapping as the single-
 // scattering kernel.  With a learned warp the first-order coordinates come from a
 // buffer (x = T(u) and log |dx/du| per packet); the optional training log records,
-// per packet, the coordinates used and the packet's total peel-off intensity.
+// per packet, the coordinates used and two norms of the intensities its peel-offs put
+// into the image (their sum, and the square root of their sum of squares).
 // Order k reads coordinates 4(k-1) + {0 azimuth, 1 cos Theta, 2 depth, 3 roulette};
 // the order loop is uniform across the warp so deposits stay
 // convergent, and the warp leaves the loop once all its packets are done.
@@ -22,7 +23,7 @@ __global__ void __launch_bounds__(256) k_trace_multiple(const __grid_constant__ 
     bool alive = live_index;
     T pos[3] = {T(0), T(0), T(0)}, n[3] = {T(0), T(0), T(1)}, a[3] = {T(1), T(0), T(0)};
     T S[3] = {T(0), T(0), T(0)};
-    T wd = T(0), total = T(0);
+    T wd = T(0), total = T(0), total2 = T(0);
     const uint64_t j = i - P.first;
     if (alive) {
         T wgt;
@@ -65,7 +66,10 @@ __global__ void __launch_bounds__(256) k_trace_multiple(const __grid_constant__ 
                 S[1] *= P.dust.albedo;
                 S[2] *= P.dust.albedo;
                 contrib = peel_polarized(P, pos, n, a, S, out, x, y);
-                if (contrib) total += out[0];
+                if (contrib && x >= -P.obs.hw && x < P.obs.hw && y >= -P.obs.hw && y < P.obs.hw) {
+                    total += out[0];
+                    total2 += out[0] * out[0];
+                }
             }
         }
         splat(P, contrib, P.per_order ? k - 1 : 0, x, y, out);
@@ -84,7 +88,7 @@ __global__ void __launch_bounds__(256) k_trace_multiple(const __grid_constant__ 
         }
     }
     if (P.train_log && live_index) {
-        float *r = P.train_log + 4 * j;
+        float *r = P.train_log + 5 * j;
         if (P.warp_x) {
             r[0] = P.warp_x[3 * j];
             r[1] = P.warp_x[3 * j + 1];
@@ -95,6 +99,7 @@ __global__ void __launch_bounds__(256) k_trace_multiple(const __grid_constant__ 
             r[2] = (float)point<T>(P.pts, i, 2);
         }
         r[3] = (float)total;
+        r[4] = (float)Mth<T>::sqrt_(total2);
     }
 }
 

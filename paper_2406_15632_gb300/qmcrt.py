@@ -501,7 +501,8 @@ class Scene:
     def trace_warped(self, first: int, count: int, buf, *, x=None, logj=None, train_log=None, accum: str = "i64",
                      frac_bits: int = 0, precision: str = "f32", stream=None) -> None:
         """Multiple scattering with the first-order coordinates of packet j taken from
-        x[j] (weight times exp(logj[j])); optionally log (x, total intensity) per packet."""
+        x[j] (weight times exp(logj[j])); optionally log per packet [n][5]: x, then the
+        sum and the L2 norm of the in-image intensities of its peel-offs."""
         p = self.prob
         pts = points_desc(p.generator, p.dims, first, count, "f64", p.seed, p.total_n)
         img = self.image_desc(buf, accum, frac_bits)

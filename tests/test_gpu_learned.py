@@ -43,7 +43,7 @@ def test_warped_fp64_trace_matches_oracle(Q, first, count):
     W = _warp(Q)
     tr = Q.LearnedTracer(sc, W, chunk=1 << 12)  # several chunks
     buf = sc.accum_buffer("f64")
-    log = torch.zeros((count, 4), dtype=torch.float32, device="cuda")
+    log = torch.zeros((count, 5), dtype=torch.float32, device="cuda")
     tr.trace(first, count, buf, frac_bits=0, accum="f64", precision="f64", train_log=log)
     u = Q.generate_points(prob.generator, 3, first, count, "f32")
     x, lj = W.forward(u)
@@ -56,7 +56,7 @@ def test_warped_fp64_trace_matches_oracle(Q, first, count):
     assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
     lg = log.cpu().numpy()
     assert np.array_equal(lg[:, :3], x.cpu().numpy())
-    assert np.allclose(lg[:, 3], rlog[:, 3], rtol=1e-6, atol=1e-30)
+    assert np.allclose(lg[:, 3:], rlog[:, 3:], rtol=1e-6, atol=1e-30)
     # the warp moved the points, and the weights are bounded by mix^-3
     assert np.abs(xh - u.cpu().numpy()).max() > 0.05
     assert ljh.max() <= 3 * np.log(10.0) + 1e-4
@@ -71,14 +71,14 @@ def test_plain_entry_point_is_the_multiple_tracer_and_logs(Q):
     a = sc.accum_buffer("i64")
     sc.trace(1, count, a, frac_bits=fb, precision="f64")
     b = sc.accum_buffer("i64")
-    log = torch.zeros((count, 4), dtype=torch.float32, device="cuda")
+    log = torch.zeros((count, 5), dtype=torch.float32, device="cuda")
     Q.LearnedTracer(sc, None).trace(1, count, b, frac_bits=fb, accum="i64", precision="f64", train_log=log)
     torch.cuda.synchronize()
     assert torch.equal(a, b)
     _, rlog = O.trace_multiple_warped(prob, 1, count, train_log=True)
     lg = log.cpu().numpy()
     assert np.array_equal(lg[:, :3], rlog[:, :3].astype(np.float32))
-    assert np.allclose(lg[:, 3], rlog[:, 3], rtol=1e-6, atol=1e-30)
+    assert np.allclose(lg[:, 3:], rlog[:, 3:], rtol=1e-6, atol=1e-30)
 
 
 def test_fp32_warped_trace_is_close_to_fp64(Q):
@@ -130,7 +130,7 @@ def test_learned_estimator_is_unbiased_after_training(Q):
     prob = _problem(n=32)
     sc = Q.Scene(prob)
     n_log = 1 << 18
-    log = torch.zeros((n_log, 4), dtype=torch.float32, device="cuda")
+    log = torch.zeros((n_log, 5), dtype=torch.float32, device="cuda")
     plain = Q.LearnedTracer(sc, None)
     plain.trace(1, n_log, sc.accum_buffer("f64"), train_log=log)
     W = Q.Warp(seed=2, uniform_mix=0.1)

@@ -282,9 +282,9 @@ def test_three_d_reuse_anti_pattern_does_not_converge():
 
 def test_identity_warp_is_the_plain_tracer_and_logs_packet_totals():
     """x = u with log J = 0 replays the plain multiple-scattering tracer exactly; the
-    training log holds the point's first coordinates, and its per-packet totals add up
-    to at least the image total (peel-offs that land outside the image are counted in
-    the log but not binned)."""
+    training log holds the point's first coordinates, its per-packet sums of in-image
+    intensity add up to the image total, and its per-packet L2 norms lie between
+    sum / sqrt(orders) and the sum."""
     p = S.clumpy_problem(n=16, max_orders=6, nx=32, ny=32, half_width=0.6)
     N = 1 << 12
     u = O.generate_points("sobol", 3, 1, N)
@@ -295,7 +295,10 @@ def test_identity_warp_is_the_plain_tracer_and_logs_packet_totals():
     assert np.array_equal(img2, plain) and np.array_equal(log2, log)
     assert np.array_equal(log[:, :3], u)
     assert np.all(log[:, 3] >= 0)
-    assert log[:, 3].sum() > img[0, 0].sum() * (1 + 1e-3)
+    assert log[:, 3].sum() == pytest.approx(img[0, 0].sum(), rel=1e-12)
+    assert np.all(log[:, 4] <= log[:, 3] * (1 + 1e-12))
+    assert np.all(log[:, 4] >= log[:, 3] / np.sqrt(p.max_orders) * (1 - 1e-12))
+    assert np.any(log[:, 4] < log[:, 3] * (1 - 1e-3))
 
 
 @pytest.mark.parametrize("use_jacobian", [True, False])
