@@ -344,7 +344,9 @@ int qmcrt_warp_adam(const qmcrt_warp *warp, const float *d_grad, float *d_m, flo
  * qmcrt_pad_grid -- prepares a grid for the faster walk (Sec. 3.4 optical-depth
  * integration, unchanged in result): writes d_padded, device float
  * [nz+2pad][ny+2pad][nx+2pad], the cells of d_k ([nz][ny][nx]) surrounded by pad layers
- * of the sentinel value -1.  Pass d_padded with qmcrt_medium.pad = pad.
+ * of the sentinel value -0.0 (negative zero); interior cells that are zero, negative or
+ * NaN are written as +0.0, so only sentinels carry a sign bit.  Pass d_padded with
+ * qmcrt_medium.pad = pad.
  * Errors: INVALID_ARG (NULL pointers, empty grid, pad < QMCRT_MIN_PAD, more than 2^31
  * padded cells), CUDA.
  */

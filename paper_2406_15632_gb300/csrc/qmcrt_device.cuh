@@ -411,12 +411,16 @@ __device__ __forceinline__ bool grid_walk(const MediumP<T> &G, const T p[3], con
 }
 
 // The same walk over a padded grid (QMCRT pad >= WALK_UNROLL): the grid is
-// surrounded by `pad` layers of sentinel cells (value -1).  The walk needs no per-axis
-// cell counters: a batch of WALK_UNROLL cells is stepped blindly (at most
-// WALK_UNROLL cells past the box, still inside the padding), sentinels contribute
-// nothing, and the walk ends after the first batch that loaded one.  The
-// box is convex and axis-aligned, so once a step leaves it along any axis every later
-// cell of the ray is outside too.
+// surrounded by `pad` layers of sentinel cells holding -0.0, and the interior holds no
+// negative zero (qmcrt_pad_grid writes +0 for empty, negative or NaN cells).  The walk
+// needs no per-axis cell counters: a batch of WALK_UNROLL cells is stepped blindly (at
+// most WALK_UNROLL cells past the box, still inside the padding), a sentinel adds
+// L * (-0) = -0, nothing, and the walk ends after the first batch in which a loaded
+// value has its sign bit set.  The box is convex and axis-aligned, so once a step
+// leaves it along any axis every later cell of the ray is outside too.  The optical
+// depths of a batch are summed in order and the batch sum enters the compensated
+// total; the march tests the batch sum against the remaining depth and only then
+// looks for the stopping cell inside the batch.
 template <class T, bool TARGET>
 __device__ __forceinline__ bool grid_walk_padded(const MediumP<T> &G, const T p[3], const T d[3], T target_raw,
                                                  T &tau_raw, T &t_out)
@@ -457,36 +461,54 @@ __device__ __forceinline__ bool grid_walk_padded(const MediumP<T> &G, const T p[
                 Z.s = Z.dt;
             }
         }
-        T kc[WALK_UNROLL];
-#pragma unroll
-        for (int u = 0; u < WALK_UNROLL; ++u) kc[u] = (T)__ldg(K + cell[u]);
-        T kmin = kc[0];
+        float kf[WALK_UNROLL];
+        unsigned sign = 0u;
 #pragma unroll
         for (int u = 0; u < WALK_UNROLL; ++u) {
-            const T k = Mth<T>::max_(kc[u], T(0));  // sentinels (outside the box) add nothing
-            kmin = Mth<T>::min_(kmin, kc[u]);
-            const T dtau = L[u] * k;
-            if (TARGET) {
-                const T rem = acc - comp;
-                if (k > T(0) && dtau >= rem) {
-                    t_out = t + rem / k;
-                    tau_raw = target_raw;
-                    return true;
-                }
-                const T y = -dtau - comp;  // acc -= dtau, compensated
-                const T s = acc + y;
-                comp = (s - acc) - y;
-                acc = s;
-                t += L[u];
-                if (k > T(0) && L[u] > T(0)) t_last = t;
-            } else {
-                const T y = dtau - comp;  // acc += dtau, compensated
-                const T s = acc + y;
-                comp = (s - acc) - y;
-                acc = s;
-            }
+            kf[u] = __ldg(K + cell[u]);
+            sign |= __float_as_uint(kf[u]);
         }
-        if (kmin < T(0)) break;
+        T dtau[WALK_UNROLL];
+        T B = T(0);
+#pragma unroll
+        for (int u = 0; u < WALK_UNROLL; ++u) {
+            dtau[u] = L[u] * (T)kf[u];
+            B += dtau[u];
+        }
+        if (TARGET) {
+            T rem = acc - comp;
+            if (B >= rem) {  // the stopping cell is in this batch (or rounding says so)
+#pragma unroll
+                for (int u = 0; u < WALK_UNROLL; ++u) {
+                    if (dtau[u] > T(0) && dtau[u] >= rem) {
+                        t_out = t + rem / (T)kf[u];
+                        tau_raw = target_raw;
+                        return true;
+                    }
+                    rem -= dtau[u];
+                    t += L[u];
+                    if (dtau[u] > T(0)) t_last = t;
+                }
+                acc = rem;
+                comp = T(0);
+            } else {
+                const T y = -B - comp;  // acc -= B, compensated
+                const T s2 = acc + y;
+                comp = (s2 - acc) - y;
+                acc = s2;
+#pragma unroll
+                for (int u = 0; u < WALK_UNROLL; ++u) {
+                    t += L[u];
+                    if (dtau[u] > T(0)) t_last = t;
+                }
+            }
+        } else {
+            const T y = B - comp;  // acc += B, compensated
+            const T s2 = acc + y;
+            comp = (s2 - acc) - y;
+            acc = s2;
+        }
+        if (sign & 0x80000000u) break;
     }
     if (TARGET) {
         t_out = t_last;

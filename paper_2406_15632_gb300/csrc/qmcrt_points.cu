@@ -55,7 +55,10 @@ __global__ void __launch_bounds__(256) k_pad_grid(const float *__restrict__ k, i
         const int y = (int)((e / px) % py) - pad;
         const int z = (int)(e / ((size_t)px * py)) - pad;
         const bool in = x >= 0 && x < nx && y >= 0 && y < ny && z >= 0 && z < nz;
-        out[e] = in ? k[((size_t)z * ny + y) * nx + x] : -1.0f;
+        // interior: the density, with empty, negative and NaN cells as +0 (no sign bit);
+        // padding: the sentinel -0.0, whose sign bit ends a padded walk
+        const float v = in ? k[((size_t)z * ny + y) * nx + x] : 0.0f;
+        out[e] = in ? (v > 0.0f ? v : 0.0f) : -0.0f;
     }
 }
 

@@ -204,11 +204,12 @@ def test_trace_multiple_fp32_bilinear(Q, name, tol_first, tol_all):
 @pytest.mark.parametrize("name", ["disk_sobol", "star_direct", "clumpy_single", "random_grid_kscale"])
 def test_padded_and_counter_walks_agree(Q, name, precision):
     """The sentinel-padded walk and the plain-grid walk with cell counters take the same
-    steps; they differ only in how the compensated sum is closed (zero-length steps past
-    the exit fold the compensation term into the sum), i.e. in the last ulps of an
-    optical depth.  Compared on continuous (tent-splat) images; the clumpy medium
-    magnifies ulp-level optical depth differences as described for FP32 above."""
-    tol = 1e-13 if precision == "f64" else (1e-4 if name == "clumpy_single" else 1e-6)
+    steps; they differ only in the rounding order of the optical-depth sum (the padded
+    walk adds each batch of four cells in order and compensates per batch, the counter
+    walk compensates per cell), i.e. in the last few ulps of an optical depth.
+    Compared on continuous (tent-splat) images; the clumpy medium magnifies ulp-level
+    optical depth differences as described for FP32 above."""
+    tol = 1e-13 if precision == "f64" else (1e-4 if name == "clumpy_single" else 3e-6)
     prob = SINGLE_CASES[name].replace(splat="bilinear")
     N = 1 << 13
     fb = Q.default_frac_bits(prob, N)
