@@ -83,9 +83,9 @@ def profiled_traffic():
     return float(m_bytes.group(1))
 
 
-def cells_per_packet():
+def cells_per_packet(workload="flared_disk_single_scattering"):
     with open(COUNTS) as f:
-        return json.load(f)["flared_disk_single_scattering"]["cells_per_packet"]
+        return json.load(f)[workload]["cells_per_packet"]
 
 
 class ClockSampler:
@@ -161,6 +161,45 @@ def run_cpu_baseline(target_seconds: float = 12.0):
     return {"value": n / dt, "unit": "packets/s", "cores": threads, "kind": "oracle",
             "sample": f"first {n} packets of the workload (same Sobol points), FP64 C oracle, {threads} threads, "
                       f"{dt:.1f} s"}
+
+
+def run_multiple_scattering(log2_n=24, repeats=3):
+    """Clumpy envelope (128^3, 20 orders, forced, roulette 1e-4, 512x512 I/Q/U), 2^24
+    Sobol packets per run, FP32 trace, int64 accumulation: packets/s over `repeats`
+    timed runs after one warm-up, and its ALU roofline fraction with the oracle's count
+    of cells visited per packet."""
+    import torch
+
+    from paper_2406_15632_gb300 import qmcrt as Q
+    from paper_2406_15632_gb300 import scenes as S
+
+    prob = S.clumpy_problem(n=128)
+    sc = Q.Scene(prob)
+    n = 1 << log2_n
+    fb = Q.default_frac_bits(prob, n)
+    buf = sc.accum_buffer("i64")
+    stream = torch.cuda.current_stream()
+
+    def run(k):
+        buf.zero_()
+        sc.trace(n * (k + 1), n, buf, frac_bits=fb)
+    run(0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(repeats):
+        run(k + 1)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / repeats
+    cpp = cells_per_packet("clumpy_multiple_scattering")
+    peak = SMS * LANES_PER_SM * measured_peaks().get("sm_max_mhz", 2070.0) * 1e6
+    ops = n * cpp * OPS_PER_CELL / (ms / 1e3)
+    return {"workload": "clumpy envelope 128^3, point source, 20 orders, forced, roulette 1e-4, 512x512 I/Q/U, "
+                        "FP32 trace, int64 accumulate", "packets": n, "ms": ms, "packets_per_s": n / (ms / 1e3),
+            "roofline": {"bound": "alu", "achieved": ops / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
+                         "frac": ops / peak, "kernel": "k_trace_multiple<float>",
+                         "per_unit": f"{OPS_PER_CELL} ops per cell visit x {cpp:.1f} cells per packet (oracle count)"}}
 
 
 def run_batched():
@@ -546,6 +585,7 @@ def main():
         "clocks": clk,
     }
     if world == 1 and not args.no_extras:
+        line["multiple_scattering"] = run_multiple_scattering()
         line["batched"] = run_batched()
         line["time_to_error"] = {"learned_vs_plain": run_time_to_error_learned(),
                                  "qmc_vs_mc_disk": run_time_to_error_disk()}

@@ -98,6 +98,7 @@ def lib():
             L.or_trace_single.argtypes = [P, u64, u64, dp, dp, i32]
             L.or_trace_multiple.argtypes = [P, u64, u64, dp, i32]
             L.or_trace_multiple_warped.argtypes = [P, u64, u64, dp, dp, dp, dp, i32]
+            L.or_trace_multiple_cells.argtypes = [P, u64, u64, dp, dp]
             L.or_tau_ray.restype = C.c_double
             L.or_tau_ray.argtypes = [P, dp, dp]
             L.or_march_ray.argtypes = [P, dp, dp, C.c_double, dp]
@@ -278,6 +279,18 @@ def trace_multiple_warped(prob, first: int, count: int, x=None, logj=None, train
     if rc != 0:
         raise RuntimeError(f"oracle trace_multiple_warped rc={rc}")
     return (img, tl) if train_log else img
+
+
+def multiple_cells(prob, first: int, count: int):
+    """Grid cells visited per packet by the multiple-scattering tracer (one thread)."""
+    h = _Holder(prob)
+    img = np.zeros((prob.n_images, 3, prob.ny, prob.nx), dtype=np.float64)
+    cells = np.zeros(count, dtype=np.float64)
+    dp = C.POINTER(C.c_double)
+    rc = lib().or_trace_multiple_cells(h.ptr, first, count, img.ctypes.data_as(dp), cells.ctypes.data_as(dp))
+    if rc != 0:
+        raise RuntimeError(f"oracle multiple_cells rc={rc}")
+    return cells
 
 
 def _vec(v):

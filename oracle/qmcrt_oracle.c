@@ -752,7 +752,7 @@ static void or_scatter(const or_dust *D, double u, double v, double n[3], double
  * 4(k-1) + {0, 1, 2, 3}: azimuth (or emission phi), cos Theta (or emission
  * theta), depth, roulette. */
 static void or_trace_multiple_range(const or_problem *Pr, uint64_t first, uint64_t count, double *img,
-                                    const double *wx, const double *wlogj, double *tlog)
+                                    const double *wx, const double *wlogj, double *tlog, double *cells)
 {
     or_view V;
     or_make_view(&Pr->obs, &V);
@@ -760,6 +760,7 @@ static void or_trace_multiple_range(const or_problem *Pr, uint64_t first, uint64
     for (uint64_t j = 0; j < count; ++j) {
         uint64_t i = first + j;
         double pos[3], n[3], a[3], wgt, w, total = 0.0, total2 = 0.0;
+        or_cells_visited = 0;
         double x0 = or_point_f64(&Pr->points, i, 0), x1 = or_point_f64(&Pr->points, i, 1);
         if (wx) {
             /* Learned proposal: the first-order coordinates are x = T(u), and the
@@ -821,13 +822,14 @@ static void or_trace_multiple_range(const or_problem *Pr, uint64_t first, uint64
             tlog[5 * j + 3] = total;
             tlog[5 * j + 4] = sqrt(total2);
         }
+        if (cells) cells[j] = (double)or_cells_visited;
     }
 }
 
 static void *or_worker(void *arg)
 {
     or_job *J = (or_job *)arg;
-    if (J->multiple) or_trace_multiple_range(J->Pr, J->first, J->count, J->img, J->wx, J->wlogj, J->tlog);
+    if (J->multiple) or_trace_multiple_range(J->Pr, J->first, J->count, J->img, J->wx, J->wlogj, J->tlog, NULL);
     else or_trace_single_range(J->Pr, J->first, J->count, J->img, J->log);
     return NULL;
 }
@@ -892,6 +894,16 @@ int or_trace_multiple_warped(const or_problem *Pr, uint64_t first, uint64_t coun
     if (Pr->source.kind != 0) return -3;
     if ((x == NULL) != (logj == NULL)) return -2;
     return or_trace(Pr, first, count, image, NULL, nthreads, 1, x, logj, train_log);
+}
+
+/* Grid cells visited by all walks of each packet of the multiple-scattering tracer
+ * (one thread); the image goes to `image`.  The per-unit work figure of the
+ * multiple-scattering kernel's roofline. */
+int or_trace_multiple_cells(const or_problem *Pr, uint64_t first, uint64_t count, double *image, double *cells)
+{
+    if (Pr->source.kind != 0) return -3;
+    or_trace_multiple_range(Pr, first, count, image, NULL, NULL, NULL, cells);
+    return 0;
 }
 
 /* Exposed for pins: tau along a ray and the position after a march. */

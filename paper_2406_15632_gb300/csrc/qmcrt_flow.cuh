@@ -43,13 +43,16 @@ __device__ __forceinline__ float blob(float v, int k)
 __device__ __forceinline__ void softmax32(const float *z, float *q)
 {
     float mx = z[0];
+#pragma unroll
     for (int k = 1; k < KB; ++k) mx = fmaxf(mx, z[k]);
     float s = 0.0f;
+#pragma unroll
     for (int k = 0; k < KB; ++k) {
         q[k] = expf(z[k] - mx);
         s += q[k];
     }
     const float inv = 1.0f / s;
+#pragma unroll
     for (int k = 0; k < KB; ++k) q[k] *= inv;
 }
 
@@ -58,20 +61,25 @@ __device__ __forceinline__ void softmax32(const float *z, float *q)
 __device__ __forceinline__ float mixed(float s, float mix) { return (1.0f - mix) * s + mix * (1.0f / KB); }
 
 // x = F^-1(uu) for the piecewise-constant pdf 32 q[b] on 32 equal bins, and
-// lq = log(32 q[b]) of the bin it falls in (log |dx/du| = -lq).
+// lq = log(32 q[b]) of the bin it falls in (log |dx/du| = -lq).  The bin search is
+// unrolled with selects so that q stays in registers.
 __device__ __forceinline__ void sample_bin(const float *q, float uu, float &xv, float &lq)
 {
-    float c = 0.0f;
+    float c = 0.0f, cb = 0.0f, qb = q[KB - 1];
     int b = KB - 1;
+    bool found = false;
+#pragma unroll
     for (int k = 0; k < KB - 1; ++k) {
-        if (uu < c + q[k]) {
-            b = k;
-            break;
-        }
+        const bool hit = !found && uu < c + q[k];
+        b = hit ? k : b;
+        qb = hit ? q[k] : qb;
+        cb = hit ? c : cb;
+        found = found || hit;
         c += q[k];
     }
-    xv = fminf(fmaxf((b + (uu - c) / q[b]) / KB, 0.0f), 1.0f);
-    lq = logf(KB * q[b]);
+    if (!found) cb = c;
+    xv = fminf(fmaxf((b + (uu - cb) / qb) / KB, 0.0f), 1.0f);
+    lq = logf(KB * qb);
 }
 
 }  // namespace flow

@@ -36,7 +36,7 @@ constexpr int W_BYTES = 3 * W_LAYER + KB * WD * 2;    // the four layers of one 
 constexpr int A_BYTES = 128 * WD * 2;                 // one activation tile
 constexpr int SBO = (WD / 8) * 128;                   // 8-row group stride (K = 128)
 constexpr int N_BIAS = 3 * WD + KB;
-constexpr int SMEM_BYTES = W_BYTES + FG * A_BYTES + N_BIAS * 4 + FG * 8 + 4 + FG * 4 + 1024;
+constexpr int SMEM_BYTES = W_BYTES + FG * A_BYTES + N_BIAS * 4 + KB * 4 + FG * 8 + 4 + FG * 4 + 1024;
 
 // Byte offset of element (r, k) of a [rows x 128] bf16 tile in the canonical K-major
 // layout: 8 x 16-byte core matrices, K-adjacent ones 128 bytes apart, 8-row groups
@@ -84,7 +84,8 @@ __global__ void __launch_bounds__(FT, 1) k_warp_fused(const float *__restrict__ 
     uint8_t *sW = sm;
     uint8_t *sA0 = sm + W_BYTES;
     float *sBias = reinterpret_cast<float *>(sA0 + FG * A_BYTES);
-    unsigned long long *sBar = reinterpret_cast<unsigned long long *>(sBias + N_BIAS);
+    float *sQ0 = sBias + N_BIAS;  // the x0 bin masses (MI 0), the same for every row
+    unsigned long long *sBar = reinterpret_cast<unsigned long long *>(sQ0 + KB);
     uint32_t *sTmem = reinterpret_cast<uint32_t *>(sBar + FG);
     int *sFail = reinterpret_cast<int *>(sTmem + 1);  // one flag per group, written by that group only
 
@@ -105,6 +106,14 @@ __global__ void __launch_bounds__(FT, 1) k_warp_fused(const float *__restrict__ 
     for (int i = tid; i < N_BIAS; i += FT) {
         const int l = i < 3 * WD ? i / WD : 3, o = i < 3 * WD ? i % WD : i - 3 * WD;
         sBias[i] = params[param_b(MI, l) + o];
+    }
+    if (MI == 0 && tid == 0) {
+        float z[KB], q[KB];
+        for (int k = 0; k < KB; ++k) z[k] = params[k];
+        softmax32(z, q);
+        if (mix != 0.0f)
+            for (int k = 0; k < KB; ++k) q[k] = mixed(q[k], mix);
+        for (int k = 0; k < KB; ++k) sQ0[k] = q[k];
     }
     if (tid == 0) {
         for (int k = 0; k < FG; ++k) sFail[k] = 0;
@@ -136,11 +145,9 @@ __global__ void __launch_bounds__(FT, 1) k_warp_fused(const float *__restrict__ 
         const bool live = j < n;
         float x0, x1 = 0.5f, lj;
         if (MI == 0) {
-            float z[KB], q[KB], lq;
-            for (int k = 0; k < KB; ++k) z[k] = params[k];
-            softmax32(z, q);
-            if (mix != 0.0f)
-                for (int k = 0; k < KB; ++k) q[k] = mixed(q[k], mix);
+            float q[KB], lq;
+#pragma unroll
+            for (int k = 0; k < KB; ++k) q[k] = sQ0[k];
             sample_bin(q, live ? u[3 * j] : 0.5f, x0, lq);
             lj = -lq;
         } else {
@@ -222,8 +229,10 @@ __global__ void __launch_bounds__(FT, 1) k_warp_fused(const float *__restrict__ 
 #pragma unroll
                 for (int k = 0; k < KB; ++k) z[k] = __uint_as_float(r[k]) + sBias[3 * WD + k];
                 softmax32(z, q);
-                if (mix != 0.0f)
+                if (mix != 0.0f) {
+#pragma unroll
                     for (int k = 0; k < KB; ++k) q[k] = mixed(q[k], mix);
+                }
                 sample_bin(q, live ? u[3 * j + 1 + MI] : 0.5f, xv, lq);
                 if (live) {
                     if (MI == 0) x[3 * j] = x0;

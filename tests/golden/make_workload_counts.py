@@ -27,6 +27,15 @@ def main():
         "contributing_fraction": float((log[:, 8] == 0).mean()),
         "note": "256^3 flared disk, point source, Sobol indices 1..2^18, all three walks per packet",
     }
+    clumpy = S.clumpy_problem(n=128)
+    n_multi = 1 << 14
+    cells = O.multiple_cells(clumpy, n_multi, n_multi)
+    out["clumpy_multiple_scattering"] = {
+        "cells_per_packet": float(cells.mean()),
+        "packets": n_multi,
+        "note": "128^3 clumpy envelope, 20 orders, forced, roulette 1e-4, Sobol indices 2^14..2^15-1, "
+                "all walks of all orders per packet",
+    }
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "workload_counts.json")
     with open(path, "w") as f:
         json.dump(out, f, indent=1)
