@@ -202,6 +202,42 @@ def run_multiple_scattering(log2_n=24, repeats=3):
                          "per_unit": f"{OPS_PER_CELL} ops per cell visit x {cpp:.1f} cells per packet (oracle count)"}}
 
 
+def run_observers(n_obs=8, log2_n=24):
+    """One trace of the 256^3 disk feeding n_obs observers (inclinations 0..90 degrees)
+    against n_obs single-observer traces of the same packets; the stacks are identical
+    (checked), so the speedup is at equal images."""
+    import torch
+
+    from paper_2406_15632_gb300 import qmcrt as Q
+
+    prob = workload_problem()
+    sc = Q.Scene(prob)
+    n = 1 << log2_n
+    fb = Q.default_frac_bits(prob, n)
+    angles = [(math.radians(90.0 * k / (n_obs - 1)), 0.0) for k in range(n_obs)]
+    stack = torch.zeros((n_obs, 1, 3, prob.ny, prob.nx), dtype=torch.int64, device="cuda")
+    sep = torch.zeros_like(stack)
+    scenes = [Q.Scene(prob.replace(theta_obs=th, phi_obs=ph), grid_device=sc.grid) for th, ph in angles]
+
+    def together():
+        stack.zero_()
+        sc.trace_observers(angles, n, n, stack, frac_bits=fb)
+
+    def apart():
+        sep.zero_()
+        for o, s_o in enumerate(scenes):
+            s_o.trace(n, n, sep[o], frac_bits=fb)
+    together()
+    apart()
+    _, ms_together = _timed(together)
+    _, ms_apart = _timed(apart)
+    return {"workload": f"flared disk 256^3 single scattering, {n_obs} observers at inclinations 0-90 deg, "
+                        "256x256 I/Q/U each, FP32 trace, int64 accumulate",
+            "packets": n, "observers": n_obs, "one_trace_ms": ms_together, "separate_traces_ms": ms_apart,
+            "packet_observers_per_s": n * n_obs / (ms_together / 1e3), "speedup": ms_apart / ms_together,
+            "identical_images": bool(torch.equal(stack, sep))}
+
+
 def run_batched():
     """Batched workload: 256 instances (32 inclinations x 8 wavelengths, budgets
     2^floor(U(18, 24))) of the flared disk lit by a finite limb-darkened star, 256x256
@@ -587,6 +623,7 @@ def main():
     if world == 1 and not args.no_extras:
         line["multiple_scattering"] = run_multiple_scattering()
         line["batched"] = run_batched()
+        line["observers"] = run_observers()
         line["time_to_error"] = {"learned_vs_plain": run_time_to_error_learned(),
                                  "qmc_vs_mc_disk": run_time_to_error_disk()}
     if world == 1 and not args.no_cpu_baseline:

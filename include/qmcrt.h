@@ -353,6 +353,25 @@ int qmcrt_warp_adam(const qmcrt_warp *warp, const float *d_grad, float *d_m, flo
 int qmcrt_pad_grid(const float *d_k, int32_t nx, int32_t ny, int32_t nz, int32_t pad, float *d_padded, void *stream);
 
 /*
+ * qmcrt_trace_observers -- one trace feeding several observers (Sec. 3.6: the peel-off
+ * is repeated toward each observer from the same scattering events).  Emission,
+ * forced depths and scattering are done once per packet; the optical depth toward
+ * each observer, its peel-off contribution and its binning are done per observer.
+ * obs: host array of n_obs (1..QMCRT_MAX_OBSERVERS) observers with equal nx, ny and
+ * splat (angles and half widths may differ).  opts->max_orders == 1 gives single
+ * scattering with the semantics of qmcrt_trace_single (any source); > 1 gives
+ * multiple scattering as qmcrt_trace_multiple (point source).  image->d_accum holds
+ * n_obs image stacks one after another: [n_obs][n_images][3][ny][nx]; stack o receives
+ * observer o and equals, value for value, what the single-observer call with obs[o]
+ * writes.  Errors: as qmcrt_trace_single / qmcrt_trace_multiple; INVALID_ARG for n_obs
+ * outside the range or observers of different image shape.
+ */
+#define QMCRT_MAX_OBSERVERS 16
+int qmcrt_trace_observers(const qmcrt_medium *medium, const qmcrt_source *source, const qmcrt_dust *dust,
+                          const qmcrt_observer *obs, int32_t n_obs, const qmcrt_points_desc *pts,
+                          const qmcrt_trace_opts *opts, const qmcrt_image *image, void *stream);
+
+/*
  * qmcrt_trace_multiple_warped -- qmcrt_trace_multiple with the learned proposal: packet
  * j (point index first_index + j) takes its first-order coordinates (emission phi,
  * theta and first depth) from d_x[j][3] (x = T(u) from qmcrt_warp_forward) and

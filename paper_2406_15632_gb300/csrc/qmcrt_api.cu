@@ -158,6 +158,30 @@ void make_order(int kind, uint64_t first, uint64_t count, qmcrt::OrderP &O)
     }
 }
 
+// Observer direction k, sky axes e_x, e_y and pixel scale (Sec. 3.6).
+template <class T>
+int make_obs(const qmcrt_observer *ob, qmcrt::ObsP<T> &O)
+{
+    if (ob->nx < 1 || ob->ny < 1) return fail(QMCRT_ERR_INVALID_ARG, "image has no pixels");
+    if (!(ob->half_width > 0)) return fail(QMCRT_ERR_INVALID_ARG, "half_width must be > 0");
+    if (ob->splat != QMCRT_SPLAT_NEAREST && ob->splat != QMCRT_SPLAT_BILINEAR)
+        return fail(QMCRT_ERR_INVALID_ARG, "unknown splat mode %d", ob->splat);
+    const double st = std::sin(ob->theta), ct = std::cos(ob->theta), sp = std::sin(ob->phi), cp = std::cos(ob->phi);
+    const double k[3] = {st * cp, st * sp, ct}, ex[3] = {-sp, cp, 0.0}, ey[3] = {-ct * cp, -ct * sp, st};
+    for (int a = 0; a < 3; ++a) {
+        O.k[a] = (T)k[a];
+        O.ex[a] = (T)ex[a];
+        O.ey[a] = (T)ey[a];
+    }
+    O.hw = (T)ob->half_width;
+    O.pix_x = (T)(ob->nx / (2.0 * ob->half_width));
+    O.pix_y = (T)(ob->ny / (2.0 * ob->half_width));
+    O.nx = ob->nx;
+    O.ny = ob->ny;
+    O.splat = ob->splat;
+    return QMCRT_OK;
+}
+
 template <class T>
 int fill_trace(const qmcrt_medium *md, const qmcrt_source *src, const qmcrt_dust *du, const qmcrt_observer *ob,
                const qmcrt_points_desc *pts, const qmcrt_trace_opts *op, const qmcrt_image *im, int multiple,
@@ -229,24 +253,9 @@ int fill_trace(const qmcrt_medium *md, const qmcrt_source *src, const qmcrt_dust
     P.dust.two_g = (T)(2.0 * du->g);
     P.dust.isotropic = std::fabs(du->g) < 1e-6;
     // observer
-    if (ob->nx < 1 || ob->ny < 1) return fail(QMCRT_ERR_INVALID_ARG, "image has no pixels");
-    if (!(ob->half_width > 0)) return fail(QMCRT_ERR_INVALID_ARG, "half_width must be > 0");
-    if (ob->splat != QMCRT_SPLAT_NEAREST && ob->splat != QMCRT_SPLAT_BILINEAR)
-        return fail(QMCRT_ERR_INVALID_ARG, "unknown splat mode %d", ob->splat);
     {
-        const double st = std::sin(ob->theta), ct = std::cos(ob->theta), sp = std::sin(ob->phi), cp = std::cos(ob->phi);
-        const double k[3] = {st * cp, st * sp, ct}, ex[3] = {-sp, cp, 0.0}, ey[3] = {-ct * cp, -ct * sp, st};
-        for (int a = 0; a < 3; ++a) {
-            P.obs.k[a] = (T)k[a];
-            P.obs.ex[a] = (T)ex[a];
-            P.obs.ey[a] = (T)ey[a];
-        }
-        P.obs.hw = (T)ob->half_width;
-        P.obs.pix_x = (T)(ob->nx / (2.0 * ob->half_width));
-        P.obs.pix_y = (T)(ob->ny / (2.0 * ob->half_width));
-        P.obs.nx = ob->nx;
-        P.obs.ny = ob->ny;
-        P.obs.splat = ob->splat;
+        int rc = make_obs(ob, P.obs);
+        if (rc) return rc;
     }
     // options
     if (op->precision != QMCRT_PREC_F32 && op->precision != QMCRT_PREC_F64)
@@ -333,6 +342,38 @@ int trace_common(const qmcrt_medium *md, const qmcrt_source *src, const qmcrt_du
                        "trace launch");
 }
 
+cudaError_t launch_observers(const qmcrt::TraceP<float> &P, const qmcrt::ObsSet<float> &S, int block, cudaStream_t s)
+{
+    return qmcrt::launch_trace_observers_f32(P, S, block, s);
+}
+
+cudaError_t launch_observers(const qmcrt::TraceP<double> &P, const qmcrt::ObsSet<double> &S, int block, cudaStream_t s)
+{
+    return qmcrt::launch_trace_observers_f64(P, S, block, s);
+}
+
+template <class T>
+int observers_common(const qmcrt_medium *md, const qmcrt_source *src, const qmcrt_dust *du, const qmcrt_observer *obs,
+                     int32_t n_obs, const qmcrt_points_desc *pts, const qmcrt_trace_opts *op, const qmcrt_image *im,
+                     cudaStream_t s)
+{
+    const int multiple = op->max_orders > 1;
+    qmcrt::TraceP<T> P;
+    int rc = fill_trace<T>(md, src, du, &obs[0], pts, op, im, multiple, P);
+    if (rc) return rc;
+    qmcrt::ObsSet<T> S;
+    memset(&S, 0, sizeof S);
+    S.n = n_obs;
+    S.stack = (size_t)im->n_images * 3 * P.acc.plane;
+    for (int o = 0; o < n_obs; ++o) {
+        if ((rc = make_obs(&obs[o], S.o[o]))) return rc;
+        if (obs[o].nx != obs[0].nx || obs[o].ny != obs[0].ny || obs[o].splat != obs[0].splat)
+            return fail(QMCRT_ERR_INVALID_ARG, "observer %d: nx, ny and splat must equal observer 0's", o);
+    }
+    const int block = op->block_size ? op->block_size : 256;
+    return cuda_status(launch_observers(P, S, block, s), "trace_observers launch");
+}
+
 }  // namespace
 
 namespace qmcrt {
@@ -385,6 +426,26 @@ int qmcrt_trace_multiple(const qmcrt_medium *medium, const qmcrt_source *source,
 {
     g_last_error.clear();
     return trace_common(medium, source, dust, obs, pts, opts, image, nullptr, stream, 1);
+}
+
+int qmcrt_trace_observers(const qmcrt_medium *medium, const qmcrt_source *source, const qmcrt_dust *dust,
+                          const qmcrt_observer *obs, int32_t n_obs, const qmcrt_points_desc *pts,
+                          const qmcrt_trace_opts *opts, const qmcrt_image *image, void *stream)
+{
+    g_last_error.clear();
+    if (!obs) return fail(QMCRT_ERR_INVALID_ARG, "obs is NULL");
+    if (n_obs < 1 || n_obs > QMCRT_MAX_OBSERVERS)
+        return fail(QMCRT_ERR_INVALID_ARG, "n_obs = %d outside 1..%d", n_obs, QMCRT_MAX_OBSERVERS);
+    for (int o = 0; o < n_obs; ++o) CHECK_STRUCT((&obs[o]), qmcrt_observer);
+    CHECK_STRUCT(medium, qmcrt_medium);
+    CHECK_STRUCT(source, qmcrt_source);
+    CHECK_STRUCT(dust, qmcrt_dust);
+    CHECK_STRUCT(opts, qmcrt_trace_opts);
+    CHECK_STRUCT(image, qmcrt_image);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (opts->precision == QMCRT_PREC_F64)
+        return observers_common<double>(medium, source, dust, obs, n_obs, pts, opts, image, s);
+    return observers_common<float>(medium, source, dust, obs, n_obs, pts, opts, image, s);
 }
 
 uint64_t qmcrt_batch_workspace_bytes(int32_t n_instances)

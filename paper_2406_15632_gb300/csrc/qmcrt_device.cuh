@@ -700,10 +700,10 @@ __device__ __forceinline__ void rotate_stokes(T cps, T sps, T &Q, T &U)
 }
 
 template <class T>
-__device__ __forceinline__ bool occulted(const TraceP<T> &P, const T pos[3])
+__device__ __forceinline__ bool occulted(const TraceP<T> &P, const ObsP<T> &O, const T pos[3])
 {
     if (P.src.kind != QMCRT_SOURCE_SPHERE) return false;
-    const T b = dot3(pos, P.obs.k);
+    const T b = dot3(pos, O.k);
     const T c = dot3(pos, pos) - P.src.R * P.src.R;
     return c <= T(0) || (b < T(0) && b * b - c > T(0));
 }
@@ -713,13 +713,12 @@ __device__ __forceinline__ bool occulted(const TraceP<T> &P, const T pos[3])
 // plane; with (dx, dy) the sky projection of d this is
 //   Q = W p_l (dx^2 - dy^2) / (1 + mu^2),  U = W p_l 2 dx dy / (1 + mu^2).
 template <class T>
-__device__ __forceinline__ bool peel_unpolarized(const TraceP<T> &P, const T pos[3], const T d[3], T W0, T S[3],
-                                                 T &x, T &y)
+__device__ __forceinline__ bool peel_unpolarized(const TraceP<T> &P, const ObsP<T> &O, const T pos[3], const T d[3],
+                                                 T W0, T S[3], T &x, T &y)
 {
-    const ObsP<T> &O = P.obs;
     x = dot3(pos, O.ex);
     y = dot3(pos, O.ey);
-    if (occulted(P, pos)) return false;
+    if (occulted(P, O, pos)) return false;
     const T tau_obs = tau_to_edge(P.med, pos, O.k);
     const T mu = dot3(d, O.k);
     const T f = W0 * Mth<T>::exp_(-tau_obs) * hg_p11(P.dust, mu) * T(0.07957747154594767);  // 1/(4 pi)
@@ -733,13 +732,12 @@ __device__ __forceinline__ bool peel_unpolarized(const TraceP<T> &P, const T pos
 
 // Peel-off of a polarized packet (direction n, Stokes S in the frame of axis a).
 template <class T>
-__device__ __forceinline__ bool peel_polarized(const TraceP<T> &P, const T pos[3], const T n[3], const T a[3],
-                                               const T S[3], T out[3], T &x, T &y)
+__device__ __forceinline__ bool peel_polarized(const TraceP<T> &P, const ObsP<T> &O, const T pos[3], const T n[3],
+                                               const T a[3], const T S[3], T out[3], T &x, T &y)
 {
-    const ObsP<T> &O = P.obs;
     x = dot3(pos, O.ex);
     y = dot3(pos, O.ey);
-    if (occulted(P, pos)) return false;
+    if (occulted(P, O, pos)) return false;
     const T tau_obs = tau_to_edge(P.med, pos, O.k);
     const T mu = dot3(n, O.k);
     const T inv1pm2 = T(1) / (T(1) + mu * mu);
@@ -767,6 +765,21 @@ __device__ __forceinline__ bool peel_polarized(const TraceP<T> &P, const T pos[3
     out[1] = Qo;
     out[2] = Uo;
     return true;
+}
+
+// The peel-offs toward the problem's own observer.
+template <class T>
+__device__ __forceinline__ bool peel_unpolarized(const TraceP<T> &P, const T pos[3], const T d[3], T W0, T S[3],
+                                                 T &x, T &y)
+{
+    return peel_unpolarized(P, P.obs, pos, d, W0, S, x, y);
+}
+
+template <class T>
+__device__ __forceinline__ bool peel_polarized(const TraceP<T> &P, const T pos[3], const T n[3], const T a[3],
+                                               const T S[3], T out[3], T &x, T &y)
+{
+    return peel_polarized(P, P.obs, pos, n, a, S, out, x, y);
 }
 
 // HG scattering of a polarized packet (Sec. 3.5): Theta from v, azimuth 2 pi u from
@@ -883,19 +896,20 @@ __device__ __forceinline__ void deposit(const AccumP &A, bool valid, size_t e, T
     }
 }
 
-// Bin a peel-off contribution at sky (x, y) into image img (Sec. 3.6).  Must be
-// called by all 32 lanes.
+// Bin a peel-off contribution at sky (x, y) of observer O into image img of the image
+// stack that starts `stack` values into the accumulator (Sec. 3.6).  Must be called
+// by all 32 lanes.
 template <class T>
-__device__ __forceinline__ void splat(const TraceP<T> &P, bool valid, int img, T x, T y, const T S[3])
+__device__ __forceinline__ void splat(const ObsP<T> &O, const AccumP &acc, size_t stack, bool valid, int img, T x, T y,
+                                      const T S[3])
 {
-    const ObsP<T> &O = P.obs;
-    const size_t img_base = (size_t)img * 3 * P.acc.plane;
+    const size_t img_base = stack + (size_t)img * 3 * acc.plane;
     if (O.splat == QMCRT_SPLAT_NEAREST) {
         const T fx = Mth<T>::floor_((x + O.hw) * O.pix_x);
         const T fy = Mth<T>::floor_((y + O.hw) * O.pix_y);
         const bool in = valid && fx >= T(0) && fx < T(O.nx) && fy >= T(0) && fy < T(O.ny);
         const size_t e = in ? img_base + (size_t)((int)fy * O.nx + (int)fx) : 0;
-        deposit<T>(P.acc, in, e, S[0], S[1], S[2]);
+        deposit<T>(acc, in, e, S[0], S[1], S[2]);
         return;
     }
     const T fx = (x + O.hw) * O.pix_x - T(0.5);
@@ -909,8 +923,14 @@ __device__ __forceinline__ void splat(const TraceP<T> &P, bool valid, int img, T
         const bool in = valid && ix >= T(0) && ix < T(O.nx) && iy >= T(0) && iy < T(O.ny);
         const T w = (dx ? ax : T(1) - ax) * (dy ? ay : T(1) - ay);
         const size_t e = in ? img_base + (size_t)((int)iy * O.nx + (int)ix) : 0;
-        deposit<T>(P.acc, in, e, w * S[0], w * S[1], w * S[2]);
+        deposit<T>(acc, in, e, w * S[0], w * S[1], w * S[2]);
     }
+}
+
+template <class T>
+__device__ __forceinline__ void splat(const TraceP<T> &P, bool valid, int img, T x, T y, const T S[3])
+{
+    splat(P.obs, P.acc, 0, valid, img, x, y, S);
 }
 
 }  // namespace qmcrt

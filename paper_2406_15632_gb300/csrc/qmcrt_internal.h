@@ -117,6 +117,18 @@ struct TraceP {
     T rr_threshold, rr_survival, inv_rr_survival;
 };
 
+// Observers fed by one trace (qmcrt_trace_observers); image o is the stack that
+// starts o * stack values into the accumulator.
+template <class T>
+struct ObsSet {
+    int n;
+    size_t stack;  // values per observer: n_images * 3 * nx * ny
+    ObsP<T> o[QMCRT_MAX_OBSERVERS];
+};
+
+cudaError_t launch_trace_observers_f32(const TraceP<float> &p, const ObsSet<float> &obs, int block, cudaStream_t s);
+cudaError_t launch_trace_observers_f64(const TraceP<double> &p, const ObsSet<double> &obs, int block, cudaStream_t s);
+
 struct GemmEpi;
 cudaError_t launch_gemm_bf16(const __nv_bfloat16 *A, const __nv_bfloat16 *B, int M, int N, int K, int splits,
                              const GemmEpi &ep, cudaStream_t s);

@@ -1,16 +1,32 @@
 // qmcrt_trace_multiple.cu -- multiple-scattering tracer kernel (Sec. 3.5, 3.7).
 //
 // One thread per packet, the same warp-coherent packet mapping as the single-
-// scattering kernel.  With a learned warp the first-order coordinates come from a
-// buffer (x = T(u) and log |dx/du| per packet); the optional training log records,
-// per packet, the coordinates used and two norms of the intensities its peel-offs put
-// into the image (their sum, and the square root of their sum of squares).
-// Order k reads coordinates 4(k-1) + {0 azimuth, 1 cos Theta, 2 depth, 3 roulette};
-// the order loop is uniform across the warp so deposits stay
-// convergent, and the warp leaves the loop once all its packets are done.
-#include "qmcrt_device.cuh"
+// scattering kernel; the orders are in qmcrt_orders.cuh.  With a learned warp the
+// first-order coordinates come from a buffer (x = T(u) and log |dx/du| per packet);
+// the optional training log records, per packet, the coordinates used and two norms
+// of the intensities its peel-offs put into the image (their sum, and the square root
+// of their sum of squares).
+#include "qmcrt_orders.cuh"
 
 namespace qmcrt {
+
+template <class T>
+struct OneObserver {
+    const TraceP<T> &P;
+    T total, total2;  // in-image Stokes I of this packet's peel-offs: sum, sum of squares
+    __device__ __forceinline__ void operator()(int k, bool alive, const T pos[3], const T n[3], const T a[3],
+                                               const T S[3])
+    {
+        T out[3] = {T(0), T(0), T(0)};
+        T x = T(0), y = T(0);
+        const bool contrib = alive && peel_polarized(P, pos, n, a, S, out, x, y);
+        if (contrib && x >= -P.obs.hw && x < P.obs.hw && y >= -P.obs.hw && y < P.obs.hw) {
+            total += out[0];
+            total2 += out[0] * out[0];
+        }
+        splat(P, contrib, P.per_order ? k - 1 : 0, x, y, out);
+    }
+};
 
 template <class T>
 __global__ void __launch_bounds__(256) k_trace_multiple(const __grid_constant__ TraceP<T> P)
@@ -20,73 +36,9 @@ __global__ void __launch_bounds__(256) k_trace_multiple(const __grid_constant__ 
     uint64_t i = P.first;
     const bool live_index = packet_index(P.ord, P.first, P.count, tid, i);
     if (!__any_sync(FULL_MASK, live_index)) return;
-    bool alive = live_index;
-    T pos[3] = {T(0), T(0), T(0)}, n[3] = {T(0), T(0), T(1)}, a[3] = {T(1), T(0), T(0)};
-    T S[3] = {T(0), T(0), T(0)};
-    T wd = T(0), total = T(0), total2 = T(0);
     const uint64_t j = i - P.first;
-    if (alive) {
-        T wgt;
-        if (P.warp_x) {  // learned proposal: first-order coordinates and their Jacobian
-            T sp, cp;
-            direction_from((T)P.warp_x[3 * j], (T)P.warp_x[3 * j + 1], n, a, sp, cp);
-            pos[0] = pos[1] = pos[2] = T(0);
-            wd = (T)P.warp_x[3 * j + 2];
-            wgt = Mth<T>::exp_((T)P.warp_logj[j]);
-        } else {
-            wd = emit(P, i, pos, n, a, wgt);
-        }
-        S[0] = wgt;
-    }
-    for (int k = 1; k <= P.max_orders; ++k) {
-        if (!__any_sync(FULL_MASK, alive)) break;
-        const int base = 4 * (k - 1);
-        T out[3] = {T(0), T(0), T(0)};
-        T x = T(0), y = T(0);
-        bool contrib = false;
-        if (alive) {
-            if (k > 1) {
-                scatter(P.dust, point<T>(P.pts, i, base), point<T>(P.pts, i, base + 1), n, a, S);
-                wd = point<T>(P.pts, i, base + 2);
-            }
-            if (k == 1 || P.force_all) {
-                T W1;
-                if (forced_step(P, pos, n, wd, W1)) {
-                    S[0] *= W1;
-                    S[1] *= W1;
-                    S[2] *= W1;
-                } else {
-                    alive = false;
-                }
-            } else if (!march(P.med, pos, n, -Mth<T>::log_(wd))) {
-                alive = false;
-            }
-            if (alive) {
-                S[0] *= P.dust.albedo;
-                S[1] *= P.dust.albedo;
-                S[2] *= P.dust.albedo;
-                contrib = peel_polarized(P, pos, n, a, S, out, x, y);
-                if (contrib && x >= -P.obs.hw && x < P.obs.hw && y >= -P.obs.hw && y < P.obs.hw) {
-                    total += out[0];
-                    total2 += out[0] * out[0];
-                }
-            }
-        }
-        splat(P, contrib, P.per_order ? k - 1 : 0, x, y, out);
-        if (alive) {
-            if (k == P.max_orders) {
-                alive = false;
-            } else if (S[0] < P.rr_threshold) {
-                if (point<T>(P.pts, i, base + 3) < P.rr_survival) {
-                    S[0] /= P.rr_survival;
-                    S[1] /= P.rr_survival;
-                    S[2] /= P.rr_survival;
-                } else {
-                    alive = false;
-                }
-            }
-        }
-    }
+    OneObserver<T> peel{P, T(0), T(0)};
+    trace_orders(P, i, j, live_index, peel);
     if (P.train_log && live_index) {
         float *r = P.train_log + 5 * j;
         if (P.warp_x) {
@@ -98,8 +50,8 @@ __global__ void __launch_bounds__(256) k_trace_multiple(const __grid_constant__ 
             r[1] = (float)point<T>(P.pts, i, 1);
             r[2] = (float)point<T>(P.pts, i, 2);
         }
-        r[3] = (float)total;
-        r[4] = (float)Mth<T>::sqrt_(total2);
+        r[3] = (float)peel.total;
+        r[4] = (float)Mth<T>::sqrt_(peel.total2);
     }
 }
 

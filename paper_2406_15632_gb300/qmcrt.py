@@ -130,6 +130,9 @@ _SIGS = [
     ("qmcrt_trace_multiple_warped", C.c_int, [_P(qmcrt_medium), _P(qmcrt_source), _P(qmcrt_dust),
                                               _P(qmcrt_observer), _P(qmcrt_points_desc), _P(qmcrt_trace_opts),
                                               C.c_void_p, C.c_void_p, _P(qmcrt_image), C.c_void_p, C.c_void_p]),
+    ("qmcrt_trace_observers", C.c_int, [_P(qmcrt_medium), _P(qmcrt_source), _P(qmcrt_dust), _P(qmcrt_observer),
+                                        C.c_int32, _P(qmcrt_points_desc), _P(qmcrt_trace_opts), _P(qmcrt_image),
+                                        C.c_void_p]),
     ("qmcrt_batch_workspace_bytes", C.c_uint64, [C.c_int32]),
     ("qmcrt_trace_batch", C.c_int, [_P(qmcrt_medium), _P(qmcrt_source), _P(qmcrt_observer), _P(qmcrt_points_desc),
                                     _P(qmcrt_trace_opts), C.c_void_p, C.c_int32, _P(qmcrt_batch_config), C.c_void_p,
@@ -344,6 +347,14 @@ def qmcrt_pad_grid(d_k: int, nx: int, ny: int, nz: int, pad: int, d_padded: int,
     _check(load().qmcrt_pad_grid(C.c_void_p(d_k), nx, ny, nz, pad, C.c_void_p(d_padded), C.c_void_p(stream)))
 
 
+MAX_OBSERVERS = 16
+
+
+def qmcrt_trace_observers(medium, source, dust, obs_array, n_obs: int, pts, opts, image, stream: int = 0) -> None:
+    _check(load().qmcrt_trace_observers(C.byref(medium), C.byref(source), C.byref(dust), obs_array, n_obs, C.byref(pts),
+                                        C.byref(opts), C.byref(image), C.c_void_p(stream)))
+
+
 def qmcrt_trace_multiple_warped(medium, source, dust, obs, pts, opts, d_x: int, d_logj: int, image,
                                 d_train_log: int = 0, stream: int = 0) -> None:
     _check(load().qmcrt_trace_multiple_warped(C.byref(medium), C.byref(source), C.byref(dust), C.byref(obs),
@@ -509,6 +520,27 @@ class Scene:
         ptr = lambda t: t.data_ptr() if t is not None else 0
         qmcrt_trace_multiple_warped(self.medium, self.source, self.dust, self.obs, pts, self.opts(precision), ptr(x),
                                     ptr(logj), img, ptr(train_log), _stream(stream))
+
+    def observer_array(self, angles, half_widths=None):
+        """ctypes array of observers at (theta, phi) pairs sharing this problem's image
+        shape and splat; half widths default to the problem's."""
+        p = self.prob
+        arr = (qmcrt_observer * len(angles))()
+        for o, (th, ph) in enumerate(angles):
+            hw = p.half_width if half_widths is None else half_widths[o]
+            arr[o] = _new(qmcrt_observer, splat=SPLAT[p.splat], theta=th, phi=ph, half_width=hw, nx=p.nx, ny=p.ny)
+        return arr
+
+    def trace_observers(self, angles, first: int, count: int, buf, *, half_widths=None, accum: str = "i64",
+                        frac_bits: int = 0, precision: str = "f32", stream=None) -> None:
+        """One trace of packets first..first+count-1 peeled off toward every observer in
+        `angles` ((theta, phi) pairs); buf is [n_obs][n_images][3][ny][nx]."""
+        p = self.prob
+        arr = self.observer_array(angles, half_widths)
+        pts = points_desc(p.generator, p.dims, first, count, "f64", p.seed, p.total_n)
+        img = self.image_desc(buf, accum, frac_bits)
+        qmcrt_trace_observers(self.medium, self.source, self.dust, arr, len(angles), pts, self.opts(precision), img,
+                              _stream(stream))
 
     def reduce(self, buf, scale: float, *, accum: str = "i64", frac_bits: int = 0, out=None, stream=None):
         torch = _torch()

@@ -121,6 +121,33 @@ def test_trace_single_validation(lib, over):
             d["opts"], d["img"], 0, 0)
 
 
+@pytest.mark.parametrize("over", BAD_TRACE[:6])
+def test_trace_observers_validation(lib, over):
+    """The observer-set entry point rejects what the single-observer one rejects, an
+    observer count outside 1..16, and observers of different image shape."""
+    d = _descs(**over)
+
+    def call(obs_list, n):
+        arr = (Q.qmcrt_observer * max(len(obs_list), 1))(*obs_list)
+        Q.qmcrt_trace_observers(d["medium"], d["source"], d["dust"], arr, n, d["pts"], d["opts"], d["img"], 0)
+
+    with pytest.raises(Q.QmcrtError) as e:
+        call([d["obs"], _descs()["obs"]], 2)
+    assert e.value.code == Q.ERR_INVALID_ARG
+    good = _descs()
+    for obs_list, n in (([good["obs"]], 0), ([good["obs"]] * 17, 17)):
+        with pytest.raises(Q.QmcrtError) as e:
+            Q.qmcrt_trace_observers(good["medium"], good["source"], good["dust"],
+                                    (Q.qmcrt_observer * len(obs_list))(*obs_list), n, good["pts"], good["opts"],
+                                    good["img"], 0)
+        assert e.value.code == Q.ERR_INVALID_ARG
+    wide = _descs(obs__nx=16)["obs"]
+    with pytest.raises(Q.QmcrtError) as e:
+        Q.qmcrt_trace_observers(good["medium"], good["source"], good["dust"],
+                                (Q.qmcrt_observer * 2)(good["obs"], wide), 2, good["pts"], good["opts"], good["img"], 0)
+    assert e.value.code == Q.ERR_INVALID_ARG
+
+
 def test_trace_multiple_validation(lib):
     d = _descs(opts__max_orders=3)
     d["pts"].dims = 11  # needs 12
