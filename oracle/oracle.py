@@ -20,7 +20,7 @@ _SRC = os.path.join(_HERE, "qmcrt_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 
-KINDS = {"sobol": 0, "sobol_owen": 1, "halton": 2, "hammersley": 3, "philox": 4}
+KINDS = {"sobol": 0, "sobol_owen": 1, "halton": 2, "hammersley": 3, "philox": 4, "niederreiter": 5, "faure": 6}
 FORMATS = {"u32": 0, "f32": 1, "f64": 2}
 
 _lock = threading.Lock()
@@ -92,6 +92,13 @@ def lib():
             L.or_prime.argtypes = [i32]
             L.or_philox4x32_10.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
             L.or_generate_points.argtypes = [i32, i32, u64, u64, C.POINTER(C.c_uint32), u64, u64, i32, C.c_void_p]
+            L.or_niederreiter_columns.argtypes = [i32, C.POINTER(C.c_uint32)]
+            L.or_niederreiter_u32.restype = C.c_uint32
+            L.or_niederreiter_u32.argtypes = [C.POINTER(C.c_uint32), i32, u64]
+            L.or_faure_base.restype = C.c_uint32
+            L.or_faure_base.argtypes = [i32]
+            L.or_faure.restype = C.c_double
+            L.or_faure.argtypes = [u64, i32, C.c_uint32]
             L.or_hg_cos.restype = C.c_double
             L.or_hg_cos.argtypes = [C.c_double, C.c_double]
             P = C.POINTER(_Problem)
@@ -137,6 +144,33 @@ def sobol_directions(dims: int) -> np.ndarray:
     return _V_cache[dims]
 
 
+_N_cache: dict = {}
+
+
+def niederreiter_columns(dims: int) -> np.ndarray:
+    """[dims][32] generator-matrix columns of the base-2 Niederreiter sequence."""
+    if dims not in _N_cache:
+        V = np.zeros((dims, 32), dtype=np.uint32)
+        rc = lib().or_niederreiter_columns(dims, V.ctypes.data_as(C.POINTER(C.c_uint32)))
+        if rc != 0:
+            raise RuntimeError(f"niederreiter columns: rc={rc}")
+        _N_cache[dims] = V
+    return _N_cache[dims]
+
+
+def digital_table(kind: str, dims: int) -> np.ndarray:
+    """The 32-bit column table a generator of this kind reads (Sobol or Niederreiter)."""
+    return niederreiter_columns(max(dims, 1)) if kind == "niederreiter" else sobol_directions(max(dims, 1))
+
+
+def faure_base(dims: int) -> int:
+    return lib().or_faure_base(dims)
+
+
+def faure(i: int, d: int, b: int) -> float:
+    return lib().or_faure(i, d, b)
+
+
 # --- points -------------------------------------------------------------------------------
 
 def generate_points(kind: str, dims: int, first: int, count: int, fmt: str = "f64", seed: int = 0,
@@ -144,7 +178,7 @@ def generate_points(kind: str, dims: int, first: int, count: int, fmt: str = "f6
     """Row-major [count][dims] points with indices first .. first+count-1."""
     dt = {"u32": np.uint32, "f32": np.float32, "f64": np.float64}[fmt]
     out = np.zeros((count, dims), dtype=dt)
-    V = sobol_directions(max(dims, 1))
+    V = digital_table(kind, dims)
     rc = lib().or_generate_points(KINDS[kind], dims, seed, total_n, V.ctypes.data_as(C.POINTER(C.c_uint32)),
                                   first, count, FORMATS[fmt], out.ctypes.data)
     if rc != 0:
@@ -212,7 +246,7 @@ class _Holder:
         s.obs.theta, s.obs.phi, s.obs.half_width = prob.theta_obs, prob.phi_obs, prob.half_width
         s.obs.nx, s.obs.ny = prob.nx, prob.ny
         s.obs.splat = 0 if prob.splat == "nearest" else 1
-        self.V = sobol_directions(prob.dims)
+        self.V = digital_table(prob.generator, prob.dims)
         s.points.kind = KINDS[prob.generator]
         s.points.dims = prob.dims
         s.points.seed = prob.seed

@@ -40,7 +40,8 @@
 /* Point generators (Sec. 3.1)                                                      */
 /* ------------------------------------------------------------------------------ */
 
-enum { OR_SOBOL = 0, OR_SOBOL_OWEN = 1, OR_HALTON = 2, OR_HAMMERSLEY = 3, OR_PHILOX = 4 };
+enum { OR_SOBOL = 0, OR_SOBOL_OWEN = 1, OR_HALTON = 2, OR_HAMMERSLEY = 3, OR_PHILOX = 4, OR_NIEDERREITER = 5,
+       OR_FAURE = 6 };
 
 /*
  * Sobol direction numbers after Bratley & Fox (1988) with the Joe & Kuo (2008)
@@ -100,6 +101,132 @@ static uint32_t or_reverse32(uint32_t x)
     for (int b = 0; b < 32; ++b)
         if ((x >> b) & 1) r |= 1u << (31 - b);
     return r;
+}
+
+/* ---- Niederreiter base 2 (Niederreiter 1988; Bratley, Fox & Niederreiter 1992) ----
+ * Polynomials over GF(2) are integers, bit i = coefficient of x^i.  Dimension j uses the
+ * j-th irreducible polynomial p_j in the order of degree, then value (x, x + 1,
+ * x^2 + x + 1, x^3 + x + 1, ...).  With e = deg p_j, the generator matrix entry for
+ * output digit r (weight 2^-(r+1)) and input digit k (weight 2^k) is the coefficient
+ * of x^-(k+1) in the Laurent expansion of x^(e - u - 1) / p_j(x)^(q+1), r = q e + u,
+ * 0 <= u < e.  Substituting t = 1/x, that coefficient is the coefficient of t^(k - r)
+ * in the power series of prev(t)^-(q+1), prev(t) = t^e p_j(1/t) (constant term 1). */
+static int or_gf2_degree(uint64_t p)
+{
+    int d = -1;
+    while (p) { ++d; p >>= 1; }
+    return d;
+}
+
+static uint64_t or_gf2_rem(uint64_t a, uint64_t b)
+{
+    int db = or_gf2_degree(b);
+    for (int da = or_gf2_degree(a); da >= db; da = or_gf2_degree(a)) a ^= b << (da - db);
+    return a;
+}
+
+static int or_gf2_irreducible(uint64_t p)
+{
+    int d = or_gf2_degree(p);
+    if (d < 1) return 0;
+    for (uint64_t q = 2; or_gf2_degree(q) <= d / 2; ++q)
+        if (or_gf2_rem(p, q) == 0) return 0;
+    return 1;
+}
+
+/* V[d*32 + k]: column k of the generator matrix of dimension d, output digit r at
+ * bit 31 - r. */
+int or_niederreiter_columns(int dims, uint32_t *V)
+{
+    uint64_t p = 1;
+    for (int d = 0; d < dims; ++d) {
+        do { ++p; } while (!or_gf2_irreducible(p));
+        int e = or_gf2_degree(p);
+        uint32_t rev = 0; /* prev(t): coefficient of t^i is that of x^(e-i) in p */
+        for (int i = 0; i <= e; ++i)
+            if ((p >> (e - i)) & 1) rev |= 1u << i;
+        /* inv: series of 1/prev to 32 terms (prev(0) = 1), by long division */
+        uint8_t inv[32], pw[32], nx[32];
+        for (int n = 0; n < 32; ++n) {
+            int c = n == 0 ? 1 : 0;
+            for (int i = 1; i <= n && i <= e; ++i)
+                if ((rev >> i) & 1) c ^= inv[n - i];
+            inv[n] = (uint8_t)c;
+        }
+        for (int n = 0; n < 32; ++n) pw[n] = inv[n]; /* prev^-(q+1), q = 0 */
+        int q_have = 0;
+        for (int k = 0; k < 32; ++k) V[d * 32 + k] = 0;
+        for (int r = 0; r < 32; ++r) {
+            int q = r / e;
+            while (q_have < q) { /* pw *= inv */
+                for (int n = 0; n < 32; ++n) {
+                    int c = 0;
+                    for (int i = 0; i <= n; ++i) c ^= pw[i] & inv[n - i];
+                    nx[n] = (uint8_t)c;
+                }
+                for (int n = 0; n < 32; ++n) pw[n] = nx[n];
+                ++q_have;
+            }
+            for (int k = r; k < 32; ++k)
+                if (pw[k - r]) V[d * 32 + k] |= 1u << (31 - r);
+        }
+    }
+    return 0;
+}
+
+/* Niederreiter point i, dimension d: XOR of the generator columns over the set bits
+ * of i (natural order). */
+uint32_t or_niederreiter_u32(const uint32_t *V, int d, uint64_t i)
+{
+    uint32_t x = 0;
+    for (int k = 0; k < 32; ++k)
+        if ((i >> k) & 1) x ^= V[d * 32 + k];
+    return x;
+}
+
+/* ---- Faure (1982): base b = the smallest prime >= the number of dimensions.
+ * Dimension j applies the j-th power of the Pascal matrix mod b to the base-b digits
+ * n_k of the index: output digit r = sum over k >= r of C(k, r) j^(k - r) n_k mod b
+ * (j^0 = 1).  The value is the exact fraction sum_r y_r b^(K-1-r) / b^K (K digits of
+ * the index), rounded once to double. */
+uint32_t or_faure_base(int dims)
+{
+    uint32_t b = dims < 2 ? 2u : (uint32_t)dims;
+    for (;; ++b) {
+        int is_p = 1;
+        for (uint32_t q = 2; q * q <= b; ++q)
+            if (b % q == 0) { is_p = 0; break; }
+        if (is_p) return b;
+    }
+}
+
+double or_faure(uint64_t i, int d, uint32_t b)
+{
+    uint32_t n[64], y[64];
+    int K = 0;
+    while (i > 0) { n[K++] = (uint32_t)(i % b); i /= b; }
+    /* binomials mod b by Pascal's rule */
+    uint32_t C[64][64];
+    for (int k = 0; k < K; ++k) {
+        C[k][0] = 1 % b;
+        C[k][k] = 1 % b;
+        for (int r = 1; r < k; ++r) C[k][r] = (C[k - 1][r - 1] + C[k - 1][r]) % b;
+    }
+    uint64_t jmod = (uint64_t)d % b;
+    for (int r = 0; r < K; ++r) {
+        uint64_t acc = 0, pw = 1; /* pw = j^(k - r) mod b */
+        for (int k = r; k < K; ++k) {
+            acc = (acc + (uint64_t)C[k][r] * pw % b * n[k]) % b;
+            pw = pw * jmod % b;
+        }
+        y[r] = (uint32_t)acc;
+    }
+    uint64_t num = 0, den = 1;
+    for (int r = 0; r < K; ++r) {
+        num = num * b + y[r];
+        den *= b;
+    }
+    return (double)num / (double)den;
 }
 
 /* MurmurHash3 32-bit finaliser (Appleby), used only to derive per-dimension seeds. */
@@ -191,7 +318,7 @@ typedef struct {
     int dims;
     uint64_t seed;
     uint64_t total_n;   /* N of the Hammersley set */
-    const uint32_t *V;  /* [dims][32] Sobol direction numbers */
+    const uint32_t *V;  /* [dims][32] Sobol direction numbers, or Niederreiter generator columns */
 } or_points;
 
 /* 32-bit integer value of point i, dimension d (Sobol, scrambled Sobol, Philox). */
@@ -204,6 +331,7 @@ static uint32_t or_point_u32(const or_points *P, uint64_t i, int d)
         or_philox4x32_10(ctr, key, out);
         return out[d % 4];
     }
+    if (P->kind == OR_NIEDERREITER) return or_niederreiter_u32(P->V, d, i);
     uint32_t x = or_sobol_u32(P->V, d, i);
     if (P->kind == OR_SOBOL_OWEN) x = or_owen_scramble(x, or_owen_seed(P->seed, d));
     return x;
@@ -220,6 +348,8 @@ double or_point_f64(const or_points *P, uint64_t i, int d)
     case OR_HAMMERSLEY:
         if (d == 0) return (double)i / (double)P->total_n;
         return or_radical_inverse(i, or_prime(d - 1));
+    case OR_FAURE:
+        return or_faure(i, d, or_faure_base(P->dims));
     default:
         return (double)or_point_u32(P, i, d) * (1.0 / 4294967296.0);
     }
@@ -243,7 +373,7 @@ int or_generate_points(int kind, int dims, uint64_t seed, uint64_t total_n, cons
         for (int d = 0; d < dims; ++d) {
             size_t o = (size_t)(j * (uint64_t)dims + (uint64_t)d);
             if (format == 0) {
-                if (kind == OR_HALTON || kind == OR_HAMMERSLEY) return -1;
+                if (kind == OR_HALTON || kind == OR_HAMMERSLEY || kind == OR_FAURE) return -1;
                 ((uint32_t *)out)[o] = or_point_u32(&P, i, d);
             } else if (format == 1) {
                 ((float *)out)[o] = or_to_f32_rz(or_point_f64(&P, i, d));

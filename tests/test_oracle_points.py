@@ -195,3 +195,96 @@ def test_u32_points_scale_to_f64_exactly():
 def test_halton_rejects_u32_format():
     with pytest.raises(ValueError):
         O.generate_points("halton", 2, 1, 4, "u32")
+
+
+# --- Niederreiter base 2 and Faure (the paper's other two low-discrepancy sequences) ---
+
+def _is_tms_net(u32, m, t):
+    """(t, m, s)-net in base 2: for every split d_1 + ... + d_s = m - t, each elementary
+    box (2^-d_1 x ... x 2^-d_s) holds exactly 2^t of the 2^m points."""
+    import itertools
+
+    x = u32.astype(np.uint64)
+    s = x.shape[1]
+    k = m - t
+    for split in itertools.product(range(k + 1), repeat=s):
+        if sum(split) != k:
+            continue
+        cell = np.zeros(len(x), np.uint64)
+        for j, dj in enumerate(split):
+            lead = x[:, j] >> np.uint64(32 - dj) if dj else np.zeros(len(x), np.uint64)
+            cell = cell * np.uint64(1 << dj) + lead
+        if not np.all(np.bincount(cell.astype(np.int64), minlength=1 << k) == (1 << t)):
+            return False
+    return True
+
+
+def test_niederreiter_dim0_is_van_der_corput_in_natural_order():
+    i = np.arange(0, 5000, dtype=np.uint64)
+    got = O.generate_points("niederreiter", 1, 0, len(i), "u32")[:, 0].astype(np.uint64)
+    assert np.array_equal(got, _bitrev32(i))
+
+
+def test_niederreiter_dim1_is_the_pascal_matrix_of_sobol_dim1():
+    """p = x + 1 gives the Pascal matrix mod 2, the generator of Sobol's second
+    dimension: the Niederreiter point i equals the Sobol point whose Gray code is i."""
+    i = np.arange(0, 4096, dtype=np.uint64)
+    nied = O.generate_points("niederreiter", 2, 0, len(i), "u32")[:, 1]
+    inv = i.copy()
+    for sh in (1, 2, 4, 8, 16, 32):
+        inv ^= inv >> np.uint64(sh)
+    sob = np.array([O.lib().or_sobol_u32(O.sobol_directions(2).ctypes.data_as(O.C.POINTER(O.C.c_uint32)), 1, int(k))
+                    for k in inv], dtype=np.uint32)
+    assert np.array_equal(nied, sob)
+
+
+@pytest.mark.parametrize("dims,t", [(3, 1), (5, 5)])
+@pytest.mark.parametrize("block", [0, 5])
+def test_niederreiter_aligned_blocks_are_tms_nets(dims, t, block):
+    """t = sum of (degree - 1) over the polynomials x, x + 1, x^2 + x + 1, x^3 + x + 1,
+    x^3 + x^2 + 1 bounds the quality parameter: a wrong polynomial order, a reducible
+    polynomial or a transposed generator matrix breaks the net property.  In three
+    dimensions the bound is attained (base 2 has no (0, m, 3)-net from these
+    matrices)."""
+    m = 10
+    pts = O.generate_points("niederreiter", dims, block << m, 1 << m, "u32")
+    assert _is_tms_net(pts, m, t)
+    if dims == 3:
+        assert not _is_tms_net(pts, m, t - 1)
+
+
+def test_faure_base_is_the_smallest_prime_not_below_the_dimension():
+    assert [O.faure_base(s) for s in (1, 2, 3, 4, 5, 6, 8, 80)] == [2, 2, 3, 5, 5, 7, 11, 83]
+
+
+def test_faure_dim0_is_the_radical_inverse_and_values_are_exact():
+    from fractions import Fraction
+
+    b = O.faure_base(5)
+    pts = O.generate_points("faure", 5, 0, 3000, "f64")
+    for i in range(3000):
+        assert pts[i, 0] == O.radical_inverse(i, b)
+    # every coordinate is a fraction with denominator b^K, rounded once
+    for i in (7, 124, 2999):
+        K = len(np.base_repr(i, b))
+        for d in range(5):
+            frac = Fraction(pts[i, d]).limit_denominator(b ** K)
+            assert float(frac) == pts[i, d] and (b ** K) % frac.denominator == 0
+
+
+@pytest.mark.parametrize("dims,m", [(3, 4), (5, 3)])
+def test_faure_is_a_0ms_net_in_base_b(dims, m):
+    """Each elementary b-adic box of volume b^-m holds exactly one of the b^m points
+    (Faure's (0, s)-sequence property), for every split of m over the dimensions."""
+    import itertools
+
+    b = O.faure_base(dims)
+    n = b ** m
+    pts = O.generate_points("faure", dims, 0, n, "f64")
+    for split in itertools.product(range(m + 1), repeat=dims):
+        if sum(split) != m:
+            continue
+        cell = np.zeros(n, np.int64)
+        for j, dj in enumerate(split):
+            cell = cell * (b ** dj) + np.floor(pts[:, j] * b ** dj + 1e-9).astype(np.int64)
+        assert np.all(np.bincount(cell, minlength=n) == 1), split
