@@ -422,8 +422,8 @@ def run_time_to_error_learned(ladder=(20, 22, 24, 26), ref_log2=28, ref_seeds=(1
 def run_time_to_error_disk(ladder=(20, 22, 24, 26), ref_log2=28, ref_seeds=(101, 102, 103, 104)):
     """The paper's comparison on the single-scattering flared disk (256^3, 256x256
     I/Q/U, 45 degrees): wall time to a fixed image error for Sobol, Owen-scrambled
-    Sobol, Halton, Hammersley (its own set of N points for every N) and Philox MC, all
-    through the same FP32 tracer with fixed-point accumulation."""
+    Sobol, Niederreiter, Faure, Halton, Hammersley (its own set of N points for every
+    N) and Philox MC, all through the same FP32 tracer with fixed-point accumulation."""
     import torch
 
     from paper_2406_15632_gb300 import qmcrt as Q
@@ -449,8 +449,9 @@ def run_time_to_error_disk(ladder=(20, 22, 24, 26), ref_log2=28, ref_seeds=(101,
             return out[0, 0].clone(), ms
         return render
 
-    gens = {"sobol": ("sobol", 0), "sobol_owen": ("sobol_owen", 1), "halton": ("halton", 0),
-            "hammersley": ("hammersley", 0), "mc_philox": ("philox", 7)}
+    gens = {"sobol": ("sobol", 0), "sobol_owen": ("sobol_owen", 1), "niederreiter": ("niederreiter", 0),
+            "faure": ("faure", 0), "halton": ("halton", 0), "hammersley": ("hammersley", 0),
+            "mc_philox": ("philox", 7)}
     for g, sd in gens.values():
         renderer(g, sd)(1 << 16)
     arms = {k: _ladder(renderer(g, sd), ladder, ref, ref_err) for k, (g, sd) in gens.items()}

@@ -45,6 +45,8 @@ extern "C" {
 #define QMCRT_HALTON 2     /* Halton, prime bases 2, 3, 5, ... */
 #define QMCRT_HAMMERSLEY 3 /* i/N in the first coordinate, Halton in the others */
 #define QMCRT_PHILOX 4     /* Philox4x32-10 pseudo-random numbers (Monte Carlo) */
+#define QMCRT_NIEDERREITER 5 /* Niederreiter base 2 (irreducible polynomials over GF(2)), natural order */
+#define QMCRT_FAURE 6      /* Faure, base = smallest prime >= dims, Pascal-matrix powers */
 
 #define QMCRT_FMT_U32 0 /* raw 32-bit integers (Sobol, scrambled Sobol, Philox only) */
 #define QMCRT_FMT_F32 1 /* the FP64 value rounded toward zero to float */
@@ -54,7 +56,7 @@ extern "C" {
 
 typedef struct qmcrt_points_desc {
     uint32_t struct_size;
-    int32_t kind;         /* QMCRT_SOBOL .. QMCRT_PHILOX */
+    int32_t kind;         /* QMCRT_SOBOL .. QMCRT_FAURE */
     uint32_t dims;        /* 1 .. QMCRT_MAX_DIMS */
     int32_t format;       /* QMCRT_FMT_* (used by qmcrt_generate_points only) */
     uint64_t first_index; /* >= 1 */

@@ -1,7 +1,7 @@
 """Build of the CUDA library libqmcrt.so (sm_103a) from csrc/.
 
-Generates _build/gen/qmcrt_tables.h (Sobol direction numbers and Halton bases as
-constant-memory initialisers) and compiles each translation unit with nvcc in
+Generates _build/gen/qmcrt_tables.h (Sobol direction numbers, Niederreiter generator
+columns and Halton bases as table initialisers) and compiles each translation unit with nvcc in
 parallel, then links one shared library.  The Sobol table is computed here from the
 Joe & Kuo (2008) primitive polynomials and initial values that ship with SciPy, by
 the Bratley-Fox recurrence m_k = 2 a_1 m_(k-1) ^ ... ^ 2^(s-1) a_(s-1) m_(k-s+1)
@@ -54,6 +54,61 @@ def sobol_direction_table(dims: int = MAX_DIMS) -> list[list[int]]:
     return table
 
 
+def _gf2_deg(p: int) -> int:
+    return p.bit_length() - 1
+
+
+def _gf2_is_irreducible(p: int) -> bool:
+    d = _gf2_deg(p)
+    if d < 1:
+        return False
+    for q in range(2, 1 << (d // 2 + 1)):
+        if _gf2_deg(q) > d // 2:
+            break
+        r = p
+        while r and _gf2_deg(r) >= _gf2_deg(q):
+            r ^= q << (_gf2_deg(r) - _gf2_deg(q))
+        if r == 0:
+            return False
+    return True
+
+
+def niederreiter_table(dims: int = MAX_DIMS) -> list[list[int]]:
+    """Generator-matrix columns of the base-2 Niederreiter sequence (Niederreiter 1988):
+    dimension j uses the j-th irreducible polynomial p over GF(2) (by degree, then
+    value); for output digit r = q e + u (e = deg p) and input digit k the entry is the
+    coefficient of t^(k-r) in the power series (t^e p(1/t))^-(q+1).  Column k holds
+    output digit r at bit 31 - r."""
+    table, p = [], 1
+    for _ in range(dims):
+        p += 1
+        while not _gf2_is_irreducible(p):
+            p += 1
+        e = _gf2_deg(p)
+        rev = [(p >> (e - i)) & 1 for i in range(e + 1)]  # coefficients of t^e p(1/t)
+        inv = []
+        for n in range(32):  # 1 / rev(t) by long division over GF(2)
+            c = 1 if n == 0 else 0
+            for i in range(1, min(n, e) + 1):
+                c ^= rev[i] & inv[n - i]
+            inv.append(c)
+
+        def mul(a, b):
+            return [sum(a[i] & b[n - i] for i in range(n + 1)) & 1 for n in range(32)]
+
+        powers = [inv]  # powers[q] = rev^-(q+1)
+        cols = [0] * 32
+        for r in range(32):
+            q = r // e
+            while len(powers) <= q:
+                powers.append(mul(powers[-1], inv))
+            for k in range(r, 32):
+                if powers[q][k - r]:
+                    cols[k] |= 1 << (31 - r)
+        table.append(cols)
+    return table
+
+
 def primes(n: int = MAX_DIMS) -> list[int]:
     out, c = [], 2
     while len(out) < n:
@@ -67,7 +122,7 @@ def write_tables() -> str:
     os.makedirs(GEN, exist_ok=True)
     path = os.path.join(GEN, "qmcrt_tables.h")
     V = sobol_direction_table()
-    lines = ["/* generated by build.py: Sobol direction numbers (Joe-Kuo) and Halton bases */",
+    lines = ["/* generated by build.py: Sobol direction numbers (Joe-Kuo), Niederreiter columns, Halton bases */",
              "#pragma once",
              f"#define QMCRT_GEN_DIMS {MAX_DIMS}",
              "#define QMCRT_GEN_SOBOL_V_INIT { \\"]
@@ -75,6 +130,10 @@ def write_tables() -> str:
         lines.append("  {" + ",".join(f"0x{v:08x}u" for v in row) + "}, \\")
     lines.append("}")
     lines.append("#define QMCRT_GEN_PRIMES_INIT {" + ",".join(f"{p}u" for p in primes()) + "}")
+    lines.append("#define QMCRT_GEN_NIED_V_INIT { \\")
+    for row in niederreiter_table():
+        lines.append("  {" + ",".join(f"0x{v:08x}u" for v in row) + "}, \\")
+    lines.append("}")
     text = "\n".join(lines) + "\n"
     if not os.path.exists(path) or open(path).read() != text:
         with open(path, "w") as f:

@@ -19,6 +19,7 @@ namespace {
 // Host copy of the Sobol direction numbers (the same generated table the kernels
 // hold in constant memory), for building the net-order packet mapping.
 const uint32_t kSobolV[QMCRT_GEN_DIMS][32] = QMCRT_GEN_SOBOL_V_INIT;
+const uint32_t kNiedV[QMCRT_GEN_DIMS][32] = QMCRT_GEN_NIED_V_INIT;
 
 thread_local std::string g_last_error;
 
@@ -50,7 +51,7 @@ int cuda_status(cudaError_t e, const char *what)
 int check_points(const qmcrt_points_desc *d, uint32_t dims_needed)
 {
     CHECK_STRUCT(d, qmcrt_points_desc);
-    if (d->kind < QMCRT_SOBOL || d->kind > QMCRT_PHILOX) return fail(QMCRT_ERR_INVALID_ARG, "unknown point kind %d", d->kind);
+    if (d->kind < QMCRT_SOBOL || d->kind > QMCRT_FAURE) return fail(QMCRT_ERR_INVALID_ARG, "unknown point kind %d", d->kind);
     if (d->dims < 1 || d->dims > QMCRT_MAX_DIMS)
         return fail(QMCRT_ERR_INVALID_ARG, "dims %u outside 1..%d", d->dims, QMCRT_MAX_DIMS);
     if (d->dims < dims_needed)
@@ -74,19 +75,33 @@ qmcrt::PointsP make_points(const qmcrt_points_desc *d)
     p.seed = d->seed;
     p.total_n = d->total_n;
     p.inv_total_n = d->total_n ? 1.0 / (double)d->total_n : 0.0;
+    uint32_t b = d->dims < 2 ? 2u : d->dims;  // Faure base: smallest prime >= dims
+    for (;; ++b) {
+        bool prime = true;
+        for (uint32_t q = 2; q * q <= b; ++q)
+            if (b % q == 0) {
+                prime = false;
+                break;
+            }
+        if (prime) break;
+    }
+    p.faure_b = b;
     return p;
 }
 
-// Packet order of a launch (see OrderP): net order for Sobol point sets of at least
-// 2^7 packets, linear otherwise.  Solves y = L g over GF(2) once per call: L maps the
-// Gray code g of an index inside a 2^m block to the leading (a, b, c) bits of its
-// coordinates 0, 1, 2 (a + b + c = m - tt, balanced); tt is the smallest value for
-// which L has full row rank (the elementary boxes then hold 2^tt points each).
+// Packet order of a launch (see OrderP): net order for digital base-2 point sets
+// (Sobol, scrambled Sobol, Niederreiter) of at least 2^7 packets, linear otherwise.
+// Solves y = L g over GF(2) once per call: L maps the digit vector g of an index
+// inside a 2^m block (its Gray code for Sobol, its binary digits for Niederreiter) to
+// the leading (a, b, c) bits of its coordinates 0, 1, 2 (a + b + c = m - tt,
+// balanced); tt is the smallest value for which L has full row rank (the elementary
+// boxes then hold 2^tt points each).
 void make_order(int kind, uint64_t first, uint64_t count, qmcrt::OrderP &O)
 {
     memset(&O, 0, sizeof O);
     O.threads = count;
-    if (count == 0 || (kind != QMCRT_SOBOL && kind != QMCRT_SOBOL_OWEN)) return;
+    if (count == 0 || (kind != QMCRT_SOBOL && kind != QMCRT_SOBOL_OWEN && kind != QMCRT_NIEDERREITER)) return;
+    const uint32_t(*V)[32] = kind == QMCRT_NIEDERREITER ? kNiedV : kSobolV;
     int m = 0;
     while (m < qmcrt::NET_MAX_M && (2ull << m) <= count) ++m;
     if (m < 7) return;
@@ -100,7 +115,7 @@ void make_order(int kind, uint64_t first, uint64_t count, qmcrt::OrderP &O)
             else if (rho < c + b) { dim = 1; bit = 32 - b + (rho - c); }
             else { dim = 0; bit = 32 - a + (rho - c - b); }
             uint32_t row = 0;
-            for (int k = 0; k < m; ++k) row |= ((kSobolV[dim][k] >> bit) & 1u) << k;
+            for (int k = 0; k < m; ++k) row |= ((V[dim][k] >> bit) & 1u) << k;
             Lr[rho] = row;
             Er[rho] = 1u << rho;
         }
@@ -120,7 +135,7 @@ void make_order(int kind, uint64_t first, uint64_t count, qmcrt::OrderP &O)
             piv[rank++] = col;
         }
         if (rank < bits) continue;
-        O.net = 1;
+        O.net = kind == QMCRT_NIEDERREITER ? 2 : 1;
         O.m = m;
         O.bits = bits;
         O.tt = tt;
@@ -405,8 +420,8 @@ int qmcrt_generate_points(const qmcrt_points_desc *d, void *d_out, void *stream)
     if (!d_out) return fail(QMCRT_ERR_INVALID_ARG, "d_out is NULL");
     if (d->format != QMCRT_FMT_U32 && d->format != QMCRT_FMT_F32 && d->format != QMCRT_FMT_F64)
         return fail(QMCRT_ERR_INVALID_ARG, "unknown format %d", d->format);
-    if (d->format == QMCRT_FMT_U32 && (d->kind == QMCRT_HALTON || d->kind == QMCRT_HAMMERSLEY))
-        return fail(QMCRT_ERR_INVALID_ARG, "Halton/Hammersley points have no 32-bit integer form");
+    if (d->format == QMCRT_FMT_U32 && (d->kind == QMCRT_HALTON || d->kind == QMCRT_HAMMERSLEY || d->kind == QMCRT_FAURE))
+        return fail(QMCRT_ERR_INVALID_ARG, "Halton/Hammersley/Faure points have no 32-bit integer form");
     return cuda_status(qmcrt::launch_generate_points(make_points(d), d->first_index, d->count, d->format, d_out,
                                                      (cudaStream_t)stream),
                        "generate_points launch");
@@ -501,8 +516,8 @@ int qmcrt_trace_batch(const qmcrt_medium *medium, const qmcrt_source *source, co
     const int ctas = per_sm * sms;
     cudaStream_t s = (cudaStream_t)stream;
     auto *ws = (unsigned long long *)d_workspace;
-    static qmcrt::NetTables tabs[QMCRT_PHILOX + 1];  // per point kind, built once (read-only after)
-    static std::once_flag once[QMCRT_PHILOX + 1];
+    static qmcrt::NetTables tabs[QMCRT_FAURE + 1];  // per point kind, built once (read-only after)
+    static std::once_flag once[QMCRT_FAURE + 1];
     std::call_once(once[pts->kind], [&] {
         for (int m = qmcrt::NET_MIN_M; m <= qmcrt::NET_MAX_M; ++m)
             make_order(pts->kind, 0, 1ull << m, tabs[pts->kind].ord[m - qmcrt::NET_MIN_M]);

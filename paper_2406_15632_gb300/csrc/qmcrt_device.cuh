@@ -20,6 +20,7 @@ namespace qmcrt {
 // Sobol direction numbers V[d][k] for bit k of the Gray-code index, and Halton bases.
 static __constant__ uint32_t c_sobol_v[QMCRT_GEN_DIMS][32] = QMCRT_GEN_SOBOL_V_INIT;
 static __constant__ uint32_t c_primes[QMCRT_GEN_DIMS] = QMCRT_GEN_PRIMES_INIT;
+static __device__ const uint32_t d_nied_v[QMCRT_GEN_DIMS][32] = QMCRT_GEN_NIED_V_INIT;
 
 constexpr unsigned FULL_MASK = 0xffffffffu;
 
@@ -105,6 +106,40 @@ __device__ __forceinline__ uint32_t sobol_u32(uint32_t i, int d)
     return x;
 }
 
+// Niederreiter point i, dimension d (natural order): XOR of the generator columns over
+// the set bits of i.
+__device__ __forceinline__ uint32_t niederreiter_u32(uint32_t i, int d)
+{
+    uint32_t x = 0;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) x ^= (i & (1u << k)) ? __ldg(&d_nied_v[d][k]) : 0u;
+    return x;
+}
+
+// Faure point (Faure 1982): output digit r = sum over k >= r of C(k, r) j^(k-r) n_k mod b
+// (n_k the base-b digits of i, j the dimension), i.e. the coefficients of N(X + j) for
+// N(X) = sum n_k X^k, computed by the Taylor shift (repeated synthetic division) mod b;
+// the value is the exact fraction y / b^K rounded once.
+__device__ __forceinline__ double faure_f64(uint32_t i, int d, uint32_t b)
+{
+    uint32_t a[32];
+    int K = 0;
+    while (i) {
+        const uint32_t q = i / b;
+        a[K++] = i - q * b;
+        i = q;
+    }
+    const uint32_t j = (uint32_t)d % b;
+    for (int s = 0; s + 1 < K; ++s)
+        for (int k = K - 2; k >= s; --k) a[k] = (a[k] + j * a[k + 1]) % b;
+    uint64_t num = 0, den = 1;
+    for (int r = 0; r < K; ++r) {
+        num = num * b + a[r];
+        den *= b;
+    }
+    return (double)num / (double)den;
+}
+
 // MurmurHash3 finaliser, for per-dimension scramble seeds.
 __device__ __forceinline__ uint32_t fmix32(uint32_t h)
 {
@@ -175,12 +210,13 @@ __device__ __forceinline__ double radical_inverse(uint32_t i, uint32_t b)
 
 __device__ __forceinline__ bool is_integer_kind(int kind)
 {
-    return kind == QMCRT_SOBOL || kind == QMCRT_SOBOL_OWEN || kind == QMCRT_PHILOX;
+    return kind == QMCRT_SOBOL || kind == QMCRT_SOBOL_OWEN || kind == QMCRT_PHILOX || kind == QMCRT_NIEDERREITER;
 }
 
 __device__ __forceinline__ uint32_t point_u32(const PointsP &P, uint64_t i, int d)
 {
     if (P.kind == QMCRT_PHILOX) return philox_u32(P.seed, i, d);
+    if (P.kind == QMCRT_NIEDERREITER) return niederreiter_u32((uint32_t)i, d);
     uint32_t x = sobol_u32((uint32_t)i, d);
     if (P.kind == QMCRT_SOBOL_OWEN) x = owen_scramble(x, owen_seed(P.seed, d));
     return x;
@@ -193,6 +229,7 @@ __device__ __forceinline__ double point_f64(const PointsP &P, uint64_t i, int d)
         if (d == 0) return (double)i / (double)P.total_n;
         return radical_inverse((uint32_t)i, c_primes[d - 1]);
     }
+    if (P.kind == QMCRT_FAURE) return faure_f64((uint32_t)i, d, P.faure_b);
     return (double)point_u32(P, i, d) * 0x1p-32;
 }
 
@@ -229,10 +266,13 @@ __device__ __forceinline__ bool packet_index(const OrderP &O, uint64_t first, ui
     uint32_t g = 0;
     for (int j = 0; j < O.bits; ++j) g ^= ((box >> j) & 1u) ? O.rm[j] : 0u;
     for (int j = 0; j < O.tt; ++j) g ^= ((tl >> j) & 1u) ? O.k[j] : 0u;
-    const uint32_t y = (lead_bits(sobol_u32((uint32_t)base, 0), O.a) << (O.b + O.c)) |
-                       (lead_bits(sobol_u32((uint32_t)base, 1), O.b) << O.c) | lead_bits(sobol_u32((uint32_t)base, 2), O.c);
+    const bool nied = O.net == 2;
+    const uint32_t b0 = nied ? niederreiter_u32((uint32_t)base, 0) : sobol_u32((uint32_t)base, 0);
+    const uint32_t b1 = nied ? niederreiter_u32((uint32_t)base, 1) : sobol_u32((uint32_t)base, 1);
+    const uint32_t b2 = nied ? niederreiter_u32((uint32_t)base, 2) : sobol_u32((uint32_t)base, 2);
+    const uint32_t y = (lead_bits(b0, O.a) << (O.b + O.c)) | (lead_bits(b1, O.b) << O.c) | lead_bits(b2, O.c);
     for (int j = 0; j < O.bits; ++j) g ^= ((y >> j) & 1u) ? O.ry[j] : 0u;
-    i = base + gray_inverse(g);
+    i = base + (nied ? g : gray_inverse(g));
     return i >= first && i < first + count;
 }
 

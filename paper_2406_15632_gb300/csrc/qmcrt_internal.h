@@ -15,8 +15,9 @@ namespace qmcrt {
 
 // Point set of Sec. 3.1.  Indices are global point indices (>= 1).
 struct PointsP {
-    int kind;          // QMCRT_SOBOL .. QMCRT_PHILOX
+    int kind;          // QMCRT_SOBOL .. QMCRT_FAURE
     int dims;
+    uint32_t faure_b;  // Faure base: the smallest prime >= dims
     uint64_t seed;
     uint64_t total_n;  // Hammersley N
     double inv_total_n;
@@ -80,7 +81,7 @@ struct AccumP {
 constexpr int NET_MAX_M = 28;
 
 struct OrderP {
-    int net;            // 0 linear, 1 net order
+    int net;            // 0 linear, 1 net order of Sobol (Gray code), 2 of Niederreiter (natural order)
     int m, bits, tt;    // block 2^m, bits = m - tt Morton bits, tt kernel bits
     int a, b, c;        // leading bits taken from coordinates 0, 1, 2
     uint64_t block0;    // first block index

@@ -21,7 +21,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libqmcrt.so")
 
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_DEVICE_TIMEOUT = 0, -1, -2, -3, -4
-KINDS = {"sobol": 0, "sobol_owen": 1, "halton": 2, "hammersley": 3, "philox": 4}
+KINDS = {"sobol": 0, "sobol_owen": 1, "halton": 2, "hammersley": 3, "philox": 4, "niederreiter": 5, "faure": 6}
 FORMATS = {"u32": 0, "f32": 1, "f64": 2}
 MEDIUM_GRID, MEDIUM_SPHERE = 0, 1
 SOURCE_POINT, SOURCE_SPHERE = 0, 1

@@ -19,7 +19,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-GENERATORS = ("sobol", "sobol_owen", "halton", "hammersley", "philox")
+GENERATORS = ("sobol", "sobol_owen", "halton", "hammersley", "philox", "niederreiter", "faure")
 
 
 @dataclass

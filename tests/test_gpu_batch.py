@@ -53,7 +53,7 @@ def alone(Q, prob, I, fb, precision):
     return buf[0, 0].cpu().numpy()
 
 
-@pytest.mark.parametrize("generator", ["sobol", "sobol_owen", "halton", "philox"])
+@pytest.mark.parametrize("generator", ["sobol", "sobol_owen", "halton", "philox", "niederreiter", "faure"])
 @pytest.mark.parametrize("precision", ["f32", "f64"])
 def test_batch_instances_equal_alone_runs(Q, generator, precision):
     import torch

@@ -32,13 +32,15 @@ CASES = [
     ("halton", 5, 1, 1000, 0, 0), ("halton", 80, 4_000_000_000, 257, 0, 0),
     ("hammersley", 5, 1, 1000, 0, 1000), ("hammersley", 3, 5, 95, 0, 99),
     ("philox", 5, 1, 1000, 12345, 0), ("philox", 9, 2 ** 33 + 1, 100, 2 ** 63 + 5, 0),
+    ("niederreiter", 5, 1, 1000, 0, 0), ("niederreiter", 256, 2 ** 31 + 7, 300, 0, 0),
+    ("faure", 3, 1, 1000, 0, 0), ("faure", 5, 3_000_000_000, 257, 0, 0), ("faure", 80, 1, 700, 0, 0),
 ]
 
 
 @pytest.mark.parametrize("kind,dims,first,count,seed,total_n", CASES)
 @pytest.mark.parametrize("fmt", ["u32", "f32", "f64"])
 def test_points_bit_exact(Q, kind, dims, first, count, seed, total_n, fmt):
-    if fmt == "u32" and kind in ("halton", "hammersley"):
+    if fmt == "u32" and kind in ("halton", "hammersley", "faure"):
         pytest.skip("no integer form")
     got = _gpu(Q, kind, dims, first, count, fmt, seed, total_n)
     ref = O.generate_points(kind, dims, first, count, fmt, seed=seed, total_n=total_n)

@@ -63,6 +63,10 @@ SINGLE_CASES = {
     "disk_halton": DISK32.replace(generator="halton"),
     "disk_hammersley": DISK32.replace(generator="hammersley", total_n=1 << 14),
     "disk_philox": DISK32.replace(generator="philox", seed=11),
+    "disk_niederreiter": DISK32.replace(generator="niederreiter"),
+    "disk_faure": DISK32.replace(generator="faure"),
+    "star_niederreiter": DISK32.replace(generator="niederreiter", source="sphere", star_r=0.05, limb_u=0.6,
+                                        emit_order="inverse"),
     "disk_bilinear": DISK32.replace(splat="bilinear"),
     "disk_face_on": DISK32.replace(theta_obs=0.0),
     "star_inverse": DISK32.replace(source="sphere", star_r=0.05, limb_u=0.6, emit_order="inverse"),
@@ -169,6 +173,8 @@ MULTI_CASES = {
     "clumpy_force_all": MULTI,
     "clumpy_force_first": MULTI.replace(force="first", rr_threshold=0.0),
     "clumpy_owen_summed": MULTI.replace(per_order=False, generator="sobol_owen", seed=9),
+    "clumpy_niederreiter": MULTI.replace(per_order=False, generator="niederreiter"),
+    "clumpy_faure": MULTI.replace(per_order=False, generator="faure"),
     "sphere_isotropic": S.homogeneous_sphere_problem(sphere_k=0.8, max_orders=12, g=0.0, p_l=0.3, per_order=True),
 }
 
