@@ -106,6 +106,7 @@ def lib():
             L.or_trace_multiple.argtypes = [P, u64, u64, dp, i32]
             L.or_trace_multiple_warped.argtypes = [P, u64, u64, dp, dp, dp, dp, i32]
             L.or_trace_multiple_cells.argtypes = [P, u64, u64, dp, dp]
+            L.or_direct_light.argtypes = [P, i32, C.c_double, dp]
             L.or_tau_ray.restype = C.c_double
             L.or_tau_ray.argtypes = [P, dp, dp]
             L.or_march_ray.argtypes = [P, dp, dp, C.c_double, dp]
@@ -313,6 +314,16 @@ def trace_multiple_warped(prob, first: int, count: int, x=None, logj=None, train
     if rc != 0:
         raise RuntimeError(f"oracle trace_multiple_warped rc={rc}")
     return (img, tl) if train_log else img
+
+
+def direct_light(prob, subsamples: int = 4, weight: float = 1.0):
+    """Direct light of the source as an image [3][ny][nx] (Stokes I only), times weight."""
+    h = _Holder(prob)
+    img = np.zeros((3, prob.ny, prob.nx), dtype=np.float64)
+    rc = lib().or_direct_light(h.ptr, subsamples, weight, img.ctypes.data_as(C.POINTER(C.c_double)))
+    if rc != 0:
+        raise RuntimeError(f"oracle direct_light rc={rc}")
+    return img
 
 
 def multiple_cells(prob, first: int, count: int):

@@ -1026,6 +1026,56 @@ int or_trace_multiple_warped(const or_problem *Pr, uint64_t first, uint64_t coun
     return or_trace(Pr, first, count, image, NULL, nthreads, 1, x, logj, train_log);
 }
 
+/* Direct (unscattered) light of the source, integrated separately from the source
+ * toward the observer (Sec. 3.4), Stokes I only, added to image[0] times `weight`
+ * (raw images are sums over packets, so weight = N makes it appear once after the
+ * 1/N scaling).  Values are in units of the source luminosity per steradian.
+ *   Point source: e^-tau(0 -> observer) / (4 pi), binned at the sky origin like a
+ *   peel-off contribution.
+ *   Sphere source of radius R and linear limb darkening u: surface brightness
+ *   (1 - u + u mu) / (1 - u/3) / (4 pi) / (pi R^2) per unit sky area at projected
+ *   radius rho, mu = sqrt(1 - rho^2 / R^2) (it integrates to 1 / (4 pi) over the disk),
+ *   attenuated by e^-tau from the visible surface point rho-offset on the facing
+ *   hemisphere toward the observer; each pixel is integrated by an S x S midpoint rule
+ *   over its area. */
+int or_direct_light(const or_problem *Pr, int S, double weight, double *img)
+{
+    const or_observer *O = &Pr->obs;
+    or_view V;
+    or_make_view(O, &V);
+    if (Pr->source.kind == 0) {
+        double origin[3] = {0.0, 0.0, 0.0};
+        double f = exp(-or_tau_to_edge(&Pr->medium, origin, V.k)) / (4.0 * OR_PI) * weight;
+        double out[3] = {f, 0.0, 0.0};
+        or_splat(O, img, 0.0, 0.0, out);
+        return 0;
+    }
+    if (S < 1) return -1;
+    double R = Pr->source.r, u = Pr->source.limb_u;
+    double px = 2.0 * O->half_width / O->nx, py = 2.0 * O->half_width / O->ny;
+    double dA = px * py / ((double)S * S);
+    for (int iy = 0; iy < O->ny; ++iy) {
+        for (int ix = 0; ix < O->nx; ++ix) {
+            double sum = 0.0;
+            for (int b = 0; b < S; ++b) {
+                for (int a = 0; a < S; ++a) {
+                    double x = -O->half_width + (ix + (a + 0.5) / S) * px;
+                    double y = -O->half_width + (iy + (b + 0.5) / S) * py;
+                    double rho2 = x * x + y * y;
+                    if (!(rho2 < R * R)) continue;
+                    double mu = sqrt(1.0 - rho2 / (R * R));
+                    double p[3];
+                    for (int c = 0; c < 3; ++c) p[c] = x * V.ex[c] + y * V.ey[c] + R * mu * V.k[c];
+                    double B = (1.0 - u + u * mu) / (1.0 - u / 3.0) / (4.0 * OR_PI) / (OR_PI * R * R);
+                    sum += B * exp(-or_tau_to_edge(&Pr->medium, p, V.k)) * dA;
+                }
+            }
+            img[(size_t)iy * O->nx + ix] += sum * weight;
+        }
+    }
+    return 0;
+}
+
 /* Grid cells visited by all walks of each packet of the multiple-scattering tracer
  * (one thread); the image goes to `image`.  The per-unit work figure of the
  * multiple-scattering kernel's roofline. */

@@ -325,3 +325,43 @@ def test_warped_estimator_keeps_energy_conservation(use_jacobian):
         assert err < 2e-3
     else:
         assert err > 5e-3
+
+
+def test_direct_light_of_a_point_source_in_a_homogeneous_sphere():
+    """e^-kR / (4 pi) in the pixel holding the sky origin, nothing elsewhere."""
+    k = 0.7
+    p = S.homogeneous_sphere_problem(sphere_k=k, nx=9, ny=9)
+    img = O.direct_light(p)
+    assert img[0, 4, 4] == pytest.approx(math.exp(-k) / (4 * math.pi), rel=1e-14)
+    assert img[0].sum() == pytest.approx(img[0, 4, 4], rel=1e-14) and np.all(img[1:] == 0)
+
+
+@pytest.mark.parametrize("u", [0.0, 0.6, 1.0])
+def test_direct_light_of_a_star_in_vacuum_integrates_to_one_over_4pi(u):
+    """Surface brightness normalised so the disk holds 1 / (4 pi): the midpoint-rule
+    total converges to it as the subsampling grows; for a uniform disk (u = 0) a
+    pixel the disk covers completely holds exactly its area share."""
+    p = S.Problem(grid=np.zeros((4, 4, 4), np.float32), source="sphere", star_r=0.5, limb_u=u, theta_obs=0.9,
+                  phi_obs=0.4, half_width=0.6, nx=24, ny=24)
+    totals = [O.direct_light(p, s)[0].sum() for s in (2, 8, 32)]
+    errs = [abs(t * 4 * math.pi - 1) for t in totals]
+    assert errs[2] < 2e-3 and errs[2] < errs[0]
+    if u == 0.0:
+        img = O.direct_light(p, 3)[0]
+        pix = (2 * 0.6 / 24) ** 2
+        assert img[12, 12] == pytest.approx(pix / (math.pi * 0.25) / (4 * math.pi), rel=1e-12)
+
+
+def test_direct_light_of_a_star_is_dimmed_by_the_medium_in_front():
+    """A slab of extinction in front of the star (toward the observer) dims every
+    pixel by e^-(k L) with L the slab thickness along the line of sight, when the slab
+    is crossed completely; an empty grid changes nothing."""
+    n = 8
+    grid = np.zeros((n, n, n), np.float32)
+    grid[:, :, 6] = 2.0  # x in [0.5, 0.75): a slab across the x axis, in front of an observer on +x
+    base = S.Problem(grid=np.zeros((n, n, n), np.float32), source="sphere", star_r=0.3, limb_u=0.5,
+                     theta_obs=math.pi / 2, phi_obs=0.0, half_width=0.4, nx=16, ny=16)
+    clear = O.direct_light(base, 4)[0]
+    dim = O.direct_light(base.replace(grid=grid), 4)[0]
+    mask = clear > 0
+    assert np.allclose(dim[mask] / clear[mask], math.exp(-2.0 * 0.25), rtol=1e-12)
