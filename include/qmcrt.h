@@ -355,6 +355,23 @@ int qmcrt_warp_adam(const qmcrt_warp *warp, const float *d_grad, float *d_m, flo
 int qmcrt_pad_grid(const float *d_k, int32_t nx, int32_t ny, int32_t nz, int32_t pad, float *d_padded, void *stream);
 
 /*
+ * qmcrt_direct_light -- adds the source's direct (unscattered) light to image 0 of the
+ * accumulator, integrated from the source toward the observer (Sec. 3.4), Stokes I
+ * only, multiplied by `weight` (images are raw sums over packets: weight = N makes the
+ * direct light appear once after qmcrt_image_reduce's 1/N).  Units: source luminosity
+ * per steradian.  Point source: e^-tau(0 -> observer) / (4 pi), binned at the sky
+ * origin with the observer's splat.  Sphere source (radius R, limb darkening u): the
+ * visible disk's surface brightness (1 - u + u mu) / (1 - u/3) / (4 pi) / (pi R^2) per
+ * unit sky area, attenuated from the visible surface point, integrated over each pixel
+ * by a subsamples x subsamples midpoint rule.  opts: only precision is read.
+ * Errors: INVALID_ARG (descriptors as qmcrt_trace_single, subsamples outside 1..64,
+ * weight negative or not finite, image->n_images != 1), CUDA.
+ */
+int qmcrt_direct_light(const qmcrt_medium *medium, const qmcrt_source *source, const qmcrt_observer *obs,
+                       int32_t subsamples, double weight, const qmcrt_trace_opts *opts, const qmcrt_image *image,
+                       void *stream);
+
+/*
  * qmcrt_trace_observers -- one trace feeding several observers (Sec. 3.6: the peel-off
  * is repeated toward each observer from the same scattering events).  Emission,
  * forced depths and scattering are done once per packet; the optical depth toward

@@ -463,6 +463,41 @@ int qmcrt_trace_observers(const qmcrt_medium *medium, const qmcrt_source *source
     return observers_common<float>(medium, source, dust, obs, n_obs, pts, opts, image, s);
 }
 
+int qmcrt_direct_light(const qmcrt_medium *medium, const qmcrt_source *source, const qmcrt_observer *obs,
+                       int32_t subsamples, double weight, const qmcrt_trace_opts *opts, const qmcrt_image *image,
+                       void *stream)
+{
+    g_last_error.clear();
+    CHECK_STRUCT(source, qmcrt_source);
+    CHECK_STRUCT(opts, qmcrt_trace_opts);
+    if (subsamples < 1 || subsamples > 64) return fail(QMCRT_ERR_INVALID_ARG, "subsamples %d outside 1..64", subsamples);
+    if (!(weight >= 0) || !std::isfinite(weight)) return fail(QMCRT_ERR_INVALID_ARG, "weight must be finite, >= 0");
+    qmcrt_dust dust;
+    memset(&dust, 0, sizeof dust);
+    dust.struct_size = sizeof dust;
+    dust.albedo = 1.0;
+    qmcrt_points_desc pts;
+    memset(&pts, 0, sizeof pts);
+    pts.struct_size = sizeof pts;
+    pts.kind = QMCRT_SOBOL;
+    pts.dims = 5;
+    pts.first_index = 1;
+    pts.count = 0;
+    qmcrt_trace_opts o = *opts;
+    o.max_orders = 1;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (opts->precision == QMCRT_PREC_F64) {
+        qmcrt::TraceP<double> P;
+        int rc = fill_trace<double>(medium, source, &dust, obs, &pts, &o, image, 0, P);
+        if (rc) return rc;
+        return cuda_status(qmcrt::launch_direct_light_f64(P, subsamples, weight, s), "direct_light launch");
+    }
+    qmcrt::TraceP<float> P;
+    int rc = fill_trace<float>(medium, source, &dust, obs, &pts, &o, image, 0, P);
+    if (rc) return rc;
+    return cuda_status(qmcrt::launch_direct_light_f32(P, subsamples, weight, s), "direct_light launch");
+}
+
 uint64_t qmcrt_batch_workspace_bytes(int32_t n_instances)
 {
     if (n_instances < 0) return 0;

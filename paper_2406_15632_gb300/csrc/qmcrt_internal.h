@@ -130,6 +130,9 @@ struct ObsSet {
 cudaError_t launch_trace_observers_f32(const TraceP<float> &p, const ObsSet<float> &obs, int block, cudaStream_t s);
 cudaError_t launch_trace_observers_f64(const TraceP<double> &p, const ObsSet<double> &obs, int block, cudaStream_t s);
 
+cudaError_t launch_direct_light_f32(const TraceP<float> &p, int subsamples, double weight, cudaStream_t s);
+cudaError_t launch_direct_light_f64(const TraceP<double> &p, int subsamples, double weight, cudaStream_t s);
+
 struct GemmEpi;
 cudaError_t launch_gemm_bf16(const __nv_bfloat16 *A, const __nv_bfloat16 *B, int M, int N, int K, int splits,
                              const GemmEpi &ep, cudaStream_t s);

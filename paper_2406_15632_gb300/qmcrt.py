@@ -133,6 +133,8 @@ _SIGS = [
     ("qmcrt_trace_observers", C.c_int, [_P(qmcrt_medium), _P(qmcrt_source), _P(qmcrt_dust), _P(qmcrt_observer),
                                         C.c_int32, _P(qmcrt_points_desc), _P(qmcrt_trace_opts), _P(qmcrt_image),
                                         C.c_void_p]),
+    ("qmcrt_direct_light", C.c_int, [_P(qmcrt_medium), _P(qmcrt_source), _P(qmcrt_observer), C.c_int32, C.c_double,
+                                     _P(qmcrt_trace_opts), _P(qmcrt_image), C.c_void_p]),
     ("qmcrt_batch_workspace_bytes", C.c_uint64, [C.c_int32]),
     ("qmcrt_trace_batch", C.c_int, [_P(qmcrt_medium), _P(qmcrt_source), _P(qmcrt_observer), _P(qmcrt_points_desc),
                                     _P(qmcrt_trace_opts), C.c_void_p, C.c_int32, _P(qmcrt_batch_config), C.c_void_p,
@@ -350,6 +352,11 @@ def qmcrt_pad_grid(d_k: int, nx: int, ny: int, nz: int, pad: int, d_padded: int,
 MAX_OBSERVERS = 16
 
 
+def qmcrt_direct_light(medium, source, obs, subsamples: int, weight: float, opts, image, stream: int = 0) -> None:
+    _check(load().qmcrt_direct_light(C.byref(medium), C.byref(source), C.byref(obs), subsamples, weight,
+                                     C.byref(opts), C.byref(image), C.c_void_p(stream)))
+
+
 def qmcrt_trace_observers(medium, source, dust, obs_array, n_obs: int, pts, opts, image, stream: int = 0) -> None:
     _check(load().qmcrt_trace_observers(C.byref(medium), C.byref(source), C.byref(dust), obs_array, n_obs, C.byref(pts),
                                         C.byref(opts), C.byref(image), C.c_void_p(stream)))
@@ -520,6 +527,12 @@ class Scene:
         ptr = lambda t: t.data_ptr() if t is not None else 0
         qmcrt_trace_multiple_warped(self.medium, self.source, self.dust, self.obs, pts, self.opts(precision), ptr(x),
                                     ptr(logj), img, ptr(train_log), _stream(stream))
+
+    def direct_light(self, buf, *, weight: float = 1.0, subsamples: int = 4, accum: str = "i64", frac_bits: int = 0,
+                     precision: str = "f32", stream=None) -> None:
+        """Add the source's direct light (times weight) to image 0 of buf."""
+        qmcrt_direct_light(self.medium, self.source, self.obs, subsamples, weight, self.opts(precision),
+                           self.image_desc(buf, accum, frac_bits), _stream(stream))
 
     def observer_array(self, angles, half_widths=None):
         """ctypes array of observers at (theta, phi) pairs sharing this problem's image
