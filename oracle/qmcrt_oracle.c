@@ -673,9 +673,12 @@ typedef struct {
 } or_source;
 
 /* Emission: position, direction, Stokes reference axis and weight from the first
- * coordinates of the point.  Returns the coordinate that sets the first depth. */
+ * coordinates of the point.  Returns the coordinate that sets the first depth.
+ * Coordinates 0, 1 give the emission point (direct order) or the direction (inverse
+ * order); c0, c1 the other pair and cw the depth (single scattering: the paper's order,
+ * direct c0, c1, cw = 2, 3, 4 and inverse 3, 4, 2). */
 static double or_emit(const or_source *S, const or_points *P, uint64_t i, double pos[3], double dir[3],
-                      double eref[3], double *weight)
+                      double eref[3], double *weight, int c0, int c1, int cw)
 {
     double et[3], ep[3];
     *weight = 1.0;
@@ -697,15 +700,15 @@ static double or_emit(const or_source *S, const or_points *P, uint64_t i, double
         from_angles(2.0 * or_point_f64(P, i, 1) - 1.0, or_point_f64(P, i, 0), ne);
         for (int a = 0; a < 3; ++a) pos[a] = S->r * ne[a];
         double spl, cpl;
-        sincos_2pi(or_point_f64(P, i, 2), &spl, &cpl);
-        mu = sqrt(or_point_f64(P, i, 3));
+        sincos_2pi(or_point_f64(P, i, c0), &spl, &cpl);
+        mu = sqrt(or_point_f64(P, i, c1));
         double sl = sqrt(fmax(0.0, 1.0 - mu * mu));
         sph_basis(ne, et, ep);
         for (int a = 0; a < 3; ++a) dir[a] = sl * cpl * et[a] + sl * spl * ep[a] + mu * ne[a];
         normalize3(dir);
         sph_basis(dir, eref, ep);
         if (S->limb_u != 0) *weight = (1.0 - S->limb_u + S->limb_u * mu) / (1.0 - S->limb_u / 3.0);
-        return or_point_f64(P, i, 4);
+        return or_point_f64(P, i, cw);
     }
     /* Inverse order: v1, v2 the direction as for a point source, v3 the depth, v4, v5
      * the emission point relative to the direction.  Reading: the point is uniform on
@@ -713,8 +716,8 @@ static double or_emit(const or_source *S, const or_points *P, uint64_t i, double
      * 2 pi v5) lifted onto the hemisphere facing the direction, which gives the same
      * joint density of (point, direction) as the direct order. */
     from_angles(2.0 * or_point_f64(P, i, 1) - 1.0, or_point_f64(P, i, 0), dir);
-    double w = or_point_f64(P, i, 2);
-    double v4 = or_point_f64(P, i, 3), v5 = or_point_f64(P, i, 4);
+    double w = or_point_f64(P, i, cw);
+    double v4 = or_point_f64(P, i, c0), v5 = or_point_f64(P, i, c1);
     double rho = S->r * sqrt(v4), sps, cps;
     sincos_2pi(v5, &sps, &cps);
     double lift = sqrt(fmax(0.0, S->r * S->r - rho * rho));
@@ -724,6 +727,14 @@ static double or_emit(const or_source *S, const or_points *P, uint64_t i, double
     mu = sqrt(fmax(0.0, 1.0 - v4));
     if (S->limb_u != 0) *weight = (1.0 - S->limb_u + S->limb_u * mu) / (1.0 - S->limb_u / 3.0);
     return w;
+}
+
+/* Emission with the single-scattering coordinate order of Sec. 3.3. */
+static double or_emit_single(const or_source *S, const or_points *P, uint64_t i, double pos[3], double dir[3],
+                             double eref[3], double *weight)
+{
+    int direct = S->order == 0;
+    return or_emit(S, P, i, pos, dir, eref, weight, direct ? 2 : 3, direct ? 3 : 4, direct ? 4 : 2);
 }
 
 /* ------------------------------------------------------------------------------ */
@@ -824,7 +835,7 @@ static void or_trace_single_range(const or_problem *Pr, uint64_t first, uint64_t
         uint64_t i = first + j;
         double pos[3], dir[3], eref[3], wgt, W1 = 0, tau1 = 0, S[3], out[3], x = 0, y = 0;
         or_cells_visited = 0;
-        double w = or_emit(&Pr->source, &Pr->points, i, pos, dir, eref, &wgt);
+        double w = or_emit_single(&Pr->source, &Pr->points, i, pos, dir, eref, &wgt);
         int status = 0;
         out[0] = out[1] = out[2] = 0;
         if (!or_forced_step(Pr, pos, dir, w, &W1, &tau1)) {
@@ -905,7 +916,9 @@ static void or_trace_multiple_range(const or_problem *Pr, uint64_t first, uint64
             w = wx[3 * j + 2];
             wgt = exp(wlogj[j]);
         } else {
-            w = or_emit(&Pr->source, &Pr->points, i, pos, n, a, &wgt);
+            /* a finite star's two other emission coordinates follow all orders' ones */
+            int e = 4 * Pr->max_orders;
+            w = or_emit(&Pr->source, &Pr->points, i, pos, n, a, &wgt, e, e + 1, 2);
         }
         const double w_first = w;
         double S[3] = {wgt, 0.0, 0.0};
@@ -1009,7 +1022,6 @@ int or_trace_single(const or_problem *Pr, uint64_t first, uint64_t count, double
 
 int or_trace_multiple(const or_problem *Pr, uint64_t first, uint64_t count, double *image, int nthreads)
 {
-    if (Pr->source.kind != 0) return -3; /* multiple scattering: point source only */
     return or_trace(Pr, first, count, image, NULL, nthreads, 1, NULL, NULL, NULL);
 }
 
@@ -1021,7 +1033,7 @@ int or_trace_multiple(const or_problem *Pr, uint64_t first, uint64_t count, doub
 int or_trace_multiple_warped(const or_problem *Pr, uint64_t first, uint64_t count, const double *x,
                              const double *logj, double *image, double *train_log, int nthreads)
 {
-    if (Pr->source.kind != 0) return -3;
+    if (Pr->source.kind != 0 && x) return -3; /* the warp replaces point-source coordinates only */
     if ((x == NULL) != (logj == NULL)) return -2;
     return or_trace(Pr, first, count, image, NULL, nthreads, 1, x, logj, train_log);
 }
@@ -1081,7 +1093,6 @@ int or_direct_light(const or_problem *Pr, int S, double weight, double *img)
  * multiple-scattering kernel's roofline. */
 int or_trace_multiple_cells(const or_problem *Pr, uint64_t first, uint64_t count, double *image, double *cells)
 {
-    if (Pr->source.kind != 0) return -3;
     or_trace_multiple_range(Pr, first, count, image, NULL, NULL, NULL, cells);
     return 0;
 }
@@ -1116,5 +1127,5 @@ int or_peel_packet(const or_problem *Pr, const double pos[3], const double n[3],
 double or_emit_packet(const or_problem *Pr, uint64_t i, double pos[3], double dir[3], double eref[3],
                       double *weight)
 {
-    return or_emit(&Pr->source, &Pr->points, i, pos, dir, eref, weight);
+    return or_emit_single(&Pr->source, &Pr->points, i, pos, dir, eref, weight);
 }

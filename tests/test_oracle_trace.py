@@ -365,3 +365,34 @@ def test_direct_light_of_a_star_is_dimmed_by_the_medium_in_front():
     dim = O.direct_light(base.replace(grid=grid), 4)[0]
     mask = clear > 0
     assert np.allclose(dim[mask] / clear[mask], math.exp(-2.0 * 0.25), rtol=1e-12)
+
+
+def test_multiple_scattering_from_a_vanishing_star_is_the_point_source():
+    """Inverse order reads direction and first depth from coordinates 0, 1, 2 as the
+    point source does (its two emission coordinates come after all orders'), so a star
+    of vanishing radius gives the point-source image of multiple scattering.  (Owen-
+    scrambled points: unscrambled Sobol points send some rays exactly along the cell
+    faces through the origin, where a source 1e-9 off the face sees the neighbouring
+    column of cells.)"""
+    p = S.clumpy_problem(n=16, max_orders=5, nx=32, ny=32, generator="sobol_owen", seed=5)
+    N = 1 << 12
+    pt = O.trace_multiple(p, 1, N)
+    st = O.trace_multiple(p.replace(source="sphere", star_r=1e-9, emit_order="inverse"), 1, N)
+    assert np.abs(st - pt).sum() <= 1e-6 * np.abs(pt).sum()
+
+
+@pytest.mark.parametrize("order", ["inverse", "direct"])
+def test_energy_conservation_of_a_small_star(order):
+    """A star of radius 1e-3 (uniform disk) at the centre of the homogeneous sphere:
+    with albedo 1 and every order forced the scattered light integrated over all
+    directions is 1 - e^-k(1 - R) up to the star's own size."""
+    k = 0.6
+    p = S.homogeneous_sphere_problem(sphere_k=k, max_orders=30, albedo=1.0, g=0.0, source="sphere", star_r=1e-3,
+                                     limb_u=0.0, emit_order=order)
+    N = 1 << 14
+    tot = 0.0
+    dirs = [(math.pi / 2, 0.0), (0.3, 1.0), (2.2, 4.0), (1.0, 2.5)]
+    for th, ph in dirs:
+        img = O.trace_multiple(p.replace(theta_obs=th, phi_obs=ph), 1, N)
+        tot += 4 * math.pi * img[:, 0].sum() / N / len(dirs)
+    assert tot == pytest.approx(1 - math.exp(-k), rel=4e-3)
