@@ -184,16 +184,21 @@ int qmcrt_trace_single(const qmcrt_medium *medium, const qmcrt_source *source, c
                        const qmcrt_image *image, double *d_log, void *stream);
 
 /*
- * qmcrt_trace_multiple -- multiple scattering of a point source (Sec. 3.5, 3.7).
+ * qmcrt_trace_multiple -- multiple scattering (Sec. 3.5, 3.7).
  * Order k (1-based) reads coordinates 4(k-1) + {0: azimuth i1 = 2 pi u (emission
  * phi at k = 1), 1: cos Theta from the HG inverse (emission theta at k = 1), 2: depth,
  * 3: roulette}.  After the peel-off of order k the packet is rouletted if its weight
  * is below rr_threshold, then scattered: the direction from HG, the Stokes vector
  * rotated into the scattering plane and multiplied by M(Theta)/P11.  Orders stop at
  * max_orders, at tau_edge < tau_min, on leaving the grid (FORCE_FIRST) or by roulette.
- * pts->dims must be >= 4 * max_orders.  image->n_images must be max_orders when
- * per_order is set, else 1.
- * Errors: as qmcrt_trace_single; UNSUPPORTED for a sphere source.
+ * A sphere source (the paper treats it in single scattering only, Sec. 7) emits as in
+ * qmcrt_trace_single with coordinates 0, 1 (emission point in the direct order,
+ * direction in the inverse order) and 2 (first depth); its other two emission
+ * coordinates are 4 max_orders and 4 max_orders + 1.  Later flights are not stopped by
+ * the star; peel-offs it hides are dropped.  pts->dims must be >= 4 * max_orders (+ 2
+ * for a sphere source).  image->n_images must be max_orders when per_order is set,
+ * else 1.
+ * Errors: as qmcrt_trace_single.
  */
 int qmcrt_trace_multiple(const qmcrt_medium *medium, const qmcrt_source *source, const qmcrt_dust *dust,
                          const qmcrt_observer *obs, const qmcrt_points_desc *pts, const qmcrt_trace_opts *opts,

@@ -247,7 +247,6 @@ int fill_trace(const qmcrt_medium *md, const qmcrt_source *src, const qmcrt_dust
         if (!(src->limb_u >= 0 && src->limb_u <= 1)) return fail(QMCRT_ERR_INVALID_ARG, "limb_u outside [0, 1]");
         if (src->order != QMCRT_ORDER_DIRECT && src->order != QMCRT_ORDER_INVERSE)
             return fail(QMCRT_ERR_INVALID_ARG, "unknown emission order %d", src->order);
-        if (multiple) return fail(QMCRT_ERR_UNSUPPORTED, "multiple scattering supports the point source only");
         P.src.kind = src->kind;
         P.src.order = src->order;
         P.src.R = (T)src->radius;
@@ -293,7 +292,8 @@ int fill_trace(const qmcrt_medium *md, const qmcrt_source *src, const qmcrt_dust
         P.inv_rr_survival = (T)(1.0 / op->rr_survival);
     }
     // points
-    const uint32_t need = multiple ? 4u * (uint32_t)op->max_orders : (src->kind == QMCRT_SOURCE_SPHERE ? 5u : 3u);
+    const uint32_t need = multiple ? 4u * (uint32_t)op->max_orders + (src->kind == QMCRT_SOURCE_SPHERE ? 2u : 0u)
+                                   : (src->kind == QMCRT_SOURCE_SPHERE ? 5u : 3u);
     int rc = check_points(pts, need);
     if (rc) return rc;
     P.pts = make_points(pts);

@@ -120,7 +120,7 @@ __device__ __forceinline__ uint32_t niederreiter_u32(uint32_t i, int d)
 // (n_k the base-b digits of i, j the dimension), i.e. the coefficients of N(X + j) for
 // N(X) = sum n_k X^k, computed by the Taylor shift (repeated synthetic division) mod b;
 // the value is the exact fraction y / b^K rounded once.
-__device__ __forceinline__ double faure_f64(uint32_t i, int d, uint32_t b)
+static __device__ __noinline__ double faure_f64(uint32_t i, int d, uint32_t b)  // off the hot path (own frame)
 {
     uint32_t a[32];
     int K = 0;
@@ -267,9 +267,16 @@ __device__ __forceinline__ bool packet_index(const OrderP &O, uint64_t first, ui
     for (int j = 0; j < O.bits; ++j) g ^= ((box >> j) & 1u) ? O.rm[j] : 0u;
     for (int j = 0; j < O.tt; ++j) g ^= ((tl >> j) & 1u) ? O.k[j] : 0u;
     const bool nied = O.net == 2;
-    const uint32_t b0 = nied ? niederreiter_u32((uint32_t)base, 0) : sobol_u32((uint32_t)base, 0);
-    const uint32_t b1 = nied ? niederreiter_u32((uint32_t)base, 1) : sobol_u32((uint32_t)base, 1);
-    const uint32_t b2 = nied ? niederreiter_u32((uint32_t)base, 2) : sobol_u32((uint32_t)base, 2);
+    uint32_t b0, b1, b2;
+    if (nied) {
+        b0 = niederreiter_u32((uint32_t)base, 0);
+        b1 = niederreiter_u32((uint32_t)base, 1);
+        b2 = niederreiter_u32((uint32_t)base, 2);
+    } else {
+        b0 = sobol_u32((uint32_t)base, 0);
+        b1 = sobol_u32((uint32_t)base, 1);
+        b2 = sobol_u32((uint32_t)base, 2);
+    }
     const uint32_t y = (lead_bits(b0, O.a) << (O.b + O.c)) | (lead_bits(b1, O.b) << O.c) | lead_bits(b2, O.c);
     for (int j = 0; j < O.bits; ++j) g ^= ((y >> j) & 1u) ? O.ry[j] : 0u;
     i = base + (nied ? g : gray_inverse(g));
@@ -651,10 +658,14 @@ __device__ __forceinline__ void e_theta_of(const T d[3], T et[3])
     et[2] = -s;
 }
 
-// Emission of packet i: position, direction, Stokes axis, weight; returns the depth
-// coordinate w.
+// Emission of packet i (Sec. 3.2, 3.3): position, direction, Stokes axis, weight;
+// returns the depth coordinate w.  Coordinates 0, 1 set the emission point (direct order) or
+// the direction (inverse order); c0, c1 the other pair (local direction, or the point
+// on the projected disk); cw the first depth.  Single scattering reads them in the
+// paper's order (direct: c0 = 2, c1 = 3, cw = 4; inverse: cw = 2, c0 = 3, c1 = 4).
 template <class T>
-__device__ __forceinline__ T emit(const TraceP<T> &P, uint64_t i, T pos[3], T d[3], T a[3], T &wgt)
+__device__ __forceinline__ T emit(const TraceP<T> &P, uint64_t i, T pos[3], T d[3], T a[3], T &wgt, int c0, int c1,
+                                  int cw)
 {
     wgt = T(1);
     T sp, cp;
@@ -672,8 +683,8 @@ __device__ __forceinline__ T emit(const TraceP<T> &P, uint64_t i, T pos[3], T d[
         direction_from(point<T>(P.pts, i, 0), point<T>(P.pts, i, 1), ne, et, sp, cp);
         const T ep[3] = {-sp, cp, T(0)};
         T spl, cpl;
-        Mth<T>::sincospi_(T(2) * point<T>(P.pts, i, 2), &spl, &cpl);
-        const T v4 = point<T>(P.pts, i, 3);
+        Mth<T>::sincospi_(T(2) * point<T>(P.pts, i, c0), &spl, &cpl);
+        const T v4 = point<T>(P.pts, i, c1);
         mu = Mth<T>::sqrt_(v4);
         const T sl = Mth<T>::sqrt_(Mth<T>::max_(T(1) - v4, T(0)));
         for (int q = 0; q < 3; ++q) {
@@ -682,16 +693,16 @@ __device__ __forceinline__ T emit(const TraceP<T> &P, uint64_t i, T pos[3], T d[
         }
         normalize3(d);
         e_theta_of(d, a);
-        w = point<T>(P.pts, i, 4);
+        w = point<T>(P.pts, i, cw);
     } else {
         // v1, v2: direction; v3: depth; v4, v5: emission point uniform on the star's
         // projected disk across the direction, lifted onto the facing hemisphere.
         direction_from(point<T>(P.pts, i, 0), point<T>(P.pts, i, 1), d, a, sp, cp);
         const T ep[3] = {-sp, cp, T(0)};
-        w = point<T>(P.pts, i, 2);
-        const T v4 = point<T>(P.pts, i, 3);
+        w = point<T>(P.pts, i, cw);
+        const T v4 = point<T>(P.pts, i, c0);
         T sps, cps;
-        Mth<T>::sincospi_(T(2) * point<T>(P.pts, i, 4), &sps, &cps);
+        Mth<T>::sincospi_(T(2) * point<T>(P.pts, i, c1), &sps, &cps);
         const T rho = R * Mth<T>::sqrt_(v4);
         mu = Mth<T>::sqrt_(Mth<T>::max_(T(1) - v4, T(0)));
         const T lift = R * mu;
@@ -699,6 +710,13 @@ __device__ __forceinline__ T emit(const TraceP<T> &P, uint64_t i, T pos[3], T d[
     }
     wgt = (T(1) - P.src.limb_u + P.src.limb_u * mu) * P.src.limb_norm;
     return w;
+}
+
+template <class T>
+__device__ __forceinline__ T emit(const TraceP<T> &P, uint64_t i, T pos[3], T d[3], T a[3], T &wgt)
+{
+    const bool direct = P.src.order == QMCRT_ORDER_DIRECT;
+    return emit(P, i, pos, d, a, wgt, direct ? 2 : 3, direct ? 3 : 4, direct ? 4 : 2);
 }
 
 // ------------------------------------------------------------------------------------

@@ -1,7 +1,8 @@
 // qmcrt_orders.cuh -- the scattering orders of one packet (Sec. 3.5, 3.7), shared by
 // the multiple-scattering kernels for one observer and for a set of observers.
 //
-// Order k reads coordinates 4(k-1) + {0 azimuth, 1 cos Theta, 2 depth, 3 roulette}; with
+// Order k reads coordinates 4(k-1) + {0 azimuth, 1 cos Theta, 2 depth, 3 roulette}; a
+// finite star reads its two other emission coordinates at 4 max_orders + {0, 1}; with
 // a learned warp the first-order coordinates come from a buffer (x = T(u)) and the
 // weight starts at |dx/du|.  The order loop is uniform across the warp, so the
 // peel-off callback (which bins into images) is reached by all 32 lanes; the warp
@@ -30,7 +31,9 @@ __device__ __forceinline__ void trace_orders(const TraceP<T> &P, uint64_t i, uin
             wd = (T)P.warp_x[3 * j + 2];
             wgt = Mth<T>::exp_((T)P.warp_logj[j]);
         } else {
-            wd = emit(P, i, pos, n, a, wgt);
+            // a finite star's two extra emission coordinates follow all orders' coordinates
+            const int e = 4 * P.max_orders;
+            wd = emit(P, i, pos, n, a, wgt, e, e + 1, 2);
         }
         S[0] = wgt;
     }

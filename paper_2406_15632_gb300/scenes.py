@@ -67,8 +67,8 @@ class Problem:
     @property
     def dims(self) -> int:
         """Coordinates one packet consumes (one long vector per packet, Sec. 3.7)."""
-        if self.max_orders > 1:
-            return 4 * self.max_orders
+        if self.max_orders > 1:  # a finite star's two extra emission coordinates go last
+            return 4 * self.max_orders + (2 if self.source == "sphere" else 0)
         return 5 if self.source == "sphere" else 3
 
     def replace(self, **kw) -> "Problem":

@@ -157,9 +157,10 @@ def test_trace_multiple_validation(lib):
     d["pts"].dims = 12
     _expect(Q.ERR_INVALID_ARG, Q.qmcrt_trace_multiple, d["medium"], d["source"], d["dust"], d["obs"], d["pts"],
             d["opts"], d["img"], 0)
+    # a finite star needs its two extra emission coordinates after all orders' ones
     d = _descs(opts__max_orders=3, source__kind=1, source__radius=0.1)
-    d["pts"].dims = 12
-    _expect(Q.ERR_UNSUPPORTED, Q.qmcrt_trace_multiple, d["medium"], d["source"], d["dust"], d["obs"], d["pts"],
+    d["pts"].dims = 13
+    _expect(Q.ERR_INVALID_ARG, Q.qmcrt_trace_multiple, d["medium"], d["source"], d["dust"], d["obs"], d["pts"],
             d["opts"], d["img"], 0)
 
 

@@ -52,6 +52,8 @@ CASES = {
     "star_single": S.finite_star_disk_problem(n=32, nx=40, ny=36),
     "disk_bilinear": S.flared_disk_problem(n=32, nx=40, ny=36, splat="bilinear"),
     "clumpy_multiple": S.clumpy_problem(n=16, max_orders=6, nx=40, ny=36, per_order=True),
+    "clumpy_star_multiple": S.clumpy_problem(n=16, max_orders=4, nx=40, ny=36).replace(
+        source="sphere", star_r=0.06, limb_u=0.5),
 }
 
 

@@ -174,6 +174,9 @@ MULTI_CASES = {
     "clumpy_force_first": MULTI.replace(force="first", rr_threshold=0.0),
     "clumpy_owen_summed": MULTI.replace(per_order=False, generator="sobol_owen", seed=9),
     "clumpy_niederreiter": MULTI.replace(per_order=False, generator="niederreiter"),
+    "clumpy_star_inverse": MULTI.replace(source="sphere", star_r=0.06, limb_u=0.6, emit_order="inverse"),
+    "clumpy_star_direct": MULTI.replace(per_order=False, source="sphere", star_r=0.06, limb_u=0.6,
+                                        emit_order="direct", generator="sobol_owen", seed=2),
     "clumpy_faure": MULTI.replace(per_order=False, generator="faure"),
     "sphere_isotropic": S.homogeneous_sphere_problem(sphere_k=0.8, max_orders=12, g=0.0, p_l=0.3, per_order=True),
 }
