@@ -420,15 +420,30 @@ def run_time_to_error_learned(ladder=(20, 22, 24, 26), ref_log2=28, ref_seeds=(1
 
 
 def run_time_to_error_disk(ladder=(20, 22, 24, 26), ref_log2=28, ref_seeds=(101, 102, 103, 104)):
-    """The paper's comparison on the single-scattering flared disk (256^3, 256x256
-    I/Q/U, 45 degrees): wall time to a fixed image error for Sobol, Owen-scrambled
-    Sobol, Niederreiter, Faure, Halton, Hammersley (its own set of N points for every
-    N) and Philox MC, all through the same FP32 tracer with fixed-point accumulation."""
+    return run_time_to_error_qmc(workload_problem(), "flared disk 256^3 single scattering, point source, "
+                                 "theta 45 deg, 256x256 I/Q/U, FP32 trace, int64 accumulate", ladder, ref_log2, ref_seeds)
+
+
+def run_time_to_error_geometries(ladder=(20, 22, 24, 26), ref_log2=27, ref_seeds=(101, 102, 103, 104)):
+    """The paper's other test geometries (Sec. 5) through the same comparison: the disk
+    seen from the pole, the dust shell and the fractal cloud."""
+    from paper_2406_15632_gb300 import scenes as S
+
+    cases = {"disk_pole": (workload_problem().replace(theta_obs=0.0), "flared disk 256^3 seen from the pole"),
+             "shell": (S.shell_envelope_problem(), "dust shell 256^3 (radial tau 0.1), pole-on"),
+             "fractal": (S.fractal_cloud_problem(), "fractal cloud 200^3 (N 32, D 2.3, tau 2), theta 60 deg")}
+    return {k: run_time_to_error_qmc(p, w, ladder, ref_log2, ref_seeds) for k, (p, w) in cases.items()}
+
+
+def run_time_to_error_qmc(prob, workload, ladder=(20, 22, 24, 26), ref_log2=28, ref_seeds=(101, 102, 103, 104)):
+    """The paper's comparison (Sec. 6) on one single-scattering problem: wall time to a
+    fixed image error for Sobol, Owen-scrambled Sobol, Niederreiter, Faure, Halton,
+    Hammersley (its own set of N points for every N) and Philox MC, all through the same
+    FP32 tracer with fixed-point accumulation, against an Owen-scrambled reference."""
     import torch
 
     from paper_2406_15632_gb300 import qmcrt as Q
 
-    prob = workload_problem()
     base = Q.Scene(prob)
     ref, ref_err, ref_n = _reference_image(Q, prob, base.grid, ref_log2, ref_seeds, "i64")
 
@@ -461,7 +476,7 @@ def run_time_to_error_disk(ladder=(20, 22, 24, 26), ref_log2=28, ref_seeds=(101,
         for k in gens:
             if k != "mc_philox" and row[k]["ms"] and m:
                 row[k]["speedup_vs_mc"] = m / row[k]["ms"]
-    return {"workload": "flared disk 256^3 single scattering, point source, 256x256 I/Q/U, FP32 trace, int64 accumulate",
+    return {"workload": workload,
             "error": "RMS relative of the I image (L1 relative, the paper's norm, also listed)",
             "reference": {"packets": ref_n, "generator": "sobol_owen", "seeds": list(ref_seeds),
                           "estimated_rms_error": ref_err},
@@ -626,7 +641,8 @@ def main():
         line["batched"] = run_batched()
         line["observers"] = run_observers()
         line["time_to_error"] = {"learned_vs_plain": run_time_to_error_learned(),
-                                 "qmc_vs_mc_disk": run_time_to_error_disk()}
+                                 "qmc_vs_mc_disk": run_time_to_error_disk(),
+                                 "qmc_vs_mc_geometries": run_time_to_error_geometries()}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = run_cpu_baseline()
     print(json.dumps(line), flush=True)

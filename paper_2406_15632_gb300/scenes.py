@@ -110,6 +110,18 @@ def random_grid(n: int = 4, seed: int = 0, kmax: float = 2.0) -> np.ndarray:
     return rng.uniform(0.0, kmax, size=(n, n, n)).astype(np.float32)
 
 
+def shell_envelope_grid(n: int = 256, r_in: float = 500.0 / 600.0, r_out: float = 550.0 / 600.0,
+                        tau: float = 0.1) -> np.ndarray:
+    """The paper's dust sphere envelope (Eq. sphere): constant density between r_in and
+    r_out (500 and 550 au on a 600 au half-width cube), sampled at cell centres of
+    [-1, 1]^3; the radial optical depth of the shell is tau (the paper gives the
+    density in g cm^-3 without the opacity, so the depth is a chosen value)."""
+    c = cell_centres(n)
+    r = np.sqrt(c[:, None, None] ** 2 + c[None, :, None] ** 2 + c[None, None, :] ** 2)
+    k = np.where((r >= r_in) & (r <= r_out), tau / (r_out - r_in), 0.0)
+    return np.ascontiguousarray(k.astype(np.float32))
+
+
 def clumpy_envelope_grid(n: int = 128, tau_radial: float = 5.0, r_in: float = 0.05, r_out: float = 1.0,
                          power: float = 1.5, sigma: float = 1.0, corr_cells: float = 4.0,
                          seed: int = 20240622) -> np.ndarray:
@@ -133,6 +145,63 @@ def clumpy_envelope_grid(n: int = 128, tau_radial: float = 5.0, r_in: float = 0.
     k = k0 * rr ** (-power) * np.exp(sigma * G - 0.5 * sigma * sigma)
     k = np.where((r >= r_in) & (r <= r_out), k, 0.0)
     return np.ascontiguousarray(k.astype(np.float32))
+
+
+def fractal_cloud_points(N: int = 32, D: float = 2.3, levels: int = 4, seed: int = 1556) -> np.ndarray:
+    """Hierarchically clumped points in the unit cube [0, 1)^3 (Elmegreen 1997; Mathis
+    et al. 2002; the paper's fractal cloud, Sec. 5): N uniform points in the cube; around
+    each point a cube of edge 1 / (2 N^(1/D)) times the parent's edge, centred on it,
+    receives N uniform points; repeated until `levels` generations (N^levels points);
+    coordinates outside the unit cube are wrapped by one cube length.  The paper draws
+    its points from L'Ecuyer's generator with seed -1556; here a seeded Philox stream
+    of NumPy supplies the uniform triples."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    pts = rng.uniform(0.0, 1.0, size=(N, 3))
+    edge = 1.0
+    for _ in range(levels - 1):
+        edge = edge / (2.0 * N ** (1.0 / D))
+        offs = rng.uniform(-0.5, 0.5, size=(len(pts), N, 3)) * edge
+        pts = (pts[:, None, :] + offs).reshape(-1, 3)
+    return np.mod(pts, 1.0)
+
+
+def fractal_cloud_grid(n: int = 200, N: int = 32, D: float = 2.3, levels: int = 4, tau: float = 2.0,
+                       seed: int = 1556, directions: int = 4096) -> np.ndarray:
+    """Density of the fractal cloud on n^3 cells over [-1, 1]^3: proportional to the
+    number of points per cell, scaled so that the optical depth from the centre to the
+    cube's surface, averaged over directions, is `tau` (the paper's tau_cube).  The
+    average is taken over a seeded set of uniform directions, each ray integrated cell
+    by cell (exact segment lengths) in float64."""
+    pts = fractal_cloud_points(N, D, levels, seed)
+    idx = np.minimum((pts * n).astype(np.int64), n - 1)
+    counts = np.zeros((n, n, n), dtype=np.float64)
+    np.add.at(counts, (idx[:, 2], idx[:, 1], idx[:, 0]), 1.0)
+    rng = np.random.Generator(np.random.Philox(seed + 1))
+    v = rng.normal(size=(directions, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    taus = np.array([_ray_sum(counts, d) for d in v])
+    k = counts * (tau / taus.mean())
+    return np.ascontiguousarray(k.astype(np.float32))
+
+
+def _ray_sum(grid: np.ndarray, d: np.ndarray) -> float:
+    """Sum of cell value x segment length along the ray from the centre of [-1, 1]^3
+    to its surface (cell faces crossed in order of distance)."""
+    n = grid.shape[0]
+    h = 2.0 / n
+    ts = [0.0]
+    for a in range(3):
+        if d[a] != 0.0:
+            faces = -1.0 + h * np.arange(n + 1)
+            t = (faces - 0.0) / d[a]
+            ts.extend(t[t > 0].tolist())
+    t_exit = min(1.0 / abs(d[a]) for a in range(3) if d[a] != 0.0)
+    ts = np.unique(np.clip(np.array(ts), 0.0, t_exit))
+    mid = 0.5 * (ts[1:] + ts[:-1])
+    seg = ts[1:] - ts[:-1]
+    p = mid[:, None] * d[None, :]
+    c = np.clip(((p + 1.0) / h).astype(np.int64), 0, n - 1)
+    return float(np.sum(grid[c[:, 2], c[:, 1], c[:, 0]] * seg))
 
 
 # --- workloads ---------------------------------------------------------------------
@@ -205,6 +274,34 @@ def batched_instances(n_incl: int = 32, n_wave: int = 8, seed: int = 4, min_log2
             out.append(Instance(theta_obs=th, albedo=0.4 + 0.5 * t, g=0.2 + 0.5 * t,
                                 kscale=0.5 * 8.0 ** t, n_packets=n, first_index=n))
     return out
+
+
+_shell_cache: dict = {}
+
+
+def shell_envelope_problem(n: int = 256, **kw) -> Problem:
+    """Point source inside the dust shell (radial tau 0.1), HG g = 0.5, albedo 0.6,
+    p_l = 0.5, observer at the pole, 256x256 image."""
+    if n not in _shell_cache:
+        _shell_cache[n] = shell_envelope_grid(n)
+    p = Problem(grid=_shell_cache[n], albedo=0.6, g=0.5, p_l=0.5, theta_obs=0.0, phi_obs=0.0, half_width=1.0,
+                nx=256, ny=256)
+    return p.replace(**kw)
+
+
+_fractal_cache: dict = {}
+
+
+def fractal_cloud_problem(n: int = 200, **kw) -> Problem:
+    """Point source at the centre of the fractal cloud (n^3 cells, N = 32 points per
+    level, four levels, fractal dimension 2.3, average radial tau 2), single
+    scattering, isotropic unpolarized dust (albedo 1, g = 0), observer at 60 degrees,
+    200x200 image."""
+    if n not in _fractal_cache:
+        _fractal_cache[n] = fractal_cloud_grid(n)
+    p = Problem(grid=_fractal_cache[n], albedo=1.0, g=0.0, p_l=0.0, theta_obs=math.radians(60.0), phi_obs=0.0,
+                half_width=1.0, nx=200, ny=200)
+    return p.replace(**kw)
 
 
 def finite_star_disk_problem(n: int = 256, **kw) -> Problem:
