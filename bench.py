@@ -192,11 +192,29 @@ def run_multiple_scattering(log2_n=24, repeats=3):
     e1.record(stream)
     e1.synchronize()
     ms = e0.elapsed_time(e1) / repeats
+    ref = buf.clone()
+    # the same packets order by order, live packets regrouped between orders
+    ws = sc.wavefront_workspace(n)
+
+    def run_wave(k):
+        buf.zero_()
+        sc.trace_wavefront(n * (k + 1), n, buf, ws, frac_bits=fb)
+    run_wave(0)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for k in range(repeats):
+        run_wave(k + 1)
+    e1.record(stream)
+    e1.synchronize()
+    ms_wave = e0.elapsed_time(e1) / repeats
+    same = bool(torch.equal(buf, ref))
     cpp = cells_per_packet("clumpy_multiple_scattering")
     peak = SMS * LANES_PER_SM * measured_peaks().get("sm_max_mhz", 2070.0) * 1e6
     ops = n * cpp * OPS_PER_CELL / (ms / 1e3)
     return {"workload": "clumpy envelope 128^3, point source, 20 orders, forced, roulette 1e-4, 512x512 I/Q/U, "
                         "FP32 trace, int64 accumulate", "packets": n, "ms": ms, "packets_per_s": n / (ms / 1e3),
+            "wavefront": {"ms": ms_wave, "packets_per_s": n / (ms_wave / 1e3), "identical_images": same,
+                          "frac": n * cpp * OPS_PER_CELL / (ms_wave / 1e3) / peak},
             "roofline": {"bound": "alu", "achieved": ops / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
                          "frac": ops / peak, "kernel": "k_trace_multiple<float>",
                          "per_unit": f"{OPS_PER_CELL} ops per cell visit x {cpp:.1f} cells per packet (oracle count)"}}

@@ -415,6 +415,25 @@ int qmcrt_trace_multiple_warped(const qmcrt_medium *medium, const qmcrt_source *
                                 void *stream);
 
 /*
+ * qmcrt_trace_multiple_wavefront -- qmcrt_trace_multiple_warped computed order by order:
+ * every scattering order is one pass over the packets still alive, and between orders
+ * the live packets are regrouped by position and direction so that a warp traces
+ * similar rays (Sec. 3.5, 3.7; the per-packet arithmetic is the same, so fixed-point
+ * images equal qmcrt_trace_multiple's / _warped's bit for bit).  d_x, d_logj,
+ * d_train_log: as qmcrt_trace_multiple_warped (may be NULL).  d_workspace: device
+ * memory, 256-byte aligned, of workspace_bytes; the packets are processed in chunks of
+ * the largest power of two whose qmcrt_wavefront_workspace_bytes fits.
+ * Errors: as qmcrt_trace_multiple_warped; INVALID_ARG for a NULL, misaligned or too
+ * small workspace.
+ */
+uint64_t qmcrt_wavefront_workspace_bytes(uint64_t max_packets, int32_t precision);
+int qmcrt_trace_multiple_wavefront(const qmcrt_medium *medium, const qmcrt_source *source, const qmcrt_dust *dust,
+                                   const qmcrt_observer *obs, const qmcrt_points_desc *pts,
+                                   const qmcrt_trace_opts *opts, const float *d_x, const float *d_logj,
+                                   const qmcrt_image *image, float *d_train_log, void *d_workspace,
+                                   uint64_t workspace_bytes, void *stream);
+
+/*
  * qmcrt_image_reduce -- final image in units of the source luminosity (Sec. 3.6):
  * d_out[j] = sum over the n_replicas accumulation buffers (each image->n_images x 3 x
  * ny x nx, consecutive in memory from image->d_accum) of raw[j] * 2^-frac_bits

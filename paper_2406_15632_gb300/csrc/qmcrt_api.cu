@@ -389,6 +389,46 @@ int observers_common(const qmcrt_medium *md, const qmcrt_source *src, const qmcr
     return cuda_status(launch_observers(P, S, block, s), "trace_observers launch");
 }
 
+cudaError_t launch_wavefront(const qmcrt::TraceP<float> &P, void *ws, uint64_t cap, int sms, cudaStream_t s)
+{
+    return qmcrt::launch_trace_wavefront_f32(P, ws, cap, sms, s);
+}
+
+cudaError_t launch_wavefront(const qmcrt::TraceP<double> &P, void *ws, uint64_t cap, int sms, cudaStream_t s)
+{
+    return qmcrt::launch_trace_wavefront_f64(P, ws, cap, sms, s);
+}
+
+// Runs the wavefront tracer over pts in chunks of the largest power of two of packets the
+// workspace holds, each chunk on cap-aligned index blocks (so each keeps whole nets).
+template <class T>
+int wavefront_run(qmcrt::TraceP<T> P, const qmcrt_points_desc *pts, WarpIO wio, void *ws, uint64_t ws_bytes,
+                  int precision, cudaStream_t s)
+{
+    uint64_t cap = 1;
+    while (cap < (1ull << 31) && qmcrt::wavefront_workspace_bytes(cap * 2, precision) <= ws_bytes) cap *= 2;
+    if (qmcrt::wavefront_workspace_bytes(cap, precision) > ws_bytes)
+        return fail(QMCRT_ERR_INVALID_ARG, "workspace below one packet");
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_status(e, "device query");
+    const uint64_t first = pts->first_index, count = pts->count;
+    for (uint64_t lo = first; lo < first + count;) {
+        const uint64_t hi = std::min(first + count, (lo / cap + 1) * cap);
+        P.first = lo;
+        P.count = hi - lo;
+        make_order(pts->kind, lo, hi - lo, P.ord);
+        const uint64_t off = lo - first;
+        P.warp_x = wio.x ? wio.x + 3 * off : nullptr;
+        P.warp_logj = wio.logj ? wio.logj + off : nullptr;
+        P.train_log = wio.log ? wio.log + 5 * off : nullptr;
+        if ((e = launch_wavefront(P, ws, cap, sms, s)) != cudaSuccess) return cuda_status(e, "wavefront launch");
+        lo = hi;
+    }
+    return QMCRT_OK;
+}
+
 }  // namespace
 
 namespace qmcrt {
@@ -648,6 +688,45 @@ int qmcrt_trace_multiple_warped(const qmcrt_medium *medium, const qmcrt_source *
     w.logj = d_logj;
     w.log = d_train_log;
     return trace_common(medium, source, dust, obs, pts, opts, image, nullptr, stream, 1, w);
+}
+
+uint64_t qmcrt_wavefront_workspace_bytes(uint64_t max_packets, int32_t precision)
+{
+    return qmcrt::wavefront_workspace_bytes(max_packets, precision);
+}
+
+int qmcrt_trace_multiple_wavefront(const qmcrt_medium *medium, const qmcrt_source *source, const qmcrt_dust *dust,
+                                   const qmcrt_observer *obs, const qmcrt_points_desc *pts,
+                                   const qmcrt_trace_opts *opts, const float *d_x, const float *d_logj,
+                                   const qmcrt_image *image, float *d_train_log, void *d_workspace,
+                                   uint64_t workspace_bytes, void *stream)
+{
+    g_last_error.clear();
+    CHECK_STRUCT(source, qmcrt_source);
+    CHECK_STRUCT(opts, qmcrt_trace_opts);
+    CHECK_STRUCT(pts, qmcrt_points_desc);
+    if ((d_x == nullptr) != (d_logj == nullptr)) return fail(QMCRT_ERR_INVALID_ARG, "d_x and d_logj go together");
+    if (d_x && source->kind != QMCRT_SOURCE_POINT)
+        return fail(QMCRT_ERR_UNSUPPORTED, "the warp replaces point-source coordinates only");
+    if (!d_workspace) return fail(QMCRT_ERR_INVALID_ARG, "d_workspace is NULL");
+    if (((uintptr_t)d_workspace) & 255) return fail(QMCRT_ERR_INVALID_ARG, "d_workspace must be 256-byte aligned");
+    WarpIO w;
+    w.x = d_x;
+    w.logj = d_logj;
+    w.log = d_train_log;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (opts->precision == QMCRT_PREC_F64) {
+        qmcrt::TraceP<double> P;
+        int rc = fill_trace<double>(medium, source, dust, obs, pts, opts, image, 1, P);
+        if (rc) return rc;
+        P.log = nullptr;
+        return wavefront_run<double>(P, pts, w, d_workspace, workspace_bytes, QMCRT_PREC_F64, s);
+    }
+    qmcrt::TraceP<float> P;
+    int rc = fill_trace<float>(medium, source, dust, obs, pts, opts, image, 1, P);
+    if (rc) return rc;
+    P.log = nullptr;
+    return wavefront_run<float>(P, pts, w, d_workspace, workspace_bytes, QMCRT_PREC_F32, s);
 }
 
 int qmcrt_image_reduce(const qmcrt_image *image, int32_t nx, int32_t ny, int32_t n_replicas, double scale,

@@ -133,6 +133,10 @@ cudaError_t launch_trace_observers_f64(const TraceP<double> &p, const ObsSet<dou
 cudaError_t launch_direct_light_f32(const TraceP<float> &p, int subsamples, double weight, cudaStream_t s);
 cudaError_t launch_direct_light_f64(const TraceP<double> &p, int subsamples, double weight, cudaStream_t s);
 
+uint64_t wavefront_workspace_bytes(uint64_t cap, int precision);
+cudaError_t launch_trace_wavefront_f32(const TraceP<float> &p, void *ws, uint64_t cap, int sms, cudaStream_t s);
+cudaError_t launch_trace_wavefront_f64(const TraceP<double> &p, void *ws, uint64_t cap, int sms, cudaStream_t s);
+
 struct GemmEpi;
 cudaError_t launch_gemm_bf16(const __nv_bfloat16 *A, const __nv_bfloat16 *B, int M, int N, int K, int splits,
                              const GemmEpi &ep, cudaStream_t s);

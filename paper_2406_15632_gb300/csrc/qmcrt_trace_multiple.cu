@@ -29,7 +29,7 @@ struct OneObserver {
 };
 
 template <class T>
-__global__ void __launch_bounds__(256) k_trace_multiple(const __grid_constant__ TraceP<T> P)
+__global__ void __launch_bounds__(256, 3) k_trace_multiple(const __grid_constant__ TraceP<T> P)
 {
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if ((tid & ~31ull) >= P.ord.threads) return;  // uniform per warp

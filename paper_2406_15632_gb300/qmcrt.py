@@ -135,6 +135,11 @@ _SIGS = [
                                         C.c_void_p]),
     ("qmcrt_direct_light", C.c_int, [_P(qmcrt_medium), _P(qmcrt_source), _P(qmcrt_observer), C.c_int32, C.c_double,
                                      _P(qmcrt_trace_opts), _P(qmcrt_image), C.c_void_p]),
+    ("qmcrt_wavefront_workspace_bytes", C.c_uint64, [C.c_uint64, C.c_int32]),
+    ("qmcrt_trace_multiple_wavefront", C.c_int, [_P(qmcrt_medium), _P(qmcrt_source), _P(qmcrt_dust),
+                                                 _P(qmcrt_observer), _P(qmcrt_points_desc), _P(qmcrt_trace_opts),
+                                                 C.c_void_p, C.c_void_p, _P(qmcrt_image), C.c_void_p, C.c_void_p,
+                                                 C.c_uint64, C.c_void_p]),
     ("qmcrt_batch_workspace_bytes", C.c_uint64, [C.c_int32]),
     ("qmcrt_trace_batch", C.c_int, [_P(qmcrt_medium), _P(qmcrt_source), _P(qmcrt_observer), _P(qmcrt_points_desc),
                                     _P(qmcrt_trace_opts), C.c_void_p, C.c_int32, _P(qmcrt_batch_config), C.c_void_p,
@@ -352,6 +357,19 @@ def qmcrt_pad_grid(d_k: int, nx: int, ny: int, nz: int, pad: int, d_padded: int,
 MAX_OBSERVERS = 16
 
 
+def qmcrt_wavefront_workspace_bytes(max_packets: int, precision: str = "f32") -> int:
+    return int(load().qmcrt_wavefront_workspace_bytes(max_packets, PREC[precision]))
+
+
+def qmcrt_trace_multiple_wavefront(medium, source, dust, obs, pts, opts, d_x: int, d_logj: int, image,
+                                   d_train_log: int, d_workspace: int, workspace_bytes: int, stream: int = 0) -> None:
+    _check(load().qmcrt_trace_multiple_wavefront(C.byref(medium), C.byref(source), C.byref(dust), C.byref(obs),
+                                                 C.byref(pts), C.byref(opts), C.c_void_p(d_x or None),
+                                                 C.c_void_p(d_logj or None), C.byref(image),
+                                                 C.c_void_p(d_train_log or None), C.c_void_p(d_workspace),
+                                                 workspace_bytes, C.c_void_p(stream)))
+
+
 def qmcrt_direct_light(medium, source, obs, subsamples: int, weight: float, opts, image, stream: int = 0) -> None:
     _check(load().qmcrt_direct_light(C.byref(medium), C.byref(source), C.byref(obs), subsamples, weight,
                                      C.byref(opts), C.byref(image), C.c_void_p(stream)))
@@ -554,6 +572,23 @@ class Scene:
         img = self.image_desc(buf, accum, frac_bits)
         qmcrt_trace_observers(self.medium, self.source, self.dust, arr, len(angles), pts, self.opts(precision), img,
                               _stream(stream))
+
+    def wavefront_workspace(self, max_packets: int, precision: str = "f32"):
+        """Device workspace for trace_wavefront of up to max_packets packets per chunk."""
+        torch = _torch()
+        n = qmcrt_wavefront_workspace_bytes(max_packets, precision)
+        return torch.empty(n, dtype=torch.uint8, device="cuda")
+
+    def trace_wavefront(self, first: int, count: int, buf, ws, *, x=None, logj=None, train_log=None,
+                        accum: str = "i64", frac_bits: int = 0, precision: str = "f32", stream=None) -> None:
+        """Multiple scattering order by order, live packets regrouped between orders
+        (the same images as trace / trace_warped)."""
+        p = self.prob
+        pts = points_desc(p.generator, p.dims, first, count, "f64", p.seed, p.total_n)
+        img = self.image_desc(buf, accum, frac_bits)
+        ptr = lambda t: t.data_ptr() if t is not None else 0
+        qmcrt_trace_multiple_wavefront(self.medium, self.source, self.dust, self.obs, pts, self.opts(precision), ptr(x),
+                                       ptr(logj), img, ptr(train_log), ws.data_ptr(), ws.numel(), _stream(stream))
 
     def reduce(self, buf, scale: float, *, accum: str = "i64", frac_bits: int = 0, out=None, stream=None):
         torch = _torch()

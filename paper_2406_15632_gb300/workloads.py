@@ -5,6 +5,7 @@
 Names:
   disk_single      single scattering, 256^3 flared disk, 256x256 I/Q/U, FP32, 2^L packets
   clumpy_multiple  multiple scattering (20 orders), 128^3 clumpy envelope, 512x512, 2^L packets
+  clumpy_wavefront the same packets order by order (live packets regrouped between orders)
   warp_forward     fused forward of the learned warp on 2^L Sobol points
   warp_train       one epoch of minibatch training (2^16 rows per step) on 2^L samples
   batch            the 256-instance finite-star batch in one persistent launch (graph replay)
@@ -40,7 +41,8 @@ def main(argv=None) -> int:
     from . import scenes as S
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("name", choices=["disk_single", "clumpy_multiple", "warp_forward", "warp_train", "batch"])
+    ap.add_argument("name", choices=["disk_single", "clumpy_multiple", "clumpy_wavefront", "warp_forward", "warp_train",
+                                     "batch"])
     ap.add_argument("--log2-n", type=int, default=20)
     ap.add_argument("--repeat", type=int, default=1)
     a = ap.parse_args(argv)
@@ -56,6 +58,17 @@ def main(argv=None) -> int:
         def run():
             buf.zero_()
             sc.trace(n, n, buf, frac_bits=fb)
+        ms = _cuda_ms(run, a.repeat)
+    elif a.name == "clumpy_wavefront":
+        prob = S.clumpy_problem(n=128)
+        sc = Q.Scene(prob)
+        fb = Q.default_frac_bits(prob, n)
+        buf = sc.accum_buffer("i64")
+        ws = sc.wavefront_workspace(n)
+
+        def run():
+            buf.zero_()
+            sc.trace_wavefront(n, n, buf, ws, frac_bits=fb)
         ms = _cuda_ms(run, a.repeat)
     elif a.name == "warp_forward":
         W = Q.Warp(seed=1, uniform_mix=0.1)
