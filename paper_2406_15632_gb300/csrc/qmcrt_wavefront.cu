@@ -5,12 +5,16 @@
 // but from the second order on each lane scatters into its own direction and the warp
 // waits for its longest walk.  Here every order is a launch over the packets still
 // alive, and between orders the live packets are regrouped by a key built from their
-// position (3 bits per axis) and their new direction (8 bins in cos theta x 16 in phi),
+// position (3 bits per axis) and their new direction (4 bins in cos theta x 8 in phi),
 // so a warp again traces 32 similar rays:
 //
-//   order 1:   emission, forced step, peel-off, roulette, scattering for order 2 -> queue
-//   order k:   key + histogram -> bucket offsets (one block) -> scatter into buckets ->
+//   order 1:   emission, forced step, peel-off, roulette, scattering for order 2 ->
+//              queue (with each packet's key, counted in the bucket histogram)
+//   order k:   bucket offsets (one block, shared memory) -> copy into buckets ->
 //              forced step (or march), peel-off, roulette, scattering for k+1 -> queue
+//
+// A queued packet is one 64-byte record (128 in FP64), so the copy into buckets moves
+// whole sectors.
 //
 // Per packet the arithmetic is the one-kernel tracer's, step for step (the scattering
 // that opens order k runs at the end of order k-1), so fixed-point images are identical.
@@ -24,59 +28,59 @@ namespace qmcrt {
 
 namespace {
 
-constexpr int WV_FIELDS = 14;  // pos[3], n[3], a[3], S[3], in-image I sum, sum of squares
-constexpr int WV_KEY_BITS = 16;
+constexpr int WV_KEY_BITS = 14;  // 3 position bits per axis, 4 x 8 direction bins
 constexpr int WV_BUCKETS = 1 << WV_KEY_BITS;
-
-template <class T>
-struct WaveQueue {
-    T *v[WV_FIELDS];
-    uint32_t *idx;  // point index - first
-};
-
-template <class T>
-struct WaveWork {
-    WaveQueue<T> q[2];
-    uint32_t *count;  // [2] live packets in q[0], q[1]
-    uint32_t *keys;   // [cap]
-    uint32_t *hist;   // [WV_BUCKETS] histogram, then bucket cursors
-};
 
 template <class T>
 struct Packet {
     T pos[3], n[3], a[3], S[3], tot, tot2;
 };
 
+// One queued packet: its state and its index, one contiguous record (64 bytes in FP32,
+// 128 in FP64) moved with 16-byte vector accesses.
 template <class T>
-__device__ __forceinline__ void load(const WaveQueue<T> &Q, uint32_t q, Packet<T> &p)
+struct alignas(16) Rec {
+    Packet<T> p;
+    uint32_t j;  // point index - first
+    uint32_t pad[sizeof(T) == 4 ? 1 : 3];
+};
+static_assert(sizeof(Rec<float>) == 64 && sizeof(Rec<double>) == 128, "record size");
+
+template <class T>
+struct WaveWork {
+    Rec<T> *q[2];       // [cap] each: q[1] unsorted (appended), q[0] sorted
+    uint32_t *count;    // [2] live packets in q[0], q[1]
+    uint32_t *keys;     // [cap] bucket of each record of q[1]
+    uint32_t *hist;     // [WV_BUCKETS] histogram of q[1], then bucket cursors
+};
+
+template <class T>
+__device__ __forceinline__ void copy_rec(Rec<T> *dst, const Rec<T> *src)
 {
-    for (int c = 0; c < 3; ++c) {
-        p.pos[c] = Q.v[c][q];
-        p.n[c] = Q.v[3 + c][q];
-        p.a[c] = Q.v[6 + c][q];
-        p.S[c] = Q.v[9 + c][q];
-    }
-    p.tot = Q.v[12][q];
-    p.tot2 = Q.v[13][q];
+    const uint4 *s = reinterpret_cast<const uint4 *>(src);
+    uint4 *d = reinterpret_cast<uint4 *>(dst);
+#pragma unroll
+    for (int v = 0; v < (int)(sizeof(Rec<T>) / 16); ++v) d[v] = s[v];
 }
 
 template <class T>
-__device__ __forceinline__ void store(const WaveQueue<T> &Q, uint32_t q, const Packet<T> &p, uint32_t j)
+__device__ __forceinline__ uint32_t wave_key(const MediumP<T> &G, const T pos[3], const T n[3])
 {
+    uint32_t key = 0;
     for (int c = 0; c < 3; ++c) {
-        Q.v[c][q] = p.pos[c];
-        Q.v[3 + c][q] = p.n[c];
-        Q.v[6 + c][q] = p.a[c];
-        Q.v[9 + c][q] = p.S[c];
+        const T f = (pos[c] - G.lo[c]) / (G.hi[c] - G.lo[c]) * T(8);
+        key = (key << 3) | (uint32_t)min(7, max(0, (int)f));
     }
-    Q.v[12][q] = p.tot;
-    Q.v[13][q] = p.tot2;
-    Q.idx[q] = j;
+    const int ct = min(3, max(0, (int)((n[2] + T(1)) * T(2))));
+    const float ph = atan2f((float)n[1], (float)n[0]);  // the key only orders packets
+    const int pb = min(7, max(0, (int)((ph + 3.14159265f) * 1.27323954f)));  // 8 / (2 pi)
+    return (key << 5) | (uint32_t)(ct << 3) | (uint32_t)pb;
 }
 
-// Append the lanes with `keep` to queue Q (one atomic per warp).  All 32 lanes call.
+// Append the lanes with `keep` to the unsorted queue with their bucket keys and count
+// them in the histogram of the next sort (one queue atomic per warp).  All 32 lanes call.
 template <class T>
-__device__ __forceinline__ void append(const WaveQueue<T> &Q, uint32_t *count, bool keep, const Packet<T> &p,
+__device__ __forceinline__ void append(const TraceP<T> &P, const WaveWork<T> &W, bool keep, const Packet<T> &p,
                                        uint32_t j)
 {
     const unsigned m = __ballot_sync(FULL_MASK, keep);
@@ -84,9 +88,19 @@ __device__ __forceinline__ void append(const WaveQueue<T> &Q, uint32_t *count, b
     const int lane = threadIdx.x & 31;
     const int first = __ffs(m) - 1;
     uint32_t base = 0;
-    if (lane == first) base = atomicAdd(count, (uint32_t)__popc(m));
+    if (lane == first) base = atomicAdd(W.count + 1, (uint32_t)__popc(m));
     base = __shfl_sync(FULL_MASK, base, first);
-    if (keep) store(Q, base + __popc(m & ((1u << lane) - 1u)), p, j);
+    if (keep) {
+        const uint32_t q = base + __popc(m & ((1u << lane) - 1u));
+        Rec<T> r;
+        r.p = p;
+        r.j = j;
+        for (int k = 0; k < (int)(sizeof(r.pad) / 4); ++k) r.pad[k] = 0u;
+        copy_rec(W.q[1] + q, &r);
+        const uint32_t key = wave_key(P.med, p.pos, p.n);
+        W.keys[q] = key;
+        atomicAdd(W.hist + key, 1u);
+    }
 }
 
 template <class T>
@@ -158,8 +172,7 @@ __device__ __forceinline__ bool run_order(const TraceP<T> &P, int k, uint64_t i,
 }
 
 template <class T>
-__global__ void __launch_bounds__(256) k_wave_first(const __grid_constant__ TraceP<T> P, WaveQueue<T> out,
-                                                   uint32_t *count)
+__global__ void __launch_bounds__(256) k_wave_first(const __grid_constant__ TraceP<T> P, WaveWork<T> W)
 {
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if ((tid & ~31ull) >= P.ord.threads) return;  // uniform per warp
@@ -188,46 +201,22 @@ __global__ void __launch_bounds__(256) k_wave_first(const __grid_constant__ Trac
         p.S[0] = wgt;
     }
     const bool on = run_order(P, 1, i, live, wd, p);
-    append(out, count, on, p, (uint32_t)j);
+    append(P, W, on, p, (uint32_t)j);
     if (live && !on && P.train_log) write_log(P, i, j, p);
 }
 
-template <class T>
-__device__ __forceinline__ uint32_t wave_key(const MediumP<T> &G, const T pos[3], const T n[3])
-{
-    uint32_t key = 0;
-    for (int c = 0; c < 3; ++c) {
-        const T f = (pos[c] - G.lo[c]) / (G.hi[c] - G.lo[c]) * T(8);
-        key = (key << 3) | (uint32_t)min(7, max(0, (int)f));
-    }
-    const int ct = min(7, max(0, (int)((n[2] + T(1)) * T(4))));
-    const float ph = atan2f((float)n[1], (float)n[0]);  // the key only orders packets
-    const int pb = min(15, max(0, (int)((ph + 3.14159265f) * 2.54647909f)));  // 16 / (2 pi)
-    return (key << 7) | (uint32_t)(ct << 4) | (uint32_t)pb;
-}
-
-template <class T>
-__global__ void __launch_bounds__(256) k_wave_key(const __grid_constant__ TraceP<T> P, WaveQueue<T> in,
-                                                 const uint32_t *count, uint32_t *keys, uint32_t *hist)
-{
-    const uint32_t n = *count;
-    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
-        const T pos[3] = {in.v[0][q], in.v[1][q], in.v[2][q]};
-        const T d[3] = {in.v[3][q], in.v[4][q], in.v[5][q]};
-        const uint32_t key = wave_key(P.med, pos, d);
-        keys[q] = key;
-        atomicAdd(hist + key, 1u);
-    }
-}
-
-// Exclusive scan of the bucket histogram into cursors (one block of 1024 threads).
+// Exclusive scan of the bucket histogram into cursors, in shared memory (one block of
+// 1024 threads, 16 buckets each).
 __global__ void __launch_bounds__(1024) k_wave_scan(uint32_t *hist)
 {
+    __shared__ uint32_t h[WV_BUCKETS];
     __shared__ uint32_t part[1024];
     constexpr int PER = WV_BUCKETS / 1024;
     const int t = threadIdx.x;
+    for (int b = t; b < WV_BUCKETS; b += 1024) h[b] = hist[b];
+    __syncthreads();
     uint32_t s = 0;
-    for (int b = 0; b < PER; ++b) s += hist[t * PER + b];
+    for (int b = 0; b < PER; ++b) s += h[t * PER + b];
     part[t] = s;
     __syncthreads();
     for (int off = 1; off < 1024; off <<= 1) {
@@ -238,48 +227,44 @@ __global__ void __launch_bounds__(1024) k_wave_scan(uint32_t *hist)
     }
     uint32_t run = t ? part[t - 1] : 0u;
     for (int b = 0; b < PER; ++b) {
-        const uint32_t h = hist[t * PER + b];
-        hist[t * PER + b] = run;
-        run += h;
+        const uint32_t x = h[t * PER + b];
+        h[t * PER + b] = run;
+        run += x;
     }
+    __syncthreads();
+    for (int b = t; b < WV_BUCKETS; b += 1024) hist[b] = h[b];
 }
 
 template <class T>
-__global__ void __launch_bounds__(256) k_wave_scatter(WaveQueue<T> in, const uint32_t *count, const uint32_t *keys,
-                                                     uint32_t *cursor, WaveQueue<T> out)
+__global__ void __launch_bounds__(256) k_wave_scatter(WaveWork<T> W)
 {
-    const uint32_t n = *count;
-    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
-        const uint32_t dst = atomicAdd(cursor + keys[q], 1u);
-        for (int f = 0; f < WV_FIELDS; ++f) out.v[f][dst] = in.v[f][q];
-        out.idx[dst] = in.idx[q];
-    }
+    const uint32_t n = W.count[1];
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x)
+        copy_rec(W.q[0] + atomicAdd(W.hist + W.keys[q], 1u), W.q[1] + q);
 }
 
-// Order k >= 2 over the sorted queue `in`; survivors go to `out`.
+// Order k >= 2 over the sorted queue q[0]; survivors are appended to q[1].
 template <class T>
-__global__ void __launch_bounds__(256) k_wave_order(const __grid_constant__ TraceP<T> P, int k, WaveQueue<T> in,
-                                                   const uint32_t *in_count, WaveQueue<T> out, uint32_t *out_count)
+__global__ void __launch_bounds__(256) k_wave_order(const __grid_constant__ TraceP<T> P, int k, WaveWork<T> W)
 {
-    const uint32_t n = *in_count;
+    const uint32_t n = W.count[0];
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t q0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); q0 < n; q0 += stride) {  // uniform per warp
         const uint32_t q = q0 + (threadIdx.x & 31u);
         const bool live = q < n;
-        Packet<T> p;
-        uint32_t j = 0;
+        Rec<T> r;
         if (live) {
-            load(in, q, p);
-            j = in.idx[q];
+            copy_rec(&r, W.q[0] + q);
         } else {
-            for (int c = 0; c < 3; ++c) p.pos[c] = p.n[c] = p.a[c] = p.S[c] = T(0);
-            p.tot = p.tot2 = T(0);
+            for (int c = 0; c < 3; ++c) r.p.pos[c] = r.p.n[c] = r.p.a[c] = r.p.S[c] = T(0);
+            r.p.tot = r.p.tot2 = T(0);
+            r.j = 0;
         }
-        const uint64_t i = P.first + j;
+        const uint64_t i = P.first + r.j;
         const T wd = live ? point<T>(P.pts, i, 4 * (k - 1) + 2) : T(0);
-        const bool on = run_order(P, k, i, live, wd, p);
-        append(out, out_count, on, p, j);
-        if (live && !on && P.train_log) write_log(P, i, j, p);
+        const bool on = run_order(P, k, i, live, wd, r.p);
+        append(P, W, on, r.p, r.j);
+        if (live && !on && P.train_log) write_log(P, i, r.j, r.p);
     }
 }
 
@@ -293,10 +278,8 @@ WaveWork<T> carve(void *ws, uint64_t cap)
         c += (bytes + 255) & ~(size_t)255;
         return r;
     };
-    for (int b = 0; b < 2; ++b) {
-        for (int f = 0; f < WV_FIELDS; ++f) W.q[b].v[f] = (T *)take(cap * sizeof(T));
-        W.q[b].idx = (uint32_t *)take(cap * 4);
-    }
+    W.q[0] = (Rec<T> *)take(cap * sizeof(Rec<T>));
+    W.q[1] = (Rec<T> *)take(cap * sizeof(Rec<T>));
     W.count = (uint32_t *)take(2 * 4);
     W.keys = (uint32_t *)take(cap * 4);
     W.hist = (uint32_t *)take(WV_BUCKETS * 4);
@@ -309,21 +292,21 @@ cudaError_t launch_wave(const TraceP<T> &P, void *ws, uint64_t cap, int sms, cud
     if (P.count == 0) return cudaSuccess;
     WaveWork<T> W = carve<T>(ws, cap);
     cudaError_t e = cudaMemsetAsync(W.count, 0, 2 * sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(W.hist, 0, WV_BUCKETS * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     const uint64_t threads = (P.ord.threads + 31) & ~31ull;
-    k_wave_first<T><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(P, W.q[1], W.count + 1);
+    k_wave_first<T><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(P, W);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const unsigned grid = (unsigned)std::max(1, sms * 8);
     for (int k = 2; k <= P.max_orders; ++k) {
-        // the queue of order k is q[1] (count[1]); sort it into q[0], trace into q[1]
-        if ((e = cudaMemsetAsync(W.hist, 0, WV_BUCKETS * sizeof(uint32_t), s)) != cudaSuccess) return e;
-        k_wave_key<T><<<grid, 256, 0, s>>>(P, W.q[1], W.count + 1, W.keys, W.hist);
+        // q[1] holds order k's packets with their keys and histogram: sort into q[0]
         k_wave_scan<<<1, 1024, 0, s>>>(W.hist);
-        k_wave_scatter<T><<<grid, 256, 0, s>>>(W.q[1], W.count + 1, W.keys, W.hist, W.q[0]);
+        k_wave_scatter<T><<<grid, 256, 0, s>>>(W);
         if ((e = cudaMemcpyAsync(W.count, W.count + 1, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
             return e;
         if ((e = cudaMemsetAsync(W.count + 1, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
-        k_wave_order<T><<<grid, 256, 0, s>>>(P, k, W.q[0], W.count, W.q[1], W.count + 1);
+        if ((e = cudaMemsetAsync(W.hist, 0, WV_BUCKETS * sizeof(uint32_t), s)) != cudaSuccess) return e;
+        k_wave_order<T><<<grid, 256, 0, s>>>(P, k, W);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -333,9 +316,9 @@ cudaError_t launch_wave(const TraceP<T> &P, void *ws, uint64_t cap, int sms, cud
 
 uint64_t wavefront_workspace_bytes(uint64_t cap, int precision)
 {
-    const uint64_t t = precision == QMCRT_PREC_F64 ? 8 : 4;
+    const uint64_t rec = precision == QMCRT_PREC_F64 ? sizeof(Rec<double>) : sizeof(Rec<float>);
     auto pad = [](uint64_t b) { return (b + 255) & ~255ull; };
-    return 2 * (WV_FIELDS * pad(cap * t) + pad(cap * 4)) + pad(8) + pad(cap * 4) + pad(WV_BUCKETS * 4);
+    return 2 * pad(cap * rec) + pad(8) + pad(cap * 4) + pad(WV_BUCKETS * 4);
 }
 
 cudaError_t launch_trace_wavefront_f32(const TraceP<float> &p, void *ws, uint64_t cap, int sms, cudaStream_t s)
