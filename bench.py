@@ -389,7 +389,8 @@ def run_time_to_error_learned(ladder=(20, 22, 24, 26), ref_log2=28, ref_seeds=(1
     sc = Q.Scene(prob)
     ref, ref_err, ref_n = _reference_image(Q, prob, sc.grid, ref_log2, ref_seeds, "f64")
     mc_sc = Q.Scene(prob.replace(generator="philox", seed=7), grid_device=sc.grid)
-    plain, mc = Q.LearnedTracer(sc, None), Q.LearnedTracer(mc_sc, None)
+    plain = Q.LearnedTracer(sc, None, wavefront=True)
+    mc = Q.LearnedTracer(mc_sc, None, wavefront=True)
 
     # training: log 2^22 plain packets (points 1 .. 2^22), minibatch Adam on the log
     n_log = 1 << n_log_log2
@@ -398,7 +399,7 @@ def run_time_to_error_learned(ladder=(20, 22, 24, 26), ref_log2=28, ref_seeds=(1
     W = Q.Warp(seed=2, uniform_mix=mix)
     xs, ws = log[:, :3].contiguous(), log[:, 4 if weight == "l2" else 3].contiguous()
     losses, ms_train = _timed(lambda: W.train(xs, ws, epochs=epochs, batch=1 << batch_log2, lr=lr))
-    learned = Q.LearnedTracer(sc, W)
+    learned = Q.LearnedTracer(sc, W, wavefront=True)
 
     def renderer(tracer, s):
         buf = s.accum_buffer("f64")

@@ -98,3 +98,25 @@ def test_wavefront_learned_warp_and_training_log(Q):
     torch.cuda.synchronize()
     assert torch.equal(a, b)
     assert torch.equal(la, lb)
+
+
+def test_learned_tracer_on_the_wavefront(Q):
+    """The learned tracer's chunked loop gives the same fixed-point image and log with
+    the wavefront as with the one-kernel tracer."""
+    import torch
+
+    from oracle import flow as F
+
+    prob = CASES["owen"]
+    sc = Q.Scene(prob)
+    W = Q.Warp(F.init_params(5, scale=2.0), rows=1 << 13, uniform_mix=0.1)
+    n = (1 << 13) + 321
+    out = []
+    for wave in (False, True):
+        t = Q.LearnedTracer(sc, W, chunk=1 << 12, wavefront=wave)
+        buf = sc.accum_buffer("i64")
+        log = torch.zeros((n, 5), device="cuda")
+        t.trace(7, n, buf, accum="i64", frac_bits=28, train_log=log)
+        out.append((buf, log))
+    torch.cuda.synchronize()
+    assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
