@@ -646,6 +646,9 @@ int qmcrt_gemm_bf16(const void *d_A, const void *d_B, int32_t M, int32_t N, int3
                        epilogue->d_out_bf16_t || !epilogue->d_out_f32))
         return fail(QMCRT_ERR_INVALID_ARG, "a K split only adds into d_out_f32 (no bias, ReLU, mask or BF16 output)");
     if (epilogue->d_out_bf16_t && epilogue->ldt < M) return fail(QMCRT_ERR_INVALID_ARG, "ldt < M");
+    if ((reinterpret_cast<uintptr_t>(epilogue->d_mask) | reinterpret_cast<uintptr_t>(epilogue->d_out_f32) |
+         reinterpret_cast<uintptr_t>(epilogue->d_out_bf16)) & 15)
+        return fail(QMCRT_ERR_INVALID_ARG, "d_mask, d_out_f32 and d_out_bf16 must be 16-byte aligned");
     qmcrt::GemmEpi ep;
     ep.bias = epilogue->d_bias;
     ep.relu = epilogue->relu;

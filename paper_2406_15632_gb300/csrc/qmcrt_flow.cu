@@ -71,23 +71,45 @@ int rows_for(uint64_t ws_bytes)
 
 
 // Input features of MLP m for rows [0, rows): one-blob(x0) [, one-blob(x1)], zero padded;
-// rows >= n use x = 0.5 (their loss weight is zero).
-__global__ void k_features(const float *__restrict__ x, int n, int rows, int m, __nv_bfloat16 *__restrict__ F,
-                           __nv_bfloat16 *__restrict__ Ft)
+// rows >= n use x = 0.5 (their loss weight is zero).  One block per 32 rows: each thread
+// writes 16 features of one row as two 16-byte vectors, and the transposed copy leaves
+// through a shared-memory tile, 16 rows of one feature per thread.
+constexpr int FEAT_ROWS = 32;
+__global__ void __launch_bounds__(256) k_features(const float *__restrict__ x, int n, int rows, int m,
+                                                 __nv_bfloat16 *__restrict__ F, __nv_bfloat16 *__restrict__ Ft)
 {
-    const long long total = (long long)rows * WD;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-        const int j = (int)(e / WD), f = (int)(e % WD);
-        float v = 0.0f;
-        if (f < BLOB) v = blob(j < n ? x[3ll * j] : 0.5f, f);
-        else if (m == 1 && f < 2 * BLOB) v = blob(j < n ? x[3ll * j + 1] : 0.5f, f - BLOB);
-        const __nv_bfloat16 b = __float2bfloat16_rn(v);
-        F[e] = b;
-        if (Ft) Ft[(long long)f * rows + j] = b;
+    __shared__ __nv_bfloat16 tile[WD][FEAT_ROWS + 8];
+    const int t = threadIdx.x;
+    const int r = t >> 3, c = t & 7;  // row in the tile, 16-feature chunk
+    const int j = blockIdx.x * FEAT_ROWS + r;
+    const float x0 = j < n ? x[3ll * j] : 0.5f, x1 = j < n ? x[3ll * j + 1] : 0.5f;
+    uint32_t w[8];
+#pragma unroll
+    for (int h = 0; h < 8; ++h) {
+        float v[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int f = c * 16 + 2 * h + e;
+            v[e] = 0.0f;
+            if (f < BLOB) v[e] = blob(x0, f);
+            else if (m == 1 && f < 2 * BLOB) v[e] = blob(x1, f - BLOB);
+        }
+        __nv_bfloat162 p2 = __floats2bfloat162_rn(v[0], v[1]);
+        w[h] = *reinterpret_cast<uint32_t *>(&p2);
+        tile[c * 16 + 2 * h][r] = p2.x;
+        tile[c * 16 + 2 * h + 1][r] = p2.y;
     }
+    uint4 *dst = reinterpret_cast<uint4 *>(F + (long long)j * WD + c * 16);
+    dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+    if (!Ft) return;
+    __syncthreads();
+    const int f = t >> 1, half = t & 1;  // feature, which 16 rows of the tile
+    const uint4 *srcv = reinterpret_cast<const uint4 *>(&tile[f][half * 16]);
+    uint4 *dt = reinterpret_cast<uint4 *>(Ft + (long long)f * rows + blockIdx.x * FEAT_ROWS + half * 16);
+    dt[0] = srcv[0];
+    dt[1] = srcv[1];
 }
-
-
 
 // Sampling step of coordinate `layer`: x_l = F^-1(u_l) for the pdf 32 Q[b] on bin b;
 // log |dx/du| accumulates -log(32 Q[b]).
@@ -133,23 +155,53 @@ __global__ void k_loss_grad(int layer, const float *__restrict__ theta0, const f
     if (j < rows) {
         const float ww = j < n ? (float)(w[j] / *wsum) : 0.0f;
         float z[KB], q[KB];
-        const float *src = layer == 0 ? theta0 : L + (long long)j * KB;
-        for (int k = 0; k < KB; ++k) z[k] = src[k];
+        if (layer == 0) {
+            for (int k = 0; k < KB; ++k) z[k] = theta0[k];
+        } else {
+            const float4 *src = reinterpret_cast<const float4 *>(L + (long long)j * KB);
+#pragma unroll
+            for (int v = 0; v < KB / 4; ++v) {
+                const float4 f4 = src[v];
+                z[4 * v] = f4.x;
+                z[4 * v + 1] = f4.y;
+                z[4 * v + 2] = f4.z;
+                z[4 * v + 3] = f4.w;
+            }
+        }
         softmax32(z, q);
         const float xv = j < n ? x[3ll * j + layer] : 0.5f;
         const int b = min((int)(xv * KB), KB - 1);
         // d log Q_b / d z_k = r (delta_bk - s_k), r = (1 - mix) s_b / Q_b (1 without mixing)
-        const float Qb = mixed(q[b], mix);
-        const float r = mix != 0.0f ? (1.0f - mix) * q[b] / Qb : 1.0f;
+        float Qb = q[0], qb = q[0];
+#pragma unroll
+        for (int k = 1; k < KB; ++k)
+            if (k == b) qb = q[k];
+        Qb = mixed(qb, mix);
+        const float r = mix != 0.0f ? (1.0f - mix) * qb / Qb : 1.0f;
         if (ww != 0.0f) atomicAdd(&s_loss, -ww * logf(KB * Qb));
-        for (int k = 0; k < KB; ++k) {
-            const float g = -ww * r * ((k == b ? 1.0f : 0.0f) - q[k]);
-            if (layer == 0) {
-                if (ww != 0.0f) atomicAdd(&s_dt[k], g);
-            } else {
-                const __nv_bfloat16 gb = __float2bfloat16_rn(g);
-                dL[(long long)j * KB + k] = gb;
-                dLt[(long long)k * rows + j] = gb;
+        float g[KB];
+#pragma unroll
+        for (int k = 0; k < KB; ++k) g[k] = -ww * r * ((k == b ? 1.0f : 0.0f) - q[k]);
+        if (layer != 0) {
+            uint32_t pk[KB / 2];
+#pragma unroll
+            for (int k = 0; k < KB; k += 2) {
+                __nv_bfloat162 p2 = __floats2bfloat162_rn(g[k], g[k + 1]);
+                pk[k / 2] = *reinterpret_cast<uint32_t *>(&p2);
+                dLt[(long long)k * rows + j] = p2.x;
+                dLt[(long long)(k + 1) * rows + j] = p2.y;
+            }
+            uint4 *dst = reinterpret_cast<uint4 *>(dL + (long long)j * KB);
+#pragma unroll
+            for (int v = 0; v < KB / 8; ++v)
+                dst[v] = make_uint4(pk[4 * v], pk[4 * v + 1], pk[4 * v + 2], pk[4 * v + 3]);
+        } else {
+            // theta0's gradient: warp sums, then one shared atomic per warp and bin
+#pragma unroll
+            for (int k = 0; k < KB; ++k) {
+                float sk = g[k];
+                for (int o = 16; o; o >>= 1) sk += __shfl_xor_sync(__activemask(), sk, o);
+                if ((threadIdx.x & 31) == 0) atomicAdd(&s_dt[k], sk);
             }
         }
     }
@@ -158,15 +210,28 @@ __global__ void k_loss_grad(int layer, const float *__restrict__ theta0, const f
     if (threadIdx.x == 0) atomicAdd(loss, s_loss);
 }
 
-// out[r] += sum_j At[r][j] (bias gradient from a transposed backward signal), one warp per row.
+// out[r] += sum_j At[r][j] (bias gradient from a transposed backward signal): one warp
+// per (row, 2048-column slice), 16-byte vector loads, one atomic per warp.
+constexpr int ROWSUM_SLICE = 2048;
 __global__ void k_rowsum(const __nv_bfloat16 *__restrict__ At, int nrows, int rows, float *__restrict__ out)
 {
     const int r = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     if (r >= nrows) return;
+    const int lane = threadIdx.x & 31;
+    const int j0 = blockIdx.y * ROWSUM_SLICE, j1 = min(rows, j0 + ROWSUM_SLICE);
+    const __nv_bfloat16 *row = At + (long long)r * rows;
     float s = 0.0f;
-    for (int j = threadIdx.x & 31; j < rows; j += 32) s += __bfloat162float(At[(long long)r * rows + j]);
+    for (int j = j0 + lane * 8; j < j1; j += 32 * 8) {  // rows is a multiple of 128: whole vectors
+        const uint4 v = *reinterpret_cast<const uint4 *>(row + j);
+        const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&v);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float2 f = __bfloat1622float2(h[q]);
+            s += f.x + f.y;
+        }
+    }
     for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) out[r] += s;
+    if (lane == 0) atomicAdd(out + r, s);
 }
 
 __global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m, float *__restrict__ v,
@@ -315,12 +380,12 @@ int qmcrt_warp_grad(const qmcrt_warp *warp, const float *d_x, const float *d_w, 
         k_loss_grad<<<(W.rows + 255) / 256, 256, 0, s>>>(0, warp->d_params, nullptr, x, w, cnt, W.rows, W.wsum, d_loss,
                                                           d_grad, nullptr, nullptr, warp->uniform_mix);
         for (int m = 0; m < 2; ++m) {
-            k_features<<<blocks((long long)W.rows * WD), 256, 0, s>>>(x, cnt, W.rows, m, W.F, W.Ft);
+            k_features<<<W.rows / FEAT_ROWS, 256, 0, s>>>(x, cnt, W.rows, m, W.F, W.Ft);
             if ((rc = mlp_forward(warp, W, m, true, s))) return rc;
             k_loss_grad<<<(W.rows + 255) / 256, 256, 0, s>>>(m + 1, warp->d_params, W.L, x, w, cnt, W.rows, W.wsum,
                                                               d_loss, d_grad, W.dL, W.dLt, warp->uniform_mix);
             if ((rc = launch_status("warp loss"))) return rc;
-            const int splits = std::max(1, W.rows / 512);  // weight gradients: K = rows split over CTAs
+            const int splits = std::max(1, W.rows / 1024);  // weight gradients: K = rows split over CTAs
             // layer 3: signal dL [rows x 32]
             const __nv_bfloat16 *dP = W.dL, *dPt = W.dLt;
             for (int l = 3; l >= 0; --l) {
@@ -331,7 +396,8 @@ int qmcrt_warp_grad(const qmcrt_warp *warp, const float *d_x, const float *d_w, 
                 gw.atomic_f32 = splits > 1;
                 if (gw.atomic_f32 == 0) gw.atomic_f32 = 1;  // accumulate into the caller's gradient
                 if ((rc = gemm(dPt, Xt, N_out, WD, W.rows, splits, gw, s))) return rc;
-                k_rowsum<<<(N_out + 7) / 8, 256, 0, s>>>(dPt, N_out, W.rows, d_grad + param_b(m, l));
+                k_rowsum<<<dim3((N_out + 7) / 8, (W.rows + ROWSUM_SLICE - 1) / ROWSUM_SLICE), 256, 0, s>>>(
+                    dPt, N_out, W.rows, d_grad + param_b(m, l));
                 if ((rc = launch_status("warp bias grad"))) return rc;
                 if (l == 0) break;
                 GemmEpi gx = epi(warp->d_error);  // dH[l-1] = (dP . W[l]) * (H[l-1] > 0)

@@ -6,15 +6,16 @@
 //
 // A and B are BF16, row-major with K contiguous, in global memory.  One CTA of 128
 // threads computes one 128-row tile of D (N = 32, 64 or 128 columns); a split of the K
-// range over gridDim.y adds partial tiles atomically.  Per 32-wide K chunk the CTA
-// copies the A and B chunks into shared memory in the canonical K-major layout without
-// swizzle (8-row x 16-byte core matrices, contiguous; adjacent core matrices along K
-// 128 bytes apart, along M/N 512 bytes apart), one thread issues two
-// tcgen05.mma.cta_group::1.kind::f16 (K = 16 each) into an FP32 accumulator in tensor
-// memory, and commits them to an mbarrier that all threads wait on (bounded: a wait
-// that runs out sets an error word and the kernel skips to the end, freeing its tensor
-// memory).  The epilogue reads the accumulator with tcgen05.ld (each warp its 32
-// lanes = rows).
+// range over gridDim.y adds partial tiles atomically.  K is taken in 64-wide chunks
+// through two shared-memory stages: asynchronous 16-byte copies (cp.async) write the A
+// and B chunks in the canonical K-major layout without swizzle (8-row x 16-byte core
+// matrices; adjacent core matrices along K 128 bytes apart, along M/N 1024 bytes
+// apart); one thread issues four tcgen05.mma.cta_group::1.kind::f16 (K = 16 each) into
+// an FP32 accumulator in tensor memory and commits them to the stage's mbarrier; the
+// stage is refilled once that barrier completes, while the other stage's copies are in
+// flight.  Every wait is bounded: one that runs out sets an error word and the kernel
+// skips to the end, freeing its tensor memory.  The epilogue reads the accumulator with
+// tcgen05.ld (each warp its 32 lanes = rows).
 #pragma once
 
 #include <cstdint>
@@ -38,9 +39,16 @@ struct GemmEpi {
 };
 
 constexpr int GEMM_BM = 128;     // rows per CTA (one TMEM lane per row)
-constexpr int GEMM_BK = 32;      // K per shared-memory chunk (two MMAs of K = 16)
+constexpr int GEMM_BK = 64;      // K per shared-memory stage (four MMAs of K = 16)
+constexpr int GEMM_STAGES = 2;   // stages in flight: the next chunk loads while the MMAs run
 constexpr int GEMM_THREADS = 128;
 constexpr long long GEMM_WAIT_LIMIT = 1ll << 24;  // mbarrier polls before giving up
+
+template <int N>
+constexpr int gemm_smem_bytes()
+{
+    return GEMM_STAGES * (GEMM_BM + N) * GEMM_BK * 2 + 64 + 128;  // stages, barriers, alignment slack
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -63,28 +71,23 @@ __host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N)
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-template <int N>
-struct GemmSmem {
-    alignas(128) uint8_t a[GEMM_BM * GEMM_BK * 2];  // 8 KB
-    alignas(128) uint8_t b[N * GEMM_BK * 2];
-    alignas(8) unsigned long long mbar;
-    uint32_t tmem;
-    int fail;
-};
-
-// Copy a [rows x 32] BF16 chunk (row stride ld elements) into the canonical layout:
-// row r, element c -> ((r / 8) * 4 + c / 8) * 128 + (r % 8) * 16 + (c % 8) * 2 bytes.
+// Start copying a [ROWS x GEMM_BK] BF16 chunk (row stride ld) into the canonical layout
+// with asynchronous 16-byte copies: row r, element c -> ((r / 8) * 8 + c / 8) * 128 +
+// (r % 8) * 16 + (c % 8) * 2 bytes.  Rows >= nrows and columns >= kend are zero-filled
+// (a copy of 0 source bytes).
 template <int ROWS>
-__device__ __forceinline__ void stage_chunk(uint8_t *dst, const __nv_bfloat16 *src, int row0, int nrows, long long ld,
-                                            int k0, int K)
+__device__ __forceinline__ void stage_async(uint8_t *dst, const __nv_bfloat16 *src, int row0, int nrows, long long ld,
+                                            int k0, int kend)
 {
-    constexpr int VEC = ROWS * GEMM_BK / 8;  // 16-byte vectors
+    constexpr int KV = GEMM_BK / 8;  // 16-byte vectors per row
+    constexpr int VEC = ROWS * KV;
     for (int v = threadIdx.x; v < VEC; v += GEMM_THREADS) {
-        const int r = v >> 2, kb = v & 3;
-        uint4 val = make_uint4(0, 0, 0, 0);
+        const int r = v / KV, kb = v % KV;
         const int gr = row0 + r, gk = k0 + kb * 8;
-        if (gr < nrows && gk < K) val = *reinterpret_cast<const uint4 *>(src + (long long)gr * ld + gk);
-        *reinterpret_cast<uint4 *>(dst + ((r >> 3) * 4 + kb) * 128 + (r & 7) * 16) = val;
+        const bool in = gr < nrows && gk < kend;
+        const __nv_bfloat16 *g = in ? src + (long long)gr * ld + gk : src;
+        const uint32_t d = smem_u32(dst + ((r >> 3) * KV + kb) * 128 + (r & 7) * 16);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(g), "r"(in ? 16 : 0) : "memory");
     }
 }
 
@@ -104,6 +107,9 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase)
     return false;
 }
 
+// D[M x N] = A[M x K] . B[N x K]^T for the 128-row tile blockIdx.x and the K range
+// blockIdx.y, two shared-memory stages deep: while the tensor core works on chunk c,
+// the asynchronous copies of chunk c + 1 are already in flight.
 template <int N>
 __global__ void __launch_bounds__(GEMM_THREADS) k_gemm_bf16(const __nv_bfloat16 *__restrict__ A,
                                                            const __nv_bfloat16 *__restrict__ B, int M, int K,
@@ -111,40 +117,59 @@ __global__ void __launch_bounds__(GEMM_THREADS) k_gemm_bf16(const __nv_bfloat16 
 {
     static_assert(N == 32 || N == 64 || N == 128, "N tile");
     constexpr int TMEM_COLS = N < 32 ? 32 : N;
-    __shared__ GemmSmem<N> sm;
+    constexpr int A_STAGE = GEMM_BM * GEMM_BK * 2, B_STAGE = N * GEMM_BK * 2;
+    constexpr int SBO = (GEMM_BK / 8) * 128;  // 8-row group stride
+    extern __shared__ uint8_t gemm_smem_raw[];
+    uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(gemm_smem_raw) + 127) & ~uintptr_t(127));
+    uint8_t *sa = sm, *sb = sm + GEMM_STAGES * A_STAGE;
+    unsigned long long *mbar = reinterpret_cast<unsigned long long *>(sb + GEMM_STAGES * B_STAGE);
+    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(mbar + GEMM_STAGES);
+    int *s_fail = reinterpret_cast<int *>(s_tmem + 1);
+
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int row0 = blockIdx.x * GEMM_BM;
     const int kbeg = blockIdx.y * k_per_split, kend = min(K, kbeg + k_per_split);
+    const int nchunks = kend > kbeg ? (kend - kbeg + GEMM_BK - 1) / GEMM_BK : 0;
     if (tid == 0) {
-        sm.fail = 0;
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sm.mbar)) : "memory");
+        *s_fail = 0;
+        for (int st = 0; st < GEMM_STAGES; ++st)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[st])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm.tmem)),
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)),
                      "r"(TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    // prologue: the first stages' copies
+    for (int c = 0; c < GEMM_STAGES && c < nchunks; ++c) {
+        const int k0 = kbeg + c * GEMM_BK;
+        stage_async<GEMM_BM>(sa + c * A_STAGE, A, row0, M, K, k0, kend);
+        stage_async<N>(sb + c * B_STAGE, B, 0, N, K, k0, kend);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = sm.tmem;
+    const uint32_t tmem = *s_tmem;
     const uint32_t idesc = umma_idesc_bf16(GEMM_BM, N);
-    uint32_t phase = 0;
-    bool any = false;
-    for (int k0 = kbeg; k0 < kend; k0 += GEMM_BK) {
-        stage_chunk<GEMM_BM>(sm.a, A, row0, M, K, k0, kend);
-        stage_chunk<N>(sm.b, B, 0, N, K, k0, kend);
+    uint32_t phase[GEMM_STAGES] = {0u, 0u};
+    bool ok = true;
+    for (int c = 0; c < nchunks; ++c) {
+        const int st = c % GEMM_STAGES;
+        // this thread's copies of chunk c have landed (the newer group may still fly)
+        if (c + 1 < nchunks) asm volatile("cp.async.wait_group 1;" ::: "memory");
+        else asm volatile("cp.async.wait_group 0;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-            for (int s = 0; s < GEMM_BK / 16; ++s) {
-                const uint64_t ad = umma_desc(smem_u32(sm.a) + s * 256, 128, 512);
-                const uint64_t bd = umma_desc(smem_u32(sm.b) + s * 256, 128, 512);
-                const uint32_t acc = (any || s > 0) ? 1u : 0u;
+            for (int k16 = 0; k16 < GEMM_BK / 16; ++k16) {
+                const uint64_t ad = umma_desc(smem_u32(sa + st * A_STAGE) + k16 * 256, 128, SBO);
+                const uint64_t bd = umma_desc(smem_u32(sb + st * B_STAGE) + k16 * 256, 128, SBO);
+                const uint32_t acc = (c > 0 || k16 > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n\t.reg .pred p;\n\t"
                     "setp.ne.b32 p, %4, 0;\n\t"
@@ -153,17 +178,31 @@ __global__ void __launch_bounds__(GEMM_THREADS) k_gemm_bf16(const __nv_bfloat16 
                     : "memory");
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_u32(&sm.mbar))
+                             smem_u32(&mbar[st]))
                          : "memory");
         }
-        any = true;
-        if (!mbar_wait(smem_u32(&sm.mbar), phase)) sm.fail = 1;
-        phase ^= 1u;
-        __syncthreads();
-        if (sm.fail) break;
+        const int next = c + GEMM_STAGES;
+        if (next < nchunks || c == nchunks - 1) {
+            // the MMAs reading stage st must finish before it is refilled (or, for the
+            // last chunk, before the accumulator is read)
+            if (!mbar_wait(smem_u32(&mbar[st]), phase[st])) atomicExch(s_fail, 1);
+            phase[st] ^= 1u;
+            __syncthreads();
+            if (*reinterpret_cast<volatile int *>(s_fail)) {
+                ok = false;
+                break;
+            }
+            if (next < nchunks) {
+                const int k0 = kbeg + next * GEMM_BK;
+                stage_async<GEMM_BM>(sa + st * A_STAGE, A, row0, M, K, k0, kend);
+                stage_async<N>(sb + st * B_STAGE, B, 0, N, K, k0, kend);
+                asm volatile("cp.async.commit_group;" ::: "memory");
+            }
+        }
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (!sm.fail && any) {
+    if (ok && nchunks > 0) {
         // epilogue: this thread owns row (32 * warp + lane) of the tile
         const int row = row0 + warp * 32 + lane;
         const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
@@ -182,24 +221,62 @@ __global__ void __launch_bounds__(GEMM_THREADS) k_gemm_bf16(const __nv_bfloat16 
                 : "r"(taddr + (uint32_t)c0));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             if (row < M) {
+                // a thread owns 32 consecutive values of its row: row-major reads and
+                // writes go as 16-byte vectors; the transposed copy is coalesced across
+                // the warp (its 32 rows are adjacent)
+                const long long rbase = (long long)row * N + c0;
+                float v[32];
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    const int col = c0 + j;
-                    float v = __uint_as_float(r[j]);
-                    if (ep.bias) v += ep.bias[col];
-                    if (ep.relu) v = fmaxf(v, 0.0f);
-                    if (ep.mask && !(__bfloat162float(ep.mask[(long long)row * N + col]) > 0.0f)) v = 0.0f;
-                    if (ep.out_f32) {
-                        if (ep.atomic_f32) atomicAdd(ep.out_f32 + (long long)row * N + col, v);
-                        else ep.out_f32[(long long)row * N + col] = v;
+                    v[j] = __uint_as_float(r[j]);
+                    if (ep.bias) v[j] += ep.bias[c0 + j];
+                    if (ep.relu) v[j] = fmaxf(v[j], 0.0f);
+                }
+                if (ep.mask) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const uint4 mv = reinterpret_cast<const uint4 *>(ep.mask + rbase)[q];
+                        const __nv_bfloat162 *mh = reinterpret_cast<const __nv_bfloat162 *>(&mv);
+#pragma unroll
+                        for (int h = 0; h < 4; ++h) {
+                            const float2 m2 = __bfloat1622float2(mh[h]);
+                            if (!(m2.x > 0.0f)) v[q * 8 + 2 * h] = 0.0f;
+                            if (!(m2.y > 0.0f)) v[q * 8 + 2 * h + 1] = 0.0f;
+                        }
                     }
-                    if (ep.out_bf16) ep.out_bf16[(long long)row * N + col] = __float2bfloat16_rn(v);
-                    if (ep.out_bf16_t) ep.out_bf16_t[(long long)col * ep.ldt + row] = __float2bfloat16_rn(v);
+                }
+                if (ep.out_f32) {
+                    if (ep.atomic_f32) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) atomicAdd(ep.out_f32 + rbase + j, v[j]);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 8; ++q)
+                            reinterpret_cast<float4 *>(ep.out_f32 + rbase)[q] =
+                                make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                    }
+                }
+                if (ep.out_bf16) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        uint32_t w[4];
+#pragma unroll
+                        for (int h = 0; h < 4; ++h) {
+                            __nv_bfloat162 p2 = __floats2bfloat162_rn(v[q * 8 + 2 * h], v[q * 8 + 2 * h + 1]);
+                            w[h] = *reinterpret_cast<uint32_t *>(&p2);
+                        }
+                        reinterpret_cast<uint4 *>(ep.out_bf16 + rbase)[q] = make_uint4(w[0], w[1], w[2], w[3]);
+                    }
+                }
+                if (ep.out_bf16_t) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        ep.out_bf16_t[(long long)(c0 + j) * ep.ldt + row] = __float2bfloat16_rn(v[j]);
                 }
             }
         }
     }
-    if (sm.fail && tid == 0 && ep.error) atomicExch(ep.error, 1);
+    if (tid == 0 && *s_fail && ep.error) atomicExch(ep.error, 1);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
