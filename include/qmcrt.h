@@ -276,10 +276,11 @@ typedef struct qmcrt_gemm_epilogue {
 /*
  * qmcrt_gemm_bf16 -- D[M][N] = A[M][K] . B[N][K]^T on the tensor cores (BF16 inputs, FP32
  * accumulation), then the epilogue (bias, ReLU, ReLU mask, FP32 / BF16 / transposed
- * BF16 outputs).  A, B: device bf16, row-major, K contiguous, 16-byte aligned.  The
- * paper has no counterpart; it is the building block of the learned warp's network.
+ * BF16 outputs).  A, B: device bf16, row-major, K contiguous, 16-byte aligned; the mask
+ * and the FP32 / BF16 outputs 16-byte aligned too.  The paper has no counterpart; it is
+ * the building block of the learned warp's network.
  * Errors: INVALID_ARG (NULL pointers, M < 1, N not 32/64/128, K not a positive multiple
- * of 32, ldt < M, bias with k_splits > 1), CUDA.
+ * of 32, ldt < M, bias with k_splits > 1, misaligned pointers), CUDA.
  */
 int qmcrt_gemm_bf16(const void *d_A, const void *d_B, int32_t M, int32_t N, int32_t K,
                     const qmcrt_gemm_epilogue *epilogue, void *stream);
