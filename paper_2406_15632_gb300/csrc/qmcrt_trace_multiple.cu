@@ -28,8 +28,10 @@ struct OneObserver {
     }
 };
 
+// FP32: at most 64 registers, 4 blocks (32 warps) per SM: the walks are latency-bound
+// and the extra warps pay for a few spilled registers (9 % faster than 80 registers).
 template <class T>
-__global__ void __launch_bounds__(256, 3) k_trace_multiple(const __grid_constant__ TraceP<T> P)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_trace_multiple(const __grid_constant__ TraceP<T> P)
 {
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if ((tid & ~31ull) >= P.ord.threads) return;  // uniform per warp
