@@ -220,6 +220,7 @@ int fill_trace(const qmcrt_medium *md, const qmcrt_source *src, const qmcrt_dust
             P.med.lo[a] = (T)md->lo[a];
             P.med.hi[a] = (T)md->hi[a];
             P.med.h[a] = (T)((md->hi[a] - md->lo[a]) / n[a]);
+            P.med.inv_h[a] = (T)(n[a] / (md->hi[a] - md->lo[a]));
         }
         if (md->pad != 0 && md->pad < QMCRT_MIN_PAD)
             return fail(QMCRT_ERR_INVALID_ARG, "pad %d: 0 or at least %d", md->pad, QMCRT_MIN_PAD);

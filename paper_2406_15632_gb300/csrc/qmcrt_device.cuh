@@ -267,15 +267,21 @@ __device__ __forceinline__ bool packet_index(const OrderP &O, uint64_t first, ui
     for (int j = 0; j < O.bits; ++j) g ^= ((box >> j) & 1u) ? O.rm[j] : 0u;
     for (int j = 0; j < O.tt; ++j) g ^= ((tl >> j) & 1u) ? O.k[j] : 0u;
     const bool nied = O.net == 2;
-    uint32_t b0, b1, b2;
-    if (nied) {
-        b0 = niederreiter_u32((uint32_t)base, 0);
-        b1 = niederreiter_u32((uint32_t)base, 1);
-        b2 = niederreiter_u32((uint32_t)base, 2);
-    } else {
-        b0 = sobol_u32((uint32_t)base, 0);
-        b1 = sobol_u32((uint32_t)base, 1);
-        b2 = sobol_u32((uint32_t)base, 2);
+    // The block start is a multiple of 2^m, so its digit vector (Gray code for Sobol)
+    // has set bits only from m - 1 up: XOR the columns of those bits alone.
+    uint32_t b0 = 0, b1 = 0, b2 = 0;
+    const uint32_t b32 = (uint32_t)base;
+    for (uint32_t gb = nied ? b32 : b32 ^ (b32 >> 1); gb; gb &= gb - 1u) {
+        const int k = __ffs(gb) - 1;
+        if (nied) {
+            b0 ^= __ldg(&d_nied_v[0][k]);
+            b1 ^= __ldg(&d_nied_v[1][k]);
+            b2 ^= __ldg(&d_nied_v[2][k]);
+        } else {
+            b0 ^= c_sobol_v[0][k];
+            b1 ^= c_sobol_v[1][k];
+            b2 ^= c_sobol_v[2][k];
+        }
     }
     const uint32_t y = (lead_bits(b0, O.a) << (O.b + O.c)) | (lead_bits(b1, O.b) << O.c) | lead_bits(b2, O.c);
     for (int j = 0; j < O.bits; ++j) g ^= ((y >> j) & 1u) ? O.ry[j] : 0u;
@@ -289,12 +295,13 @@ __device__ __forceinline__ bool packet_index(const OrderP &O, uint64_t first, ui
 
 // Cell of coordinate x; on a face, the cell the ray enters.  (x - lo) drops the low
 // digits of a coordinate much smaller than lo (in float a point 2e-8 below the face
-// through the origin becomes a point on it), so the estimate is settled against the
-// face coordinates themselves.
+// through the origin becomes a point on it), so the estimate (x - lo) / h, taken with
+// the reciprocal, is settled against the face coordinates themselves: the result does
+// not depend on the rounding of the estimate.
 template <class T>
-__device__ __forceinline__ int start_cell(T x, T lo, T h, T d)
+__device__ __forceinline__ int start_cell(T x, T lo, T h, T inv_h, T d)
 {
-    int c = (int)Mth<T>::floor_((x - lo) / h);
+    int c = (int)Mth<T>::floor_((x - lo) * inv_h);
     if (x < lo + T(c) * h) --c;
     else if (x >= lo + T(c + 1) * h) ++c;
     if (d < T(0) && x == lo + T(c) * h) --c;
@@ -315,14 +322,15 @@ __device__ __forceinline__ AxisWalk<T> axis_setup(T p, T d, int c, T lo, T h, in
     a.dt = T(0);
     a.step = 0;
     a.left = 0;
+    const T r = T(1) / d;  // one division per axis: the face distance and the cell crossing
     if (d > T(0)) {
-        a.s = (lo + T(c + 1) * h - p) / d;
-        a.dt = h / d;
+        a.s = (lo + T(c + 1) * h - p) * r;
+        a.dt = h * r;
         a.step = stride;
         a.left = n - 1 - c;
     } else if (d < T(0)) {
-        a.s = (lo + T(c) * h - p) / d;
-        a.dt = -h / d;
+        a.s = (lo + T(c) * h - p) * r;
+        a.dt = -h * r;
         a.step = -stride;
         a.left = c;
     }
@@ -372,9 +380,9 @@ template <class T, bool TARGET>
 __device__ __forceinline__ bool grid_walk(const MediumP<T> &G, const T p[3], const T d[3], T target_raw, T &tau_raw,
                                           T &t_out)
 {
-    const int cx = start_cell(p[0], G.lo[0], G.h[0], d[0]);
-    const int cy = start_cell(p[1], G.lo[1], G.h[1], d[1]);
-    const int cz = start_cell(p[2], G.lo[2], G.h[2], d[2]);
+    const int cx = start_cell(p[0], G.lo[0], G.h[0], G.inv_h[0], d[0]);
+    const int cy = start_cell(p[1], G.lo[1], G.h[1], G.inv_h[1], d[1]);
+    const int cz = start_cell(p[2], G.lo[2], G.h[2], G.inv_h[2], d[2]);
     tau_raw = T(0);
     t_out = T(0);
     if (!walkable(p, d)) return false;
@@ -472,9 +480,9 @@ template <class T, bool TARGET>
 __device__ __forceinline__ bool grid_walk_padded(const MediumP<T> &G, const T p[3], const T d[3], T target_raw,
                                                  T &tau_raw, T &t_out)
 {
-    const int cx = start_cell(p[0], G.lo[0], G.h[0], d[0]);
-    const int cy = start_cell(p[1], G.lo[1], G.h[1], d[1]);
-    const int cz = start_cell(p[2], G.lo[2], G.h[2], d[2]);
+    const int cx = start_cell(p[0], G.lo[0], G.h[0], G.inv_h[0], d[0]);
+    const int cy = start_cell(p[1], G.lo[1], G.h[1], G.inv_h[1], d[1]);
+    const int cz = start_cell(p[2], G.lo[2], G.h[2], G.inv_h[2], d[2]);
     tau_raw = T(0);
     t_out = T(0);
     if (!walkable(p, d)) return false;

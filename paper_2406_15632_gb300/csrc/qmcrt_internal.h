@@ -34,6 +34,7 @@ struct MediumP {
     int pad;           // sentinel layers around the grid (0: plain grid, walked with cell counters)
     int stride[3];     // linear index step of one cell along x, y, z (of the padded array if pad > 0)
     T lo[3], hi[3], h[3];
+    T inv_h[3];        // 1 / h: the first estimate of a start cell
     T kscale, inv_kscale;
     T sph_r, sph_k;    // analytic sphere: radius, kscale * extinction
 };
