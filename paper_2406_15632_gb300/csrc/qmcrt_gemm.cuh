@@ -16,10 +16,19 @@
 // flight.  Every wait is bounded: one that runs out sets an error word and the kernel
 // skips to the end, freeing its tensor memory.  The epilogue reads the accumulator with
 // tcgen05.ld (each warp its 32 lanes = rows).
+//
+// For K <= 128 without a K split (every GEMM of the training step over the rows) a
+// persistent form runs instead, one CTA of 256 threads per SM: B stays in shared memory,
+// A is fetched a 128-row tile at a time by 2-D tensor copies (cp.async.bulk.tensor, boxes
+// of 8 K-elements x 128 rows, no swizzle, rows beyond M read as zeros) three tiles ahead,
+// and the epilogue stages the bf16 results in shared memory (row-major with the 16-byte
+// chunks of a row XOR-permuted, and transposed) so that both outputs leave as coalesced
+// 16-byte stores.
 #pragma once
 
 #include <cstdint>
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -276,6 +285,248 @@ __global__ void __launch_bounds__(GEMM_THREADS) k_gemm_bf16(const __nv_bfloat16 
             }
         }
     }
+    if (tid == 0 && *s_fail && ep.error) atomicExch(ep.error, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+constexpr int GEMM_T_KMAX = 128;   // K of the persistent form (B and the A tiles fit in shared memory)
+constexpr int GEMM_T_THREADS = 256;
+constexpr int GEMM_T_ABUF = 3;     // A tiles in flight
+
+template <int N>
+constexpr int gemm_tma_smem_bytes()
+{
+    return N * GEMM_T_KMAX * 2 + GEMM_T_ABUF * GEMM_BM * GEMM_T_KMAX * 2 + GEMM_BM * N * 2 * 2 + 128 + 1024;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t mbar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar)
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect(uint32_t mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_only(uint32_t mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+// Load rows [row0, row0 + ROWS) x K of a K-contiguous matrix as KP / 8 boxes of
+// 8 elements x ROWS rows; box j lands at dst + j * ROWS * 16.  ARRIVE: this thread's
+// arrival on the barrier comes with the expected bytes (else they are only added).
+template <int ROWS, bool ARRIVE>
+__device__ __forceinline__ void tma_tile(uint32_t dst, const CUtensorMap *map, int row0, int KP, uint32_t mbar)
+{
+    if (ARRIVE) mbar_expect(mbar, (uint32_t)(KP / 8) * ROWS * 16);
+    else mbar_expect_only(mbar, (uint32_t)(KP / 8) * ROWS * 16);
+    for (int j = 0; j < KP / 8; ++j) tma_load_2d(dst + j * ROWS * 16, map, 8 * j, row0, mbar);
+}
+
+// The persistent form (K <= GEMM_T_KMAX, no K split): CTA b takes the 128-row tiles
+// b, b + gridDim.x, ...  Thread 0 issues the tensor copies and the MMAs and waits on
+// their barriers (bounded); the 8 warps share the epilogue (warp w: TMEM lanes
+// 32 (w % 4) .., half (w / 4) of the columns).  A tensor map row box of 128 rows (A)
+// and N rows (B), inner box 8 elements.
+template <int N>
+__global__ void __launch_bounds__(GEMM_T_THREADS, 1) k_gemm_bf16_tma(const __grid_constant__ CUtensorMap tmA,
+                                                        const __grid_constant__ CUtensorMap tmB, int M, int K,
+                                                        GemmEpi ep)
+{
+    constexpr int TMEM_COLS = N < 32 ? 32 : N;
+    extern __shared__ uint8_t gemm_smem_raw[];
+    uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(gemm_smem_raw) + 1023) & ~uintptr_t(1023));
+    const int KP = (K + 15) / 16 * 16;
+    constexpr int A_BUF = GEMM_BM * GEMM_T_KMAX * 2;
+    uint8_t *sb = sm;                                  // N x KP
+    uint8_t *sa = sb + N * GEMM_T_KMAX * 2;                 // GEMM_T_ABUF x 128 x KP
+    uint8_t *ss = sa + GEMM_T_ABUF * A_BUF;                 // 128 rows x N bf16, 16-byte chunks XOR-swizzled
+    uint8_t *st = ss + GEMM_BM * N * 2;                // N x 128 bf16 (transposed tile)
+    unsigned long long *mbar = reinterpret_cast<unsigned long long *>(st + GEMM_BM * N * 2);  // [0..2] loads, [3] mma
+    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(mbar + 4);
+    int *s_fail = reinterpret_cast<int *>(s_tmem + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ntiles = (M + GEMM_BM - 1) / GEMM_BM;
+    if (tid == 0) {
+        *s_fail = 0;
+        for (int q = 0; q < 4; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[q])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *s_tmem;
+    // prologue: B with the first A tile (barrier 0), then the next two A tiles
+    int issued = 0;  // A tiles whose loads thread 0 has issued (sequence numbers 0 .. issued - 1)
+    if (tid == 0) {
+        for (int q = 0; q < GEMM_T_ABUF - 1; ++q) {
+            const int t = blockIdx.x + q * gridDim.x;
+            if (t >= ntiles) break;
+            if (q == 0) tma_tile<N, false>(smem_u32(sb), &tmB, 0, KP, smem_u32(&mbar[0]));
+            ++issued;
+            tma_tile<GEMM_BM, true>(smem_u32(sa + q * A_BUF), &tmA, t * GEMM_BM, KP, smem_u32(&mbar[q]));
+        }
+    }
+    const uint32_t idesc = umma_idesc_bf16(GEMM_BM, N);
+    uint32_t lphase[GEMM_T_ABUF] = {0u, 0u, 0u}, mphase = 0u;
+    int i = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+        const int b = i % GEMM_T_ABUF;
+        if (tid == 0) {
+            // refill the buffer the previous tile used (its MMAs are complete)
+            const int tn = t + (GEMM_T_ABUF - 1) * gridDim.x;
+            if (tn < ntiles) {
+                const int bn = (i + GEMM_T_ABUF - 1) % GEMM_T_ABUF;
+                tma_tile<GEMM_BM, true>(smem_u32(sa + bn * A_BUF), &tmA, tn * GEMM_BM, KP, smem_u32(&mbar[bn]));
+                ++issued;
+            }
+            bool ok = mbar_wait(smem_u32(&mbar[b]), lphase[b]);
+            if (ok) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t a0 = smem_u32(sa + b * A_BUF), b0 = smem_u32(sb);
+                for (int k16 = 0; k16 < KP / 16; ++k16) {
+                    const uint64_t ad = umma_desc(a0 + k16 * 2 * GEMM_BM * 16, GEMM_BM * 16, 128);
+                    const uint64_t bd = umma_desc(b0 + k16 * 2 * N * 16, N * 16, 128);
+                    const uint32_t acc = k16 > 0 ? 1u : 0u;
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\t"
+                        "setp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                        : "memory");
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(&mbar[3]))
+                             : "memory");
+                ok = mbar_wait(smem_u32(&mbar[3]), mphase);
+            }
+            if (!ok) *s_fail = 1;
+        }
+        lphase[b] ^= 1u;
+        mphase ^= 1u;
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (*reinterpret_cast<volatile int *>(s_fail)) break;
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31, columns [half * N / 2, + N / 2)
+        const int rl = (warp & 3) * 32 + lane;  // row within the tile
+        const int row = t * GEMM_BM + rl;
+        const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+        constexpr int CH = N >= 64 ? N / 2 : N;  // columns per warp
+        const int cbeg = N >= 64 ? (warp >> 2) * CH : 0;
+        if (N >= 64 || warp < 4) {
+#pragma unroll
+            for (int cc = 0; cc < CH; cc += 32) {
+                const int c0 = cbeg + cc;
+                uint32_t r[32];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                    "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                      "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                      "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                      "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                    : "r"(taddr + (uint32_t)c0));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                float v[32];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    v[j] = __uint_as_float(r[j]);
+                    if (ep.bias) v[j] += __ldg(ep.bias + c0 + j);
+                    if (ep.relu) v[j] = fmaxf(v[j], 0.0f);
+                }
+                const long long rbase = (long long)row * N + c0;
+                if (ep.mask && row < M) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const uint4 mv = reinterpret_cast<const uint4 *>(ep.mask + rbase)[q];
+                        const __nv_bfloat162 *mh = reinterpret_cast<const __nv_bfloat162 *>(&mv);
+#pragma unroll
+                        for (int h = 0; h < 4; ++h) {
+                            const float2 m2 = __bfloat1622float2(mh[h]);
+                            if (!(m2.x > 0.0f)) v[q * 8 + 2 * h] = 0.0f;
+                            if (!(m2.y > 0.0f)) v[q * 8 + 2 * h + 1] = 0.0f;
+                        }
+                    }
+                }
+                if (ep.out_f32 && row < M) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        reinterpret_cast<float4 *>(ep.out_f32 + rbase)[q] =
+                            make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                }
+                if (ep.out_bf16) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        uint32_t w[4];
+#pragma unroll
+                        for (int h = 0; h < 4; ++h) {
+                            __nv_bfloat162 p2 = __floats2bfloat162_rn(v[q * 8 + 2 * h], v[q * 8 + 2 * h + 1]);
+                            w[h] = *reinterpret_cast<uint32_t *>(&p2);
+                        }
+                        const int chunk = (c0 / 8 + q) ^ (rl & (N * 2 / 16 - 1));  // 16-byte chunk within the row
+                        *reinterpret_cast<uint4 *>(ss + rl * (N * 2) + chunk * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+                    }
+                }
+                if (ep.out_bf16_t) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        *reinterpret_cast<__nv_bfloat16 *>(st + (c0 + j) * (GEMM_BM * 2) + rl * 2) = __float2bfloat16_rn(v[j]);
+                }
+            }
+        }
+        __syncthreads();
+        // coalesced stores of the staged tile
+        const int row0 = t * GEMM_BM;
+        if (ep.out_bf16) {
+            constexpr int CPR = N * 2 / 16;  // chunks per row
+            for (int id = tid; id < GEMM_BM * CPR; id += GEMM_T_THREADS) {
+                const int rr = id / CPR, q = id % CPR;
+                if (row0 + rr < M) {
+                    const uint4 val = *reinterpret_cast<const uint4 *>(ss + rr * (N * 2) + (q ^ (rr & (CPR - 1))) * 16);
+                    *reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(ep.out_bf16) + ((long long)(row0 + rr) * N) * 2 + q * 16) = val;
+                }
+            }
+        }
+        if (ep.out_bf16_t) {
+            const bool full = row0 + GEMM_BM <= M && (ep.ldt % 8) == 0;
+            for (int id = tid; id < N * (GEMM_BM / 8); id += GEMM_T_THREADS) {
+                const int c = id / (GEMM_BM / 8), q = id % (GEMM_BM / 8);
+                const uint8_t *srcp = st + c * (GEMM_BM * 2) + q * 16;
+                __nv_bfloat16 *dst = ep.out_bf16_t + (long long)c * ep.ldt + row0 + q * 8;
+                if (full) {
+                    *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(srcp);
+                } else {
+                    for (int e = 0; e < 8; ++e)
+                        if (row0 + q * 8 + e < M) dst[e] = reinterpret_cast<const __nv_bfloat16 *>(srcp)[e];
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();  // staging buffers and the accumulator are free for the next tile
+    }
+    // drain (only after a failed wait): loads issued but not consumed must land before
+    // the shared memory is released
+    if (tid == 0)
+        for (int s = i; s < issued; ++s) mbar_wait(smem_u32(&mbar[s % GEMM_T_ABUF]), (uint32_t)((s / GEMM_T_ABUF) & 1));
     if (tid == 0 && *s_fail && ep.error) atomicExch(ep.error, 1);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
