@@ -385,7 +385,7 @@ int qmcrt_warp_grad(const qmcrt_warp *warp, const float *d_x, const float *d_w, 
             k_loss_grad<<<(W.rows + 255) / 256, 256, 0, s>>>(m + 1, warp->d_params, W.L, x, w, cnt, W.rows, W.wsum,
                                                               d_loss, d_grad, W.dL, W.dLt, warp->uniform_mix);
             if ((rc = launch_status("warp loss"))) return rc;
-            const int splits = std::max(1, W.rows / 1024);  // weight gradients: K = rows split over CTAs
+            const int splits = std::max(1, W.rows / 512);  // weight gradients: K = rows split over CTAs
             // layer 3: signal dL [rows x 32]
             const __nv_bfloat16 *dP = W.dL, *dPt = W.dLt;
             for (int l = 3; l >= 0; --l) {

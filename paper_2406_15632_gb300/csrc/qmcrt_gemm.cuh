@@ -536,4 +536,144 @@ __global__ void __launch_bounds__(GEMM_T_THREADS, 1) k_gemm_bf16_tma(const __gri
     }
 }
 
+
+// Split-K form for the weight gradients (M <= 128 rows, K = the training rows split in
+// k_per_split slices over blockIdx.y): 64-wide K chunks of A (128 x 64) and B (N x 64)
+// arrive by tensor copies in GEMM_SK_STAGES stages; thread 0 issues copies and MMAs, and
+// refills a stage once its MMAs have completed, so GEMM_SK_STAGES - 1 chunks are always in
+// flight.  The epilogue adds the FP32 partial tile into out_f32 with vector reductions.
+constexpr int GEMM_SK_STAGES = 4;
+
+template <int N>
+constexpr int gemm_sk_smem_bytes()
+{
+    return GEMM_SK_STAGES * (GEMM_BM + N) * GEMM_BK * 2 + 128 + 1024;
+}
+
+template <int N>
+__global__ void __launch_bounds__(GEMM_THREADS, 1) k_gemm_bf16_splitk(const __grid_constant__ CUtensorMap tmA,
+                                                                     const __grid_constant__ CUtensorMap tmB, int M,
+                                                                     int K, int k_per_split, GemmEpi ep)
+{
+    constexpr int TMEM_COLS = N < 32 ? 32 : N;
+    constexpr int A_ST = GEMM_BM * GEMM_BK * 2, B_ST = N * GEMM_BK * 2;
+    extern __shared__ uint8_t gemm_smem_raw[];
+    uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(gemm_smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *sa = sm, *sb = sm + GEMM_SK_STAGES * A_ST;
+    unsigned long long *full = reinterpret_cast<unsigned long long *>(sb + GEMM_SK_STAGES * B_ST);
+    unsigned long long *done = full + GEMM_SK_STAGES;
+    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(done + GEMM_SK_STAGES);
+    int *s_fail = reinterpret_cast<int *>(s_tmem + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int kbeg = blockIdx.y * k_per_split, kend = min(K, kbeg + k_per_split);
+    const int nchunks = kend > kbeg ? (kend - kbeg + GEMM_BK - 1) / GEMM_BK : 0;
+    if (tid == 0) {
+        *s_fail = 0;
+        for (int q = 0; q < 2 * GEMM_SK_STAGES; ++q)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[q])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *s_tmem;
+    if (tid == 0) {
+        const uint32_t idesc = umma_idesc_bf16(GEMM_BM, N);
+        constexpr uint32_t BYTES = (uint32_t)(A_ST + B_ST);
+        int issued = 0;
+        auto issue = [&](int c) {
+            const int st = c % GEMM_SK_STAGES, k0 = kbeg + c * GEMM_BK;
+            const uint32_t mb = smem_u32(&full[st]);
+            mbar_expect(mb, BYTES);
+            for (int j = 0; j < GEMM_BK / 8; ++j) {
+                tma_load_2d(smem_u32(sa + st * A_ST) + j * GEMM_BM * 16, &tmA, k0 + 8 * j, 0, mb);
+                tma_load_2d(smem_u32(sb + st * B_ST) + j * N * 16, &tmB, k0 + 8 * j, 0, mb);
+            }
+            ++issued;
+        };
+        for (int c = 0; c < GEMM_SK_STAGES && c < nchunks; ++c) issue(c);
+        bool ok = true;
+        int c = 0;
+        for (; c < nchunks && ok; ++c) {
+            const int st = c % GEMM_SK_STAGES;
+            const uint32_t par = (uint32_t)((c / GEMM_SK_STAGES) & 1);
+            ok = mbar_wait(smem_u32(&full[st]), par);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int k16 = 0; k16 < GEMM_BK / 16; ++k16) {
+                const uint64_t ad = umma_desc(smem_u32(sa + st * A_ST) + k16 * 2 * GEMM_BM * 16, GEMM_BM * 16, 128);
+                const uint64_t bd = umma_desc(smem_u32(sb + st * B_ST) + k16 * 2 * N * 16, N * 16, 128);
+                const uint32_t acc = (c > 0 || k16 > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\t"
+                    "setp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&done[st]))
+                         : "memory");
+            if (c + GEMM_SK_STAGES < nchunks || c == nchunks - 1) {
+                // the stage's MMAs must finish before it is refilled (or, after the last
+                // chunk, before the accumulator is read)
+                ok = mbar_wait(smem_u32(&done[st]), par);
+                if (ok && c + GEMM_SK_STAGES < nchunks) issue(c + GEMM_SK_STAGES);
+            }
+        }
+        if (!ok) {
+            *s_fail = 1;
+            // loads issued but not consumed must land before the shared memory is released
+            for (int q = c; q < issued; ++q)
+                mbar_wait(smem_u32(&full[q % GEMM_SK_STAGES]), (uint32_t)((q / GEMM_SK_STAGES) & 1));
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!*reinterpret_cast<volatile int *>(s_fail) && nchunks > 0) {
+        const int row = warp * 32 + lane;
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+        for (int c0 = 0; c0 < N; c0 += 32) {
+            uint32_t r[32];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                  "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                  "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                : "r"(taddr + (uint32_t)c0));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (row < M) {
+                // 16-byte vector reductions (out_f32 is 16-byte aligned, N a multiple of 32)
+                float *dst = ep.out_f32 + (long long)row * N + c0;
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst + 4 * q),
+                                 "f"(__uint_as_float(r[4 * q])), "f"(__uint_as_float(r[4 * q + 1])),
+                                 "f"(__uint_as_float(r[4 * q + 2])), "f"(__uint_as_float(r[4 * q + 3]))
+                                 : "memory");
+            }
+        }
+    }
+    if (tid == 0 && *s_fail && ep.error) atomicExch(ep.error, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
 }  // namespace qmcrt

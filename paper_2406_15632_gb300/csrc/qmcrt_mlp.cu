@@ -1,5 +1,6 @@
 // qmcrt_mlp.cu -- launchers of the tensor-core GEMM (qmcrt_gemm.cuh) used by the
 // learned proposal: the persistent tensor-copy form for K <= 128 without a K split, the
+// tensor-copy split-K form for the weight gradients (one 128-row tile, FP32 atomics), the
 // streaming form otherwise (and wherever a tensor map cannot be made).
 #include <cudaTypedefs.h>
 
@@ -64,6 +65,22 @@ static bool launch_tma(const __nv_bfloat16 *A, const __nv_bfloat16 *B, int M, in
     return true;
 }
 
+// false: the tensor-copy split-K form does not apply.
+template <int N>
+static bool launch_splitk(const __nv_bfloat16 *A, const __nv_bfloat16 *B, int M, int K, int k_per, dim3 grid,
+                          const GemmEpi &ep, cudaStream_t s, cudaError_t &err)
+{
+    constexpr int smem = gemm_sk_smem_bytes<N>();
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(k_gemm_bf16_splitk<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (attr != cudaSuccess) return false;
+    CUtensorMap ma, mb;
+    if (!make_tmap(&ma, A, K, M, GEMM_BM) || !make_tmap(&mb, B, K, N, N)) return false;
+    k_gemm_bf16_splitk<N><<<grid, GEMM_THREADS, smem, s>>>(ma, mb, M, K, k_per, ep);
+    err = cudaGetLastError();
+    return true;
+}
+
 cudaError_t launch_gemm_bf16(const __nv_bfloat16 *A, const __nv_bfloat16 *B, int M, int N, int K, int splits,
                              const GemmEpi &ep, cudaStream_t s)
 {
@@ -80,6 +97,17 @@ cudaError_t launch_gemm_bf16(const __nv_bfloat16 *A, const __nv_bfloat16 *B, int
     }
     const int k_per = ((K + splits - 1) / splits + GEMM_BK - 1) / GEMM_BK * GEMM_BK;
     const dim3 grid((M + GEMM_BM - 1) / GEMM_BM, (K + k_per - 1) / k_per);
+    if (ep.atomic_f32 && ep.out_f32 && !ep.bias && !ep.mask && !ep.out_bf16 && !ep.out_bf16_t && M <= GEMM_BM) {
+        cudaError_t err = cudaSuccess;
+        bool done = false;
+        switch (N) {
+        case 32: done = launch_splitk<32>(A, B, M, K, k_per, grid, ep, s, err); break;
+        case 64: done = launch_splitk<64>(A, B, M, K, k_per, grid, ep, s, err); break;
+        case 128: done = launch_splitk<128>(A, B, M, K, k_per, grid, ep, s, err); break;
+        default: return cudaErrorInvalidValue;
+        }
+        if (done) return err;
+    }
     switch (N) {
     case 32: return launch_n<32>(A, B, M, K, k_per, grid, ep, s);
     case 64: return launch_n<64>(A, B, M, K, k_per, grid, ep, s);
