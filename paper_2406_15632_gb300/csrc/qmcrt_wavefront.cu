@@ -10,11 +10,13 @@
 //
 //   order 1:   emission, forced step, peel-off, roulette, scattering for order 2 ->
 //              queue (with each packet's key, counted in the bucket histogram)
-//   order k:   bucket offsets (one block, shared memory) -> copy into buckets ->
-//              forced step (or march), peel-off, roulette, scattering for k+1 -> queue
+//   order k:   bucket offsets (one block, shared memory) -> record indices into
+//              buckets -> forced step (or march), peel-off, roulette, scattering for
+//              k+1 -> the other queue
 //
-// A queued packet is one 64-byte record (128 in FP64), so the copy into buckets moves
-// whole sectors.
+// A queued packet is one 64-byte record (128 in FP64) that stays where it was appended:
+// the sort moves 4-byte indices, and order k gathers its records through them (two
+// whole sectors per record), appending the survivors to the other queue.
 //
 // Per packet the arithmetic is the one-kernel tracer's, step for step (the scattering
 // that opens order k runs at the end of order k-1), so fixed-point images are identical.
@@ -48,10 +50,11 @@ static_assert(sizeof(Rec<float>) == 64 && sizeof(Rec<double>) == 128, "record si
 
 template <class T>
 struct WaveWork {
-    Rec<T> *q[2];       // [cap] each: q[1] unsorted (appended), q[0] sorted
-    uint32_t *count;    // [2] live packets in q[0], q[1]
-    uint32_t *keys;     // [cap] bucket of each record of q[1]
-    uint32_t *hist;     // [WV_BUCKETS] histogram of q[1], then bucket cursors
+    Rec<T> *q[2];       // [cap] each: order k reads q[(k + 1) & 1] and appends to q[k & 1]
+    uint32_t *count;    // [2] packets of this order, packets appended for the next
+    uint32_t *keys;     // [cap] bucket of each appended record
+    uint32_t *perm;     // [cap] record indices of the queue being read, in bucket order
+    uint32_t *hist;     // [WV_BUCKETS] histogram of the appended records, then bucket cursors
 };
 
 template <class T>
@@ -77,11 +80,11 @@ __device__ __forceinline__ uint32_t wave_key(const MediumP<T> &G, const T pos[3]
     return (key << 5) | (uint32_t)(ct << 3) | (uint32_t)pb;
 }
 
-// Append the lanes with `keep` to the unsorted queue with their bucket keys and count
-// them in the histogram of the next sort (one queue atomic per warp).  All 32 lanes call.
+// Append the lanes with `keep` to queue dst with their bucket keys and count them in
+// the histogram of the next sort (one queue atomic per warp).  All 32 lanes call.
 template <class T>
-__device__ __forceinline__ void append(const TraceP<T> &P, const WaveWork<T> &W, bool keep, const Packet<T> &p,
-                                       uint32_t j)
+__device__ __forceinline__ void append(const TraceP<T> &P, const WaveWork<T> &W, Rec<T> *dst, bool keep,
+                                       const Packet<T> &p, uint32_t j)
 {
     const unsigned m = __ballot_sync(FULL_MASK, keep);
     if (!m) return;
@@ -90,16 +93,19 @@ __device__ __forceinline__ void append(const TraceP<T> &P, const WaveWork<T> &W,
     uint32_t base = 0;
     if (lane == first) base = atomicAdd(W.count + 1, (uint32_t)__popc(m));
     base = __shfl_sync(FULL_MASK, base, first);
+    const uint32_t key = keep ? wave_key(P.med, p.pos, p.n) : 0xffffffffu;
+    // lanes with equal keys count into the histogram with one atomic (a warp's
+    // packets come from one bucket of the last sort and mostly share their key)
+    const unsigned peers = __match_any_sync(FULL_MASK, key);
     if (keep) {
         const uint32_t q = base + __popc(m & ((1u << lane) - 1u));
         Rec<T> r;
         r.p = p;
         r.j = j;
         for (int k = 0; k < (int)(sizeof(r.pad) / 4); ++k) r.pad[k] = 0u;
-        copy_rec(W.q[1] + q, &r);
-        const uint32_t key = wave_key(P.med, p.pos, p.n);
+        copy_rec(dst + q, &r);
         W.keys[q] = key;
-        atomicAdd(W.hist + key, 1u);
+        if (lane == __ffs(peers) - 1) atomicAdd(W.hist + key, (uint32_t)__popc(peers));
     }
 }
 
@@ -201,7 +207,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_wave_first(cons
         p.S[0] = wgt;
     }
     const bool on = run_order(P, 1, i, live, wd, p);
-    append(P, W, on, p, (uint32_t)j);
+    append(P, W, W.q[1], on, p, (uint32_t)j);
     if (live && !on && P.train_log) write_log(P, i, j, p);
 }
 
@@ -235,27 +241,43 @@ __global__ void __launch_bounds__(1024) k_wave_scan(uint32_t *hist)
     for (int b = t; b < WV_BUCKETS; b += 1024) hist[b] = h[b];
 }
 
+// Bucket order of the appended records: perm[cursor of its key] = record index, one
+// cursor atomic per run of equal keys in a warp.
 template <class T>
 __global__ void __launch_bounds__(256) k_wave_scatter(WaveWork<T> W)
 {
     const uint32_t n = W.count[1];
-    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x)
-        copy_rec(W.q[0] + atomicAdd(W.hist + W.keys[q], 1u), W.q[1] + q);
+    const int lane = threadIdx.x & 31;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t q0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); q0 < n; q0 += stride) {  // uniform per warp
+        const uint32_t q = q0 + lane;
+        const bool v = q < n;
+        const uint32_t key = v ? W.keys[q] : 0xffffffffu;
+        const unsigned peers = __match_any_sync(FULL_MASK, key);
+        const int leader = __ffs(peers) - 1;
+        uint32_t base = 0;
+        if (v && lane == leader) base = atomicAdd(W.hist + key, (uint32_t)__popc(peers));
+        base = __shfl_sync(FULL_MASK, base, leader);
+        if (v) W.perm[base + __popc(peers & ((1u << lane) - 1u))] = q;
+    }
 }
 
-// Order k >= 2 over the sorted queue q[0]; survivors are appended to q[1].  FP32 is
-// held to 64 registers (4 blocks, 32 warps per SM; 7 % faster than at 80 registers).
+// Order k >= 2 over queue q[(k + 1) & 1] in bucket order; survivors are appended to
+// q[k & 1].  FP32 is held to 64 registers (4 blocks, 32 warps per SM; 7 % faster than
+// at 80 registers).
 template <class T>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_wave_order(const __grid_constant__ TraceP<T> P, int k, WaveWork<T> W)
 {
     const uint32_t n = W.count[0];
     const uint32_t stride = gridDim.x * blockDim.x;
+    Rec<T> *const src = (k & 1) ? W.q[0] : W.q[1];  // selects, not an indexed parameter array
+    Rec<T> *const dst = (k & 1) ? W.q[1] : W.q[0];
     for (uint32_t q0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); q0 < n; q0 += stride) {  // uniform per warp
         const uint32_t q = q0 + (threadIdx.x & 31u);
         const bool live = q < n;
         Rec<T> r;
         if (live) {
-            copy_rec(&r, W.q[0] + q);
+            copy_rec(&r, src + W.perm[q]);
         } else {
             for (int c = 0; c < 3; ++c) r.p.pos[c] = r.p.n[c] = r.p.a[c] = r.p.S[c] = T(0);
             r.p.tot = r.p.tot2 = T(0);
@@ -264,7 +286,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_wave_order(cons
         const uint64_t i = P.first + r.j;
         const T wd = live ? point<T>(P.pts, i, 4 * (k - 1) + 2) : T(0);
         const bool on = run_order(P, k, i, live, wd, r.p);
-        append(P, W, on, r.p, r.j);
+        append(P, W, dst, on, r.p, r.j);
         if (live && !on && P.train_log) write_log(P, i, r.j, r.p);
     }
 }
@@ -283,6 +305,7 @@ WaveWork<T> carve(void *ws, uint64_t cap)
     W.q[1] = (Rec<T> *)take(cap * sizeof(Rec<T>));
     W.count = (uint32_t *)take(2 * 4);
     W.keys = (uint32_t *)take(cap * 4);
+    W.perm = (uint32_t *)take(cap * 4);
     W.hist = (uint32_t *)take(WV_BUCKETS * 4);
     return W;
 }
@@ -300,7 +323,8 @@ cudaError_t launch_wave(const TraceP<T> &P, void *ws, uint64_t cap, int sms, cud
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const unsigned grid = (unsigned)std::max(1, sms * 8);
     for (int k = 2; k <= P.max_orders; ++k) {
-        // q[1] holds order k's packets with their keys and histogram: sort into q[0]
+        // the queue appended by order k - 1 holds order k's packets with their keys and
+        // histogram: their indices in bucket order into perm
         k_wave_scan<<<1, 1024, 0, s>>>(W.hist);
         k_wave_scatter<T><<<grid, 256, 0, s>>>(W);
         if ((e = cudaMemcpyAsync(W.count, W.count + 1, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
@@ -319,7 +343,7 @@ uint64_t wavefront_workspace_bytes(uint64_t cap, int precision)
 {
     const uint64_t rec = precision == QMCRT_PREC_F64 ? sizeof(Rec<double>) : sizeof(Rec<float>);
     auto pad = [](uint64_t b) { return (b + 255) & ~255ull; };
-    return 2 * pad(cap * rec) + pad(8) + pad(cap * 4) + pad(WV_BUCKETS * 4);
+    return 2 * pad(cap * rec) + pad(8) + 2 * pad(cap * 4) + pad(WV_BUCKETS * 4);
 }
 
 cudaError_t launch_trace_wavefront_f32(const TraceP<float> &p, void *ws, uint64_t cap, int sms, cudaStream_t s)
