@@ -5,8 +5,8 @@
 // but from the second order on each lane scatters into its own direction and the warp
 // waits for its longest walk.  Here every order is a launch over the packets still
 // alive, and between orders the live packets are regrouped by a key built from their
-// position (3 bits per axis) and their new direction (4 bins in cos theta x 8 in phi),
-// so a warp again traces 32 similar rays:
+// position (its octant) and their new direction (32 bins in cos theta x 64 in phi), so a
+// warp again traces 32 similar rays:
 //
 //   order 1:   emission, forced step, peel-off, roulette, scattering for order 2 ->
 //              queue (with each packet's key, counted in the bucket histogram)
@@ -30,8 +30,15 @@ namespace qmcrt {
 
 namespace {
 
-constexpr int WV_KEY_BITS = 14;  // 3 position bits per axis, 4 x 8 direction bins
+// Key split measured on the clumpy envelope (2^24 packets, 20 orders): the octant of
+// the position with 32 x 64 direction bins beats 8^3 position cells with 4 x 8 direction
+// bins by 2 % (walks from one octant in one direction cross nearly the same cells).
+constexpr int WV_POS_BITS = 1;  // per axis: the octant
+constexpr int WV_COS_BITS = 5;  // direction bins: 32 in cos theta
+constexpr int WV_PHI_BITS = 6;  //                 x 64 in phi
+constexpr int WV_KEY_BITS = 3 * WV_POS_BITS + WV_COS_BITS + WV_PHI_BITS;
 constexpr int WV_BUCKETS = 1 << WV_KEY_BITS;
+static_assert(WV_KEY_BITS == 14, "the shared-memory scan holds 2^14 buckets");
 
 template <class T>
 struct Packet {
@@ -69,15 +76,16 @@ __device__ __forceinline__ void copy_rec(Rec<T> *dst, const Rec<T> *src)
 template <class T>
 __device__ __forceinline__ uint32_t wave_key(const MediumP<T> &G, const T pos[3], const T n[3])
 {
+    constexpr int NP = 1 << WV_POS_BITS, NC = 1 << WV_COS_BITS, NF = 1 << WV_PHI_BITS;
     uint32_t key = 0;
     for (int c = 0; c < 3; ++c) {
-        const T f = (pos[c] - G.lo[c]) / (G.hi[c] - G.lo[c]) * T(8);
-        key = (key << 3) | (uint32_t)min(7, max(0, (int)f));
+        const T f = (pos[c] - G.lo[c]) / (G.hi[c] - G.lo[c]) * T(NP);
+        key = (key << WV_POS_BITS) | (uint32_t)min(NP - 1, max(0, (int)f));
     }
-    const int ct = min(3, max(0, (int)((n[2] + T(1)) * T(2))));
+    const int ct = min(NC - 1, max(0, (int)((n[2] + T(1)) * T(NC / 2.0))));
     const float ph = atan2f((float)n[1], (float)n[0]);  // the key only orders packets
-    const int pb = min(7, max(0, (int)((ph + 3.14159265f) * 1.27323954f)));  // 8 / (2 pi)
-    return (key << 5) | (uint32_t)(ct << 3) | (uint32_t)pb;
+    const int pb = min(NF - 1, max(0, (int)((ph + 3.14159265f) * (float)(NF / 6.283185307179586))));
+    return (key << (WV_COS_BITS + WV_PHI_BITS)) | (uint32_t)(ct << WV_PHI_BITS) | (uint32_t)pb;
 }
 
 // Append the lanes with `keep` to queue dst with their bucket keys and count them in
