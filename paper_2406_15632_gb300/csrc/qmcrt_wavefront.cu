@@ -285,7 +285,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_wave_order(cons
         const bool live = q < n;
         Rec<T> r;
         if (live) {
+            const uint32_t qn = q + stride;
+            const uint32_t pn = qn < n ? W.perm[qn] : 0u;
             copy_rec(&r, src + W.perm[q]);
+            // the record this lane gathers next: into L2 while this one is traced
+            if (qn < n) asm volatile("prefetch.global.L2 [%0];" ::"l"(src + pn));
         } else {
             for (int c = 0; c < 3; ++c) r.p.pos[c] = r.p.n[c] = r.p.a[c] = r.p.S[c] = T(0);
             r.p.tot = r.p.tot2 = T(0);
