@@ -369,7 +369,7 @@ def _tte_summary(arms, targets, overhead_ms=None):
     return out
 
 
-def run_time_to_error_learned(ladder=(20, 22, 24, 26), ref_log2=28, ref_seeds=(101, 102, 103, 104),
+def run_time_to_error_learned(ladder=(20, 22, 24, 26, 28), ref_log2=28, ref_seeds=(101, 102, 103, 104),
                               n_log_log2=22, epochs=2, batch_log2=16, lr=1e-2, mix=0.1, weight="l2"):
     """Clumpy envelope (128^3, total radial tau 5, 20 orders, roulette at 1e-4, 512x512
     I/Q/U): wall time to a fixed RMS error of the I image for plain QMC (Sobol), the
