@@ -18,12 +18,12 @@
 // tcgen05.ld (each warp its 32 lanes = rows).
 //
 // For K <= 128 without a K split (every GEMM of the training step over the rows) a
-// persistent form runs instead, one CTA of 256 threads per SM: B stays in shared memory,
-// A is fetched a 128-row tile at a time by 2-D tensor copies (cp.async.bulk.tensor, boxes
-// of 8 K-elements x 128 rows, no swizzle, rows beyond M read as zeros) three tiles ahead,
-// and the epilogue stages the bf16 results in shared memory (row-major with the 16-byte
-// chunks of a row XOR-permuted, and transposed) so that both outputs leave as coalesced
-// 16-byte stores.
+// persistent warp-specialised form runs instead, one CTA of 320 threads per SM: B stays in
+// shared memory, A is fetched a 128-row tile at a time by 2-D tensor copies
+// (cp.async.bulk.tensor, boxes of 8 K-elements x 128 rows, no swizzle, rows beyond M read
+// as zeros) three tiles ahead, two TMEM accumulators alternate, and the epilogue warps
+// store through a shared-memory staging tile with coalesced 16-byte stores.  The weight
+// gradients (one 128-row tile, K split over CTAs) take a tensor-copy split-K form.
 #pragma once
 
 #include <cstdint>
@@ -295,14 +295,7 @@ __global__ void __launch_bounds__(GEMM_THREADS) k_gemm_bf16(const __nv_bfloat16 
 }
 
 constexpr int GEMM_T_KMAX = 128;   // K of the persistent form (B and the A tiles fit in shared memory)
-constexpr int GEMM_T_THREADS = 256;
 constexpr int GEMM_T_ABUF = 3;     // A tiles in flight
-
-template <int N>
-constexpr int gemm_tma_smem_bytes()
-{
-    return N * GEMM_T_KMAX * 2 + GEMM_T_ABUF * GEMM_BM * GEMM_T_KMAX * 2 + GEMM_BM * N * 2 * 2 + 128 + 1024;
-}
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t mbar)
 {
@@ -334,33 +327,71 @@ __device__ __forceinline__ void tma_tile(uint32_t dst, const CUtensorMap *map, i
     for (int j = 0; j < KP / 8; ++j) tma_load_2d(dst + j * ROWS * 16, map, 8 * j, row0, mbar);
 }
 
-// The persistent form (K <= GEMM_T_KMAX, no K split): CTA b takes the 128-row tiles
-// b, b + gridDim.x, ...  Thread 0 issues the tensor copies and the MMAs and waits on
-// their barriers (bounded); the 8 warps share the epilogue (warp w: TMEM lanes
-// 32 (w % 4) .., half (w / 4) of the columns).  A tensor map row box of 128 rows (A)
-// and N rows (B), inner box 8 elements.
+// The persistent form (K <= GEMM_T_KMAX, no K split): every training GEMM over the
+// rows.  Warp 0 (one lane) issues the tensor copies of B once and of the A tiles
+// GEMM_T_ABUF deep; warp 1 (one lane) issues each tile's MMAs into one of two TMEM
+// accumulators; warps 2..9 drain an accumulator (each its 32 TMEM lanes and half the
+// columns), release it to the MMA warp and stage the bf16 results in shared memory
+// (row-major with the 16-byte chunks of a row XOR-permuted, and transposed), from where
+// both outputs leave as coalesced 16-byte stores.  So the MMAs of tile i + 1 and the
+// copies of the tiles after it run while tile i is stored.  mbarriers: full/empty per A
+// buffer (copy -> MMA -> copy), tfull/tempty per accumulator (MMA -> epilogue -> MMA);
+// every wait is bounded, and the epilogue warps decide together (after a named barrier)
+// whether to stop.
+constexpr int GEMM_WS_EPI_WARPS = 8;
+constexpr int GEMM_WS_THREADS = 64 + 32 * GEMM_WS_EPI_WARPS;
+
 template <int N>
-__global__ void __launch_bounds__(GEMM_T_THREADS, 1) k_gemm_bf16_tma(const __grid_constant__ CUtensorMap tmA,
-                                                        const __grid_constant__ CUtensorMap tmB, int M, int K,
-                                                        GemmEpi ep)
+constexpr int gemm_ws_smem_bytes()
 {
-    constexpr int TMEM_COLS = N < 32 ? 32 : N;
+    return N * GEMM_T_KMAX * 2 + GEMM_T_ABUF * GEMM_BM * GEMM_T_KMAX * 2 + GEMM_BM * N * 2 * 2 + 256 + 1024;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void epi_bar()
+{
+    asm volatile("bar.sync 1, %0;" ::"r"(32 * GEMM_WS_EPI_WARPS) : "memory");
+}
+
+template <int N>
+__global__ void __launch_bounds__(GEMM_WS_THREADS, 1) k_gemm_bf16_ws(const __grid_constant__ CUtensorMap tmA,
+                                                                   const __grid_constant__ CUtensorMap tmB, int M,
+                                                                   int K, GemmEpi ep)
+{
+    constexpr int ACC = N < 32 ? 32 : N;  // TMEM columns of one accumulator
+    constexpr int TMEM_COLS = 2 * ACC;
+    constexpr int A_BUF = GEMM_BM * GEMM_T_KMAX * 2;
+    constexpr int NB = GEMM_T_ABUF;
     extern __shared__ uint8_t gemm_smem_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(gemm_smem_raw) + 1023) & ~uintptr_t(1023));
     const int KP = (K + 15) / 16 * 16;
-    constexpr int A_BUF = GEMM_BM * GEMM_T_KMAX * 2;
-    uint8_t *sb = sm;                                  // N x KP
-    uint8_t *sa = sb + N * GEMM_T_KMAX * 2;                 // GEMM_T_ABUF x 128 x KP
-    uint8_t *ss = sa + GEMM_T_ABUF * A_BUF;                 // 128 rows x N bf16, 16-byte chunks XOR-swizzled
-    uint8_t *st = ss + GEMM_BM * N * 2;                // N x 128 bf16 (transposed tile)
-    unsigned long long *mbar = reinterpret_cast<unsigned long long *>(st + GEMM_BM * N * 2);  // [0..2] loads, [3] mma
-    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(mbar + 4);
+    uint8_t *sb = sm;
+    uint8_t *sa = sb + N * GEMM_T_KMAX * 2;
+    uint8_t *ss = sa + NB * A_BUF;
+    uint8_t *st = ss + GEMM_BM * N * 2;
+    unsigned long long *full = reinterpret_cast<unsigned long long *>(st + GEMM_BM * N * 2);
+    unsigned long long *empty = full + NB, *tfull = empty + NB, *tempty = tfull + 2, *bfull = tempty + 2;
+    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(bfull + 1);
     int *s_fail = reinterpret_cast<int *>(s_tmem + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntiles = (M + GEMM_BM - 1) / GEMM_BM;
     if (tid == 0) {
         *s_fail = 0;
-        for (int q = 0; q < 4; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[q])) : "memory");
+        for (int q = 0; q < NB; ++q) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[q])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[q])) : "memory");
+        }
+        for (int q = 0; q < 2; ++q) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&tfull[q])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&tempty[q])),
+                         "r"(GEMM_WS_EPI_WARPS)
+                         : "memory");
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bfull)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -373,169 +404,182 @@ __global__ void __launch_bounds__(GEMM_T_THREADS, 1) k_gemm_bf16_tma(const __gri
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *s_tmem;
-    // prologue: B with the first A tile (barrier 0), then the next two A tiles
-    int issued = 0;  // A tiles whose loads thread 0 has issued (sequence numbers 0 .. issued - 1)
-    if (tid == 0) {
-        for (int q = 0; q < GEMM_T_ABUF - 1; ++q) {
-            const int t = blockIdx.x + q * gridDim.x;
-            if (t >= ntiles) break;
-            if (q == 0) tma_tile<N, false>(smem_u32(sb), &tmB, 0, KP, smem_u32(&mbar[0]));
-            ++issued;
-            tma_tile<GEMM_BM, true>(smem_u32(sa + q * A_BUF), &tmA, t * GEMM_BM, KP, smem_u32(&mbar[q]));
-        }
-    }
-    const uint32_t idesc = umma_idesc_bf16(GEMM_BM, N);
-    uint32_t lphase[GEMM_T_ABUF] = {0u, 0u, 0u}, mphase = 0u;
-    int i = 0;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
-        const int b = i % GEMM_T_ABUF;
-        if (tid == 0) {
-            // refill the buffer the previous tile used (its MMAs are complete)
-            const int tn = t + (GEMM_T_ABUF - 1) * gridDim.x;
-            if (tn < ntiles) {
-                const int bn = (i + GEMM_T_ABUF - 1) % GEMM_T_ABUF;
-                tma_tile<GEMM_BM, true>(smem_u32(sa + bn * A_BUF), &tmA, tn * GEMM_BM, KP, smem_u32(&mbar[bn]));
-                ++issued;
+    volatile int *vfail = s_fail;
+
+    if (warp == 0) {
+        if (lane == 0 && (int)blockIdx.x < ntiles) {
+            tma_tile<N, true>(smem_u32(sb), &tmB, 0, KP, smem_u32(bfull));
+            int issued = 0;
+            for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++issued) {
+                const int b = issued % NB;
+                if (issued >= NB && !mbar_wait(smem_u32(&empty[b]), (uint32_t)((issued / NB - 1) & 1))) {
+                    *vfail = 1;
+                    break;
+                }
+                if (*vfail) break;
+                tma_tile<GEMM_BM, true>(smem_u32(sa + b * A_BUF), &tmA, t * GEMM_BM, KP, smem_u32(&full[b]));
             }
-            bool ok = mbar_wait(smem_u32(&mbar[b]), lphase[b]);
-            if (ok) {
+            // copies still in flight must land before the shared memory is released (only
+            // after a failure can one be unconsumed)
+            mbar_wait(smem_u32(bfull), 0u);
+            for (int q = issued - NB < 0 ? 0 : issued - NB; q < issued; ++q)
+                mbar_wait(smem_u32(&full[q % NB]), (uint32_t)((q / NB) & 1));
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && (int)blockIdx.x < ntiles) {
+            const uint32_t idesc = umma_idesc_bf16(GEMM_BM, N);
+            bool ok = mbar_wait(smem_u32(bfull), 0u);
+            int i = 0;
+            for (int t = blockIdx.x; ok && t < ntiles; t += gridDim.x, ++i) {
+                const int b = i % NB, acc = i & 1;
+                ok = mbar_wait(smem_u32(&full[b]), (uint32_t)((i / NB) & 1));
+                if (ok && i >= 2) ok = mbar_wait(smem_u32(&tempty[acc]), (uint32_t)((i / 2 - 1) & 1));
+                if (!ok || *vfail) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t a0 = smem_u32(sa + b * A_BUF), b0 = smem_u32(sb);
+                const uint32_t d = tmem + (uint32_t)(acc * ACC);
                 for (int k16 = 0; k16 < KP / 16; ++k16) {
                     const uint64_t ad = umma_desc(a0 + k16 * 2 * GEMM_BM * 16, GEMM_BM * 16, 128);
                     const uint64_t bd = umma_desc(b0 + k16 * 2 * N * 16, N * 16, 128);
-                    const uint32_t acc = k16 > 0 ? 1u : 0u;
+                    const uint32_t accum = k16 > 0 ? 1u : 0u;
                     asm volatile(
                         "{\n\t.reg .pred p;\n\t"
                         "setp.ne.b32 p, %4, 0;\n\t"
-                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
-                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
                         : "memory");
                 }
+                // both barriers track these MMAs: the A buffer and the accumulator
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                 smem_u32(&mbar[3]))
+                                 smem_u32(&empty[b]))
                              : "memory");
-                ok = mbar_wait(smem_u32(&mbar[3]), mphase);
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(&tfull[acc]))
+                             : "memory");
             }
-            if (!ok) *s_fail = 1;
+            if (!ok) *vfail = 1;
         }
-        lphase[b] ^= 1u;
-        mphase ^= 1u;
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (*reinterpret_cast<volatile int *>(s_fail)) break;
-        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31, columns [half * N / 2, + N / 2)
-        const int rl = (warp & 3) * 32 + lane;  // row within the tile
-        const int row = t * GEMM_BM + rl;
-        const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    } else {
+        const int e = tid - 64;  // epilogue thread 0 .. 255
+        const int lg = warp & 3, half = (warp - 2) >> 2;
+        const int rl = lg * 32 + lane;  // row within the tile
         constexpr int CH = N >= 64 ? N / 2 : N;  // columns per warp
-        const int cbeg = N >= 64 ? (warp >> 2) * CH : 0;
-        if (N >= 64 || warp < 4) {
+        const bool active = N >= 64 || half == 0;
+        int i = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+            const int acc = i & 1;
+            if (lane == 0 && !mbar_wait(smem_u32(&tfull[acc]), (uint32_t)((i / 2) & 1))) *vfail = 1;
+            epi_bar();
+            if (*vfail) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int row = t * GEMM_BM + rl;
+            const uint32_t taddr = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(acc * ACC);
+            if (active) {
 #pragma unroll
-            for (int cc = 0; cc < CH; cc += 32) {
-                const int c0 = cbeg + cc;
-                uint32_t r[32];
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                    "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                      "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                      "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-                      "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                    : "r"(taddr + (uint32_t)c0));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                float v[32];
+                for (int cc = 0; cc < CH; cc += 32) {
+                    const int c0 = half * CH + cc;
+                    uint32_t r[32];
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+                          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+                          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                        : "r"(taddr + (uint32_t)c0));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    float v[32];
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    v[j] = __uint_as_float(r[j]);
-                    if (ep.bias) v[j] += __ldg(ep.bias + c0 + j);
-                    if (ep.relu) v[j] = fmaxf(v[j], 0.0f);
-                }
-                const long long rbase = (long long)row * N + c0;
-                if (ep.mask && row < M) {
+                    for (int j = 0; j < 32; ++j) {
+                        v[j] = __uint_as_float(r[j]);
+                        if (ep.bias) v[j] += __ldg(ep.bias + c0 + j);
+                        if (ep.relu) v[j] = fmaxf(v[j], 0.0f);
+                    }
+                    const long long rbase = (long long)row * N + c0;
+                    if (ep.mask && row < M) {
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const uint4 mv = reinterpret_cast<const uint4 *>(ep.mask + rbase)[q];
-                        const __nv_bfloat162 *mh = reinterpret_cast<const __nv_bfloat162 *>(&mv);
+                        for (int q = 0; q < 4; ++q) {
+                            const uint4 mv = reinterpret_cast<const uint4 *>(ep.mask + rbase)[q];
+                            const __nv_bfloat162 *mh = reinterpret_cast<const __nv_bfloat162 *>(&mv);
 #pragma unroll
-                        for (int h = 0; h < 4; ++h) {
-                            const float2 m2 = __bfloat1622float2(mh[h]);
-                            if (!(m2.x > 0.0f)) v[q * 8 + 2 * h] = 0.0f;
-                            if (!(m2.y > 0.0f)) v[q * 8 + 2 * h + 1] = 0.0f;
+                            for (int h = 0; h < 4; ++h) {
+                                const float2 m2 = __bfloat1622float2(mh[h]);
+                                if (!(m2.x > 0.0f)) v[q * 8 + 2 * h] = 0.0f;
+                                if (!(m2.y > 0.0f)) v[q * 8 + 2 * h + 1] = 0.0f;
+                            }
                         }
                     }
-                }
-                if (ep.out_f32 && row < M) {
+                    if (ep.out_f32 && row < M) {
 #pragma unroll
-                    for (int q = 0; q < 8; ++q)
-                        reinterpret_cast<float4 *>(ep.out_f32 + rbase)[q] =
-                            make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-                }
-                if (ep.out_bf16) {
+                        for (int q = 0; q < 8; ++q)
+                            reinterpret_cast<float4 *>(ep.out_f32 + rbase)[q] =
+                                make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                    }
+                    if (ep.out_bf16) {
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        uint32_t w[4];
+                        for (int q = 0; q < 4; ++q) {
+                            uint32_t w[4];
 #pragma unroll
-                        for (int h = 0; h < 4; ++h) {
-                            __nv_bfloat162 p2 = __floats2bfloat162_rn(v[q * 8 + 2 * h], v[q * 8 + 2 * h + 1]);
-                            w[h] = *reinterpret_cast<uint32_t *>(&p2);
+                            for (int h = 0; h < 4; ++h) {
+                                __nv_bfloat162 p2 = __floats2bfloat162_rn(v[q * 8 + 2 * h], v[q * 8 + 2 * h + 1]);
+                                w[h] = *reinterpret_cast<uint32_t *>(&p2);
+                            }
+                            const int chunk = (c0 / 8 + q) ^ (rl & (N * 2 / 16 - 1));
+                            *reinterpret_cast<uint4 *>(ss + rl * (N * 2) + chunk * 16) =
+                                make_uint4(w[0], w[1], w[2], w[3]);
                         }
-                        const int chunk = (c0 / 8 + q) ^ (rl & (N * 2 / 16 - 1));  // 16-byte chunk within the row
-                        *reinterpret_cast<uint4 *>(ss + rl * (N * 2) + chunk * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+                    }
+                    if (ep.out_bf16_t) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            *reinterpret_cast<__nv_bfloat16 *>(st + (c0 + j) * (GEMM_BM * 2) + rl * 2) =
+                                __float2bfloat16_rn(v[j]);
                     }
                 }
-                if (ep.out_bf16_t) {
-#pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        *reinterpret_cast<__nv_bfloat16 *>(st + (c0 + j) * (GEMM_BM * 2) + rl * 2) = __float2bfloat16_rn(v[j]);
+            }
+            // the accumulator is in registers and shared memory: hand it back to the MMA warp
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&tempty[acc]));
+            epi_bar();
+            const int row0 = t * GEMM_BM;
+            if (ep.out_bf16) {
+                constexpr int CPR = N * 2 / 16;  // 16-byte chunks per row
+                for (int id = e; id < GEMM_BM * CPR; id += 32 * GEMM_WS_EPI_WARPS) {
+                    const int rr = id / CPR, q = id % CPR;
+                    if (row0 + rr < M) {
+                        const uint4 val = *reinterpret_cast<const uint4 *>(ss + rr * (N * 2) + (q ^ (rr & (CPR - 1))) * 16);
+                        *reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(ep.out_bf16) + ((long long)(row0 + rr) * N) * 2 +
+                                                   q * 16) = val;
+                    }
                 }
             }
-        }
-        __syncthreads();
-        // coalesced stores of the staged tile
-        const int row0 = t * GEMM_BM;
-        if (ep.out_bf16) {
-            constexpr int CPR = N * 2 / 16;  // chunks per row
-            for (int id = tid; id < GEMM_BM * CPR; id += GEMM_T_THREADS) {
-                const int rr = id / CPR, q = id % CPR;
-                if (row0 + rr < M) {
-                    const uint4 val = *reinterpret_cast<const uint4 *>(ss + rr * (N * 2) + (q ^ (rr & (CPR - 1))) * 16);
-                    *reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(ep.out_bf16) + ((long long)(row0 + rr) * N) * 2 + q * 16) = val;
+            if (ep.out_bf16_t) {
+                const bool whole = row0 + GEMM_BM <= M && (ep.ldt % 8) == 0;
+                for (int id = e; id < N * (GEMM_BM / 8); id += 32 * GEMM_WS_EPI_WARPS) {
+                    const int c = id / (GEMM_BM / 8), q = id % (GEMM_BM / 8);
+                    const uint8_t *srcp = st + c * (GEMM_BM * 2) + q * 16;
+                    __nv_bfloat16 *dst = ep.out_bf16_t + (long long)c * ep.ldt + row0 + q * 8;
+                    if (whole) {
+                        *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(srcp);
+                    } else {
+                        for (int x = 0; x < 8; ++x)
+                            if (row0 + q * 8 + x < M) dst[x] = reinterpret_cast<const __nv_bfloat16 *>(srcp)[x];
+                    }
                 }
             }
+            epi_bar();  // the staging tiles are free for the next tile
         }
-        if (ep.out_bf16_t) {
-            const bool full = row0 + GEMM_BM <= M && (ep.ldt % 8) == 0;
-            for (int id = tid; id < N * (GEMM_BM / 8); id += GEMM_T_THREADS) {
-                const int c = id / (GEMM_BM / 8), q = id % (GEMM_BM / 8);
-                const uint8_t *srcp = st + c * (GEMM_BM * 2) + q * 16;
-                __nv_bfloat16 *dst = ep.out_bf16_t + (long long)c * ep.ldt + row0 + q * 8;
-                if (full) {
-                    *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(srcp);
-                } else {
-                    for (int e = 0; e < 8; ++e)
-                        if (row0 + q * 8 + e < M) dst[e] = reinterpret_cast<const __nv_bfloat16 *>(srcp)[e];
-                }
-            }
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();  // staging buffers and the accumulator are free for the next tile
     }
-    // drain (only after a failed wait): loads issued but not consumed must land before
-    // the shared memory is released
-    if (tid == 0)
-        for (int s = i; s < issued; ++s) mbar_wait(smem_u32(&mbar[s % GEMM_T_ABUF]), (uint32_t)((s / GEMM_T_ABUF) & 1));
-    if (tid == 0 && *s_fail && ep.error) atomicExch(ep.error, 1);
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
+    if (tid == 0 && *vfail && ep.error) atomicExch(ep.error, 1);
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
     }
 }
-
 
 // Split-K form for the weight gradients (M <= 128 rows, K = the training rows split in
 // k_per_split slices over blockIdx.y): 64-wide K chunks of A (128 x 64) and B (N x 64)

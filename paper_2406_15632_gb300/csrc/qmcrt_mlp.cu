@@ -1,7 +1,8 @@
 // qmcrt_mlp.cu -- launchers of the tensor-core GEMM (qmcrt_gemm.cuh) used by the
-// learned proposal: the persistent tensor-copy form for K <= 128 without a K split, the
-// tensor-copy split-K form for the weight gradients (one 128-row tile, FP32 atomics), the
-// streaming form otherwise (and wherever a tensor map cannot be made).
+// learned proposal: the persistent warp-specialised tensor-copy form for K <= 128 without
+// a K split, the tensor-copy split-K form for the weight gradients (one 128-row tile,
+// FP32 vector reductions), the streaming form otherwise (and wherever a tensor map cannot
+// be made).
 #include <cudaTypedefs.h>
 
 #include "qmcrt.h"
@@ -49,9 +50,9 @@ template <int N>
 static bool launch_tma(const __nv_bfloat16 *A, const __nv_bfloat16 *B, int M, int K, const GemmEpi &ep,
                        cudaStream_t s, cudaError_t &err)
 {
-    constexpr int smem = gemm_tma_smem_bytes<N>();
+    constexpr int smem = gemm_ws_smem_bytes<N>();
     static const cudaError_t attr =
-        cudaFuncSetAttribute(k_gemm_bf16_tma<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_gemm_bf16_ws<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (attr != cudaSuccess) return false;
     CUtensorMap ma, mb;
     if (!make_tmap(&ma, A, K, M, GEMM_BM) || !make_tmap(&mb, B, K, N, N)) return false;
@@ -60,7 +61,7 @@ static bool launch_tma(const __nv_bfloat16 *A, const __nv_bfloat16 *B, int M, in
                                                   cudaSuccess)
         return false;
     const int ntiles = (M + GEMM_BM - 1) / GEMM_BM;
-    k_gemm_bf16_tma<N><<<ntiles < sms ? ntiles : sms, GEMM_T_THREADS, smem, s>>>(ma, mb, M, K, ep);
+    k_gemm_bf16_ws<N><<<ntiles < sms ? ntiles : sms, GEMM_WS_THREADS, smem, s>>>(ma, mb, M, K, ep);
     err = cudaGetLastError();
     return true;
 }
