@@ -58,7 +58,7 @@ static_assert(sizeof(Rec<float>) == 64 && sizeof(Rec<double>) == 128, "record si
 template <class T>
 struct WaveWork {
     Rec<T> *q[2];       // [cap] each: order k reads q[(k + 1) & 1] and appends to q[k & 1]
-    uint32_t *count;    // [2] packets of this order, packets appended for the next
+    uint32_t *count;    // [3] packets of this order, packets appended for the next, chunk counter
     uint32_t *keys;     // [cap] bucket of each appended record
     uint32_t *perm;     // [cap] record indices of the queue being read, in bucket order
     uint32_t *hist;     // [WV_BUCKETS] histogram of the appended records, then bucket cursors
@@ -277,15 +277,25 @@ template <class T>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_wave_order(const __grid_constant__ TraceP<T> P, int k, WaveWork<T> W)
 {
     const uint32_t n = W.count[0];
-    const uint32_t stride = gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
     Rec<T> *const src = (k & 1) ? W.q[0] : W.q[1];  // selects, not an indexed parameter array
     Rec<T> *const dst = (k & 1) ? W.q[1] : W.q[0];
-    for (uint32_t q0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); q0 < n; q0 += stride) {  // uniform per warp
-        const uint32_t q = q0 + (threadIdx.x & 31u);
+    // warps claim 32-packet chunks from a counter, one chunk ahead: walk lengths differ
+    // from chunk to chunk, and a warp that finishes early takes the next one (n <= 2^31,
+    // so the counter, which passes n by at most two chunks per warp, cannot wrap)
+    auto claim = [&]() {
+        uint32_t c = 0;
+        if (lane == 0) c = atomicAdd(W.count + 2, 32u);
+        return __shfl_sync(FULL_MASK, c, 0);
+    };
+    uint32_t q0 = claim();
+    while (q0 < n) {  // uniform per warp
+        const uint32_t q1 = claim();
+        const uint32_t q = q0 + lane;
         const bool live = q < n;
         Rec<T> r;
         if (live) {
-            const uint32_t qn = q + stride;
+            const uint32_t qn = q1 + lane;
             const uint32_t pn = qn < n ? W.perm[qn] : 0u;
             copy_rec(&r, src + W.perm[q]);
             // the record this lane gathers next: into L2 while this one is traced
@@ -300,6 +310,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_wave_order(cons
         const bool on = run_order(P, k, i, live, wd, r.p);
         append(P, W, dst, on, r.p, r.j);
         if (live && !on && P.train_log) write_log(P, i, r.j, r.p);
+        q0 = q1;
     }
 }
 
@@ -315,7 +326,7 @@ WaveWork<T> carve(void *ws, uint64_t cap)
     };
     W.q[0] = (Rec<T> *)take(cap * sizeof(Rec<T>));
     W.q[1] = (Rec<T> *)take(cap * sizeof(Rec<T>));
-    W.count = (uint32_t *)take(2 * 4);
+    W.count = (uint32_t *)take(3 * 4);
     W.keys = (uint32_t *)take(cap * 4);
     W.perm = (uint32_t *)take(cap * 4);
     W.hist = (uint32_t *)take(WV_BUCKETS * 4);
@@ -327,7 +338,7 @@ cudaError_t launch_wave(const TraceP<T> &P, void *ws, uint64_t cap, int sms, cud
 {
     if (P.count == 0) return cudaSuccess;
     WaveWork<T> W = carve<T>(ws, cap);
-    cudaError_t e = cudaMemsetAsync(W.count, 0, 2 * sizeof(uint32_t), s);
+    cudaError_t e = cudaMemsetAsync(W.count, 0, 3 * sizeof(uint32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(W.hist, 0, WV_BUCKETS * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     const uint64_t threads = (P.ord.threads + 31) & ~31ull;
@@ -341,7 +352,7 @@ cudaError_t launch_wave(const TraceP<T> &P, void *ws, uint64_t cap, int sms, cud
         k_wave_scatter<T><<<grid, 256, 0, s>>>(W);
         if ((e = cudaMemcpyAsync(W.count, W.count + 1, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
             return e;
-        if ((e = cudaMemsetAsync(W.count + 1, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(W.count + 1, 0, 2 * sizeof(uint32_t), s)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(W.hist, 0, WV_BUCKETS * sizeof(uint32_t), s)) != cudaSuccess) return e;
         k_wave_order<T><<<grid, 256, 0, s>>>(P, k, W);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -355,7 +366,7 @@ uint64_t wavefront_workspace_bytes(uint64_t cap, int precision)
 {
     const uint64_t rec = precision == QMCRT_PREC_F64 ? sizeof(Rec<double>) : sizeof(Rec<float>);
     auto pad = [](uint64_t b) { return (b + 255) & ~255ull; };
-    return 2 * pad(cap * rec) + pad(8) + 2 * pad(cap * 4) + pad(WV_BUCKETS * 4);
+    return 2 * pad(cap * rec) + pad(12) + 2 * pad(cap * 4) + pad(WV_BUCKETS * 4);
 }
 
 cudaError_t launch_trace_wavefront_f32(const TraceP<float> &p, void *ws, uint64_t cap, int sms, cudaStream_t s)
