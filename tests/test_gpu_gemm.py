@@ -29,7 +29,10 @@ def _check(got, ref, K):
     assert np.abs(got - ref).max() <= tol * 8, (np.abs(got - ref).max(), tol)
 
 
-@pytest.mark.parametrize("M,N,K", [(128, 128, 32), (300, 128, 96), (77, 32, 256), (1000, 64, 1024), (5, 32, 64)])
+# K <= 128 runs the persistent warp-specialised form (several tiles per CTA once M passes
+# 152 x 128 rows, both TMEM accumulators in turn); larger K the streaming form
+@pytest.mark.parametrize("M,N,K", [(128, 128, 32), (300, 128, 96), (77, 32, 256), (1000, 64, 1024), (5, 32, 64),
+                                   (1000, 64, 128), (129, 128, 128), (40000, 128, 128), (40001, 32, 32)])
 def test_gemm_plain(Q, M, N, K):
     import torch
 
@@ -43,16 +46,19 @@ def test_gemm_plain(Q, M, N, K):
     assert err.item() == 0
 
 
-def test_gemm_epilogues(Q):
+@pytest.mark.parametrize("M,ldt", [(257, 320), (40000, 40003)])
+def test_gemm_epilogues(Q, M, ldt):
+    """Bias, ReLU, mask and all three outputs; the transposed copy with a row length that
+    is and is not a multiple of 8 (vector and element stores)."""
     import torch
 
-    M, N, K = 257, 128, 128
+    N, K = 128, 128
     A, B = _bf16((M, K), 3), _bf16((N, K), 4)
     bias = torch.randn(N, generator=torch.Generator().manual_seed(5))
     mask = _bf16((M, N), 6)
     o32 = torch.zeros((M, N), dtype=torch.float32, device="cuda")
     o16 = torch.zeros((M, N), dtype=torch.bfloat16, device="cuda")
-    ot = torch.zeros((N, 320), dtype=torch.bfloat16, device="cuda")
+    ot = torch.zeros((N, ldt), dtype=torch.bfloat16, device="cuda")
     Q.gemm(A.cuda(), B.cuda(), bias=bias.cuda(), relu=True, mask=mask.cuda(), out_f32=o32, out_bf16=o16, out_bf16_t=ot)
     torch.cuda.synchronize()
     ref = A.double().numpy() @ B.double().numpy().T + bias.double().numpy()[None, :]
@@ -63,13 +69,16 @@ def test_gemm_epilogues(Q):
     assert torch.all(ot[:, M:] == 0)
 
 
-def test_gemm_split_k_adds_atomically(Q):
+@pytest.mark.parametrize("M,N,K,splits", [(128, 32, 4096, 8), (32, 128, 4096, 8), (128, 128, 65536, 128),
+                                           (100, 64, 3000 // 32 * 32, 7)])
+def test_gemm_split_k_adds_atomically(Q, M, N, K, splits):
+    """The weight-gradient form: K split over CTAs, partial tiles added into out_f32
+    (fewer rows than a tile, and slices that do not divide K, included)."""
     import torch
 
-    M, N, K = 128, 32, 4096
     A, B = _bf16((M, K), 7), _bf16((N, K), 8)
     out = torch.ones((M, N), dtype=torch.float32, device="cuda")
-    Q.gemm(A.cuda(), B.cuda(), out_f32=out, k_splits=8)
+    Q.gemm(A.cuda(), B.cuda(), out_f32=out, k_splits=splits)
     torch.cuda.synchronize()
     ref = 1.0 + A.double().numpy() @ B.double().numpy().T
     _check(out.cpu().numpy(), ref, K)
