@@ -267,9 +267,10 @@ __device__ __forceinline__ bool packet_index(const OrderP &O, uint64_t first, ui
     for (int j = 0; j < O.bits; ++j) g ^= ((box >> j) & 1u) ? O.rm[j] : 0u;
     for (int j = 0; j < O.tt; ++j) g ^= ((tl >> j) & 1u) ? O.k[j] : 0u;
     const bool nied = O.net == 2;
+    const bool extra = O.nb[3] + O.nb[4] > 0;  // uniform: the order also groups xdim[0], xdim[1]
     // The block start is a multiple of 2^m, so its digit vector (Gray code for Sobol)
     // has set bits only from m - 1 up: XOR the columns of those bits alone.
-    uint32_t b0 = 0, b1 = 0, b2 = 0;
+    uint32_t b0 = 0, b1 = 0, b2 = 0, b3 = 0, b4 = 0;
     const uint32_t b32 = (uint32_t)base;
     for (uint32_t gb = nied ? b32 : b32 ^ (b32 >> 1); gb; gb &= gb - 1u) {
         const int k = __ffs(gb) - 1;
@@ -277,13 +278,24 @@ __device__ __forceinline__ bool packet_index(const OrderP &O, uint64_t first, ui
             b0 ^= __ldg(&d_nied_v[0][k]);
             b1 ^= __ldg(&d_nied_v[1][k]);
             b2 ^= __ldg(&d_nied_v[2][k]);
+            if (extra) {
+                b3 ^= __ldg(&d_nied_v[O.xdim[0]][k]);
+                b4 ^= __ldg(&d_nied_v[O.xdim[1]][k]);
+            }
         } else {
             b0 ^= c_sobol_v[0][k];
             b1 ^= c_sobol_v[1][k];
             b2 ^= c_sobol_v[2][k];
+            if (extra) {
+                b3 ^= c_sobol_v[O.xdim[0]][k];
+                b4 ^= c_sobol_v[O.xdim[1]][k];
+            }
         }
     }
-    const uint32_t y = (lead_bits(b0, O.a) << (O.b + O.c)) | (lead_bits(b1, O.b) << O.c) | lead_bits(b2, O.c);
+    // y: the leading bits of coordinates 2, 1, 0, xdim[0], xdim[1], least significant first
+    const int s1 = O.nb[2], s0 = s1 + O.nb[1], s3 = s0 + O.nb[0], s4 = s3 + O.nb[3];
+    const uint32_t y = lead_bits(b2, O.nb[2]) | (lead_bits(b1, O.nb[1]) << s1) | (lead_bits(b0, O.nb[0]) << s0) |
+                       (lead_bits(b3, O.nb[3]) << s3) | (lead_bits(b4, O.nb[4]) << s4);
     for (int j = 0; j < O.bits; ++j) g ^= ((y >> j) & 1u) ? O.ry[j] : 0u;
     i = base + (nied ? g : gray_inverse(g));
     return i >= first && i < first + count;

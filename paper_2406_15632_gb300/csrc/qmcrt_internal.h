@@ -81,15 +81,18 @@ struct AccumP {
 // start in nearly the same direction and scatter at nearly the same depth.
 constexpr int NET_MAX_M = 28;
 
+constexpr int NET_MAX_TT = 6;  // points per elementary box up to 2^6
+
 struct OrderP {
     int net;            // 0 linear, 1 net order of Sobol (Gray code), 2 of Niederreiter (natural order)
     int m, bits, tt;    // block 2^m, bits = m - tt Morton bits, tt kernel bits
-    int a, b, c;        // leading bits taken from coordinates 0, 1, 2
+    int nb[5];          // leading bits taken from coordinates 0, 1, 2, xdim[0], xdim[1]
+    int xdim[2];        // the two further coordinates ordered (a finite star's emission point)
     uint64_t block0;    // first block index
     uint64_t threads;   // threads to launch (count when linear)
     uint32_t rm[NET_MAX_M];  // R column for Morton bit j of the thread's box index
     uint32_t ry[NET_MAX_M];  // R column for bit j of y
-    uint32_t k[4];           // kernel basis of L
+    uint32_t k[NET_MAX_TT];  // kernel basis of L
 };
 
 // Net-order tables for every block size a batch may use (m = NET_MIN_M .. NET_MAX_M).
