@@ -174,6 +174,10 @@ typedef struct qmcrt_trace_opts {
  * star blocks its path, and is added to the pixel under its projection.
  * Coordinates: point source (u, v, w) = dims (0, 1, 2); sphere source dims 0..4.
  * pts->dims must be >= the coordinates used; pts->format is ignored.
+ * Speed: digital base-2 point sets are traced in net order, one aligned block of 2^m
+ * indices at a time (2^m <= count); a range that starts or ends inside such a block
+ * launches the whole block, whose threads outside the range only compute their index.
+ * first_index a multiple of a power-of-two count traces no such threads.
  * d_log (optional, NULL to skip): device double [count][9] = scattering x, y, z,
  * peel-off I, Q, U, sky x, y, status (0 contributed, 1 tau_1 < tau_min, 2 occulted).
  * Errors: INVALID_ARG (NULL descriptors, bad sizes or enums, |g| >= 1, albedo outside

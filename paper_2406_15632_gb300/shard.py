@@ -10,10 +10,12 @@ from __future__ import annotations
 
 def step_range(step: int, rank: int, world: int, n: int, n_blocks: int) -> int:
     """First point index of the n-packet block traced by `rank` at `step`: blocks of n
-    consecutive indices starting at 1, assigned round-robin over (step, rank), wrapping
-    after n_blocks blocks so every index stays below 2^32."""
+    consecutive indices starting at multiples of n from n on (index 0 is never used), so
+    a power-of-two n is one whole net block of the sequence; assigned round-robin over
+    (step, rank), wrapping after n_blocks blocks so every index stays below 2^32 (n_blocks
+    at most 2^32 / n - 1)."""
     b = (step * world + rank) % n_blocks
-    return 1 + b * n
+    return (1 + b) * n
 
 
 def split_range(first: int, count: int, rank: int, world: int) -> tuple[int, int]:
