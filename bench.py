@@ -348,7 +348,7 @@ def _reference_image(Q, prob, grid, render_log2, seeds, accum):
         n = 1 << render_log2
         fb = Q.default_frac_bits(sc.prob, n) if accum == "i64" else 0
         buf = sc.accum_buffer(accum)
-        sc.trace(1, n, buf, accum=accum, frac_bits=fb)
+        sc.trace(n, n, buf, accum=accum, frac_bits=fb)  # points n .. 2n - 1: one whole net block
         imgs.append(sc.reduce(buf, 1.0 / n, accum=accum, frac_bits=fb)[0, 0].clone())
     stack = torch.stack(imgs)
     ref = stack.mean(0)
@@ -382,7 +382,7 @@ def _tte_summary(arms, targets, overhead_ms=None):
     return out
 
 
-def run_time_to_error_learned(ladder=(20, 22, 24, 26, 28), ref_log2=28, ref_seeds=(101, 102, 103, 104),
+def run_time_to_error_learned(ladder=(20, 22, 24, 26, 28), ref_log2=28, ref_seeds=tuple(range(101, 109)),
                               n_log_log2=22, epochs=2, batch_log2=16, lr=1e-2, mix=0.1, weight="l2"):
     """Clumpy envelope (128^3, total radial tau 5, 20 orders, roulette at 1e-4, 512x512
     I/Q/U): wall time to a fixed RMS error of the I image for plain QMC (Sobol), the
