@@ -45,6 +45,7 @@ def main(argv=None) -> int:
                                      "batch"])
     ap.add_argument("--log2-n", type=int, default=20)
     ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--instances", type=int, default=0, help="batch: the first N instances only (0: all 256)")
     a = ap.parse_args(argv)
     Q.load()
     n = 1 << a.log2_n
@@ -83,7 +84,10 @@ def main(argv=None) -> int:
         ms = _cuda_ms(lambda: W.train(xs, ws, epochs=1, batch=min(n, 1 << 16), lr=1e-3), a.repeat)
     else:
         prob = S.finite_star_disk_problem(n=256)
-        B = Q.Batch(prob, S.batched_instances(), chunk_log2=24, block_size=256, ctas_per_sm=0, packets_per_thread=1)
+        inst = S.batched_instances()
+        if a.instances > 0:
+            inst = inst[: a.instances]
+        B = Q.Batch(prob, inst, chunk_log2=24, block_size=256, ctas_per_sm=0, packets_per_thread=1)
         B.capture()
         ms = _cuda_ms(B.replay, a.repeat)
     print(f"{a.name} log2_n={a.log2_n}: {ms:.3f} ms per run ({time.perf_counter() - t0:.1f} s wall)")
