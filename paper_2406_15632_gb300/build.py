@@ -118,6 +118,25 @@ def primes(n: int = MAX_DIMS) -> list[int]:
     return out
 
 
+SOBOL_BYTE_DIMS = 8
+
+
+def sobol_byte_table(V: list[list[int]], dims: int = SOBOL_BYTE_DIMS) -> list[list[list[int]]]:
+    """T[d][b][v]: XOR of the direction numbers V[d][8 b + k] over the set bits k of the
+    byte v, so that a coordinate is the XOR of four lookups, one per byte of the Gray code."""
+    out = []
+    for d in range(dims):
+        per = []
+        for b in range(4):
+            row = [0] * 256
+            for v in range(1, 256):
+                low = v & -v
+                row[v] = row[v ^ low] ^ V[d][8 * b + low.bit_length() - 1]
+            per.append(row)
+        out.append(per)
+    return out
+
+
 def write_tables() -> str:
     os.makedirs(GEN, exist_ok=True)
     path = os.path.join(GEN, "qmcrt_tables.h")
@@ -128,6 +147,14 @@ def write_tables() -> str:
              "#define QMCRT_GEN_SOBOL_V_INIT { \\"]
     for row in V:
         lines.append("  {" + ",".join(f"0x{v:08x}u" for v in row) + "}, \\")
+    lines.append("}")
+    lines.append(f"#define QMCRT_GEN_SOBOL_BYTE_DIMS {SOBOL_BYTE_DIMS}")
+    lines.append("#define QMCRT_GEN_SOBOL_BYTE_INIT { \\")
+    for per in sobol_byte_table(V):
+        lines.append("  { \\")
+        for row in per:
+            lines.append("    {" + ",".join(f"0x{v:08x}u" for v in row) + "}, \\")
+        lines.append("  }, \\")
     lines.append("}")
     lines.append("#define QMCRT_GEN_PRIMES_INIT {" + ",".join(f"{p}u" for p in primes()) + "}")
     lines.append("#define QMCRT_GEN_NIED_V_INIT { \\")

@@ -189,6 +189,24 @@ void make_order(int kind, uint64_t first, uint64_t count, qmcrt::OrderP &O, int 
             O.block0 = first >> m;
             const uint64_t nblocks = ((first + count - 1) >> m) - O.block0 + 1;
             O.threads = nblocks << m;
+            // The part of g that depends only on the block (the leading bits y of the
+            // block start's coordinates), for the first block: the kernels take it from
+            // here instead of recomputing it per packet.
+            const uint32_t b32 = (uint32_t)(O.block0 << m);
+            const uint32_t gb = O.net == 2 ? b32 : b32 ^ (b32 >> 1);
+            const int bd[5] = {0, 1, 2, O.xdim[0], O.xdim[1]};
+            uint32_t bv[5] = {0, 0, 0, 0, 0};
+            for (int k = 0; k < 32; ++k)
+                if ((gb >> k) & 1u)
+                    for (int c = 0; c < 5; ++c) bv[c] ^= V[bd[c]][k];
+            auto lead = [](uint32_t x, int n) { return n ? x >> (32 - n) : 0u; };
+            const int s1 = nb[2], s0 = s1 + nb[1], s3 = s0 + nb[0], s4 = s3 + nb[3];
+            const uint32_t y = lead(bv[2], nb[2]) | (lead(bv[1], nb[1]) << s1) | (lead(bv[0], nb[0]) << s0) |
+                               (lead(bv[3], nb[3]) << s3) | (lead(bv[4], nb[4]) << s4);
+            O.g0_block = O.block0;
+            O.g0 = 0;
+            for (int j = 0; j < bits; ++j)
+                if ((y >> j) & 1u) O.g0 ^= O.ry[j];
             return;
         }
         if (xbits == 0) return;  // no full rank even without the further coordinates

@@ -131,6 +131,10 @@ __global__ void __launch_bounds__(256) k_trace_batch(const __grid_constant__ Tra
             const unsigned long long tpc = ((1ull << m) + tile_packets - 1) / tile_packets;
             const unsigned long long local = w - ws[1 + lo];
             sP.ord.block0 = (I.first_index >> m) + local / tpc;
+            if (sP.ord.net && sP.ord.g0_block != sP.ord.block0) {  // the block's term, once per tile
+                sP.ord.g0 = block_columns(sP.ord, sP.ord.block0 << m);
+                sP.ord.g0_block = sP.ord.block0;
+            }
             sP.ord.threads = (local % tpc) * tile_packets;  // first position of this tile
         }
         __syncthreads();

@@ -21,6 +21,9 @@ namespace qmcrt {
 static __constant__ uint32_t c_sobol_v[QMCRT_GEN_DIMS][32] = QMCRT_GEN_SOBOL_V_INIT;
 static __constant__ uint32_t c_primes[QMCRT_GEN_DIMS] = QMCRT_GEN_PRIMES_INIT;
 static __device__ const uint32_t d_nied_v[QMCRT_GEN_DIMS][32] = QMCRT_GEN_NIED_V_INIT;
+// The same direction numbers of the leading dimensions grouped by bytes of the Gray code:
+// entry [d][b][v] is the XOR of V[d][8 b + k] over the set bits k of v.
+static __device__ const uint32_t d_sobol_byte[QMCRT_GEN_SOBOL_BYTE_DIMS][4][256] = QMCRT_GEN_SOBOL_BYTE_INIT;
 
 constexpr unsigned FULL_MASK = 0xffffffffu;
 
@@ -95,11 +98,16 @@ __device__ __forceinline__ void normalize3(T a[3])
 // Point generators (Sec. 3.1)
 // ------------------------------------------------------------------------------------
 
-// Sobol: XOR of the direction numbers over the set bits of gray(i).  The loop is
-// uniform across the warp so every constant load is a broadcast.
+// Sobol: XOR of the direction numbers over the set bits of gray(i).  The leading
+// dimensions take it a byte at a time from the grouped table (four independent loads);
+// the rest loop over the bits, uniform across the warp so every constant load is a
+// broadcast.
 __device__ __forceinline__ uint32_t sobol_u32(uint32_t i, int d)
 {
     const uint32_t g = i ^ (i >> 1);
+    if (d < QMCRT_GEN_SOBOL_BYTE_DIMS)
+        return __ldg(&d_sobol_byte[d][0][g & 255u]) ^ __ldg(&d_sobol_byte[d][1][(g >> 8) & 255u]) ^
+               __ldg(&d_sobol_byte[d][2][(g >> 16) & 255u]) ^ __ldg(&d_sobol_byte[d][3][g >> 24]);
     uint32_t x = 0;
 #pragma unroll
     for (int k = 0; k < 32; ++k) x ^= (g & (1u << k)) ? c_sobol_v[d][k] : 0u;
@@ -240,7 +248,7 @@ __device__ __forceinline__ T point(const PointsP &P, uint64_t i, int d)
     return Mth<T>::from_f64(point_f64(P, i, d));
 }
 
-// Point index traced by thread tid (see OrderP); false if it lies outside the range.
+// Inverse of the Gray code g = i ^ (i >> 1).
 __device__ __forceinline__ uint32_t gray_inverse(uint32_t g)
 {
     g ^= g >> 1;
@@ -253,19 +261,10 @@ __device__ __forceinline__ uint32_t gray_inverse(uint32_t g)
 
 __device__ __forceinline__ uint32_t lead_bits(uint32_t x, int n) { return n ? x >> (32 - n) : 0u; }
 
-__device__ __forceinline__ bool packet_index(const OrderP &O, uint64_t first, uint64_t count, uint64_t tid,
-                                             uint64_t &i)
+// The part of the GF(2) combination that depends only on the block starting at base (a
+// multiple of 2^m): the columns ry of the leading bits y of the block start's coordinates.
+__device__ __forceinline__ uint32_t block_columns(const OrderP &O, uint64_t base)
 {
-    if (!O.net) {
-        i = first + tid;
-        return tid < count;
-    }
-    const uint64_t base = (O.block0 + (tid >> O.m)) << O.m;
-    const uint32_t tl = (uint32_t)(tid & ((1ull << O.m) - 1));
-    const uint32_t box = tl >> O.tt;
-    uint32_t g = 0;
-    for (int j = 0; j < O.bits; ++j) g ^= ((box >> j) & 1u) ? O.rm[j] : 0u;
-    for (int j = 0; j < O.tt; ++j) g ^= ((tl >> j) & 1u) ? O.k[j] : 0u;
     const bool nied = O.net == 2;
     const bool extra = O.nb[3] + O.nb[4] > 0;  // uniform: the order also groups xdim[0], xdim[1]
     // The block start is a multiple of 2^m, so its digit vector (Gray code for Sobol)
@@ -296,7 +295,36 @@ __device__ __forceinline__ bool packet_index(const OrderP &O, uint64_t first, ui
     const int s1 = O.nb[2], s0 = s1 + O.nb[1], s3 = s0 + O.nb[0], s4 = s3 + O.nb[3];
     const uint32_t y = lead_bits(b2, O.nb[2]) | (lead_bits(b1, O.nb[1]) << s1) | (lead_bits(b0, O.nb[0]) << s0) |
                        (lead_bits(b3, O.nb[3]) << s3) | (lead_bits(b4, O.nb[4]) << s4);
-    for (int j = 0; j < O.bits; ++j) g ^= ((y >> j) & 1u) ? O.ry[j] : 0u;
+    uint32_t g = 0;
+#pragma unroll
+    for (int j = 0; j < NET_MAX_M; ++j) g ^= ((y >> j) & 1u) ? O.ry[j] : 0u;  // y < 2^bits
+    return g;
+}
+
+// Point index traced by thread tid: with the net order, thread t of a block traces the
+// point in elementary box t (Morton order); the block's own term comes from the host
+// (O.g0) for the block O.g0_block and is computed here for any other.  False if the
+// index lies outside the range.
+__device__ __forceinline__ bool packet_index(const OrderP &O, uint64_t first, uint64_t count, uint64_t tid,
+                                             uint64_t &i)
+{
+    if (!O.net) {
+        i = first + tid;
+        return tid < count;
+    }
+    const uint64_t base = (O.block0 + (tid >> O.m)) << O.m;
+    const uint32_t tl = (uint32_t)(tid & ((1ull << O.m) - 1));
+    const uint32_t box = tl >> O.tt;                 // < 2^bits
+    const uint32_t kt = tl & ((1u << O.tt) - 1u);   // < 2^tt
+    // Unrolled over the largest sizes: the bits of box, kt and y above bits (tt) are zero,
+    // so the columns past them (zero-filled) never enter.
+    uint32_t g = 0;
+#pragma unroll
+    for (int j = 0; j < NET_MAX_M; ++j) g ^= ((box >> j) & 1u) ? O.rm[j] : 0u;
+#pragma unroll
+    for (int j = 0; j < NET_MAX_TT; ++j) g ^= ((kt >> j) & 1u) ? O.k[j] : 0u;
+    const bool nied = O.net == 2;
+    g ^= base >> O.m == O.g0_block ? O.g0 : block_columns(O, base);
     i = base + (nied ? g : gray_inverse(g));
     return i >= first && i < first + count;
 }

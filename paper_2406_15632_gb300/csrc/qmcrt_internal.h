@@ -93,6 +93,8 @@ struct OrderP {
     uint32_t rm[NET_MAX_M];  // R column for Morton bit j of the thread's box index
     uint32_t ry[NET_MAX_M];  // R column for bit j of y
     uint32_t k[NET_MAX_TT];  // kernel basis of L
+    uint64_t g0_block;       // a block whose y part is precomputed (the launch's first)
+    uint32_t g0;             // XOR of ry over the bits of that block's y
 };
 
 // Net-order tables for every block size a batch may use (m = NET_MIN_M .. NET_MAX_M).

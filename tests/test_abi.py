@@ -181,6 +181,25 @@ def test_missing_library_fails_loudly(tmp_path):
             Q._lib = Q._lib_saved
 
 
+def test_sobol_byte_table_gives_the_oracle_points():
+    """The byte-grouped direction numbers the kernels use for the leading dimensions: the
+    XOR of one entry per byte of gray(i) is the Sobol coordinate the oracle computes."""
+    from oracle import oracle as O
+
+    T = B.sobol_byte_table(B.sobol_direction_table(B.SOBOL_BYTE_DIMS))
+    idx = np.concatenate([np.arange(4096), np.random.default_rng(3).integers(0, 1 << 32, 4096)]).astype(np.uint64)
+    g = idx ^ (idx >> np.uint64(1))
+    got = np.zeros((idx.size, B.SOBOL_BYTE_DIMS), dtype=np.uint64)
+    for d in range(B.SOBOL_BYTE_DIMS):
+        for b in range(4):
+            got[:, d] ^= np.asarray(T[d][b], dtype=np.uint64)[(g >> np.uint64(8 * b)) & np.uint64(255)]
+    for lo in (0, 4096):
+        ref = O.generate_points("sobol", B.SOBOL_BYTE_DIMS, 0, 4096, "u32") if lo == 0 else np.stack(
+            [O.generate_points("sobol", B.SOBOL_BYTE_DIMS, int(i), 1, "u32")[0] for i in idx[4096:4160]])
+        n = ref.shape[0]
+        assert np.array_equal(got[lo:lo + n], ref.astype(np.uint64))
+
+
 def test_default_frac_bits_never_overflows():
     from paper_2406_15632_gb300 import scenes as S
 

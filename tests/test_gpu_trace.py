@@ -87,11 +87,15 @@ def test_trace_single_fp64_matches_oracle(Q, name, accum):
     assert rel_l2(got, ref) <= 1e-10
 
 
-def test_trace_single_fp64_packet_log(Q):
+@pytest.mark.parametrize("first", [1, 5 * 2048 + 77])
+def test_trace_single_fp64_packet_log(Q, first):
+    """Packet by packet against the oracle.  N = 3000 is ragged (not a multiple of 32) and
+    spans two aligned blocks of 2048 indices: the first block's own term of the net order
+    comes from the host, the second block's is computed on the device."""
     prob = DISK32.replace(source="sphere", star_r=0.05, limb_u=0.6)
-    N = 3000  # ragged: not a multiple of 32
-    _, lg = gpu_image(Q, prob, N, precision="f64", log=True)
-    _, ref = O.trace_single(prob, 1, N, log=True)
+    N = 3000
+    _, lg = gpu_image(Q, prob, N, first=first, precision="f64", log=True)
+    _, ref = O.trace_single(prob, first, N, log=True)
     assert np.array_equal(lg[:, 8], ref[:, 8])
     assert np.allclose(lg[:, :8], ref[:, :8], rtol=1e-11, atol=1e-13)
 
