@@ -34,7 +34,8 @@ METRIC = "packets/s and wall time to fixed image RMS error (QMC, learned vs plai
 PACKETS_PER_STEP = 1 << 26
 OPS_PER_CELL = 10          # algorithmic ALU operations per grid-cell visit (see design notes)
 SMS, LANES_PER_SM = 152, 128
-KERNEL_SOURCES = ["paper_2406_15632_gb300/csrc/qmcrt_device.cuh", "paper_2406_15632_gb300/csrc/qmcrt_trace_single.cu"]
+KERNEL_SOURCES = ["paper_2406_15632_gb300/csrc/qmcrt_device.cuh", "paper_2406_15632_gb300/csrc/qmcrt_trace_single.cu",
+                  "paper_2406_15632_gb300/csrc/qmcrt_api.cu"]  # the kernel and the host side of its packet order
 PROFILE = os.path.join(ROOT, "profiles", "trace_single_flared_disk_256.md")
 COUNTS = os.path.join(ROOT, "tests", "golden", "workload_counts.json")
 

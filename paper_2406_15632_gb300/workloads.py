@@ -3,7 +3,7 @@
     python -m paper_2406_15632_gb300.workloads <name> [--log2-n L] [--repeat R]
 
 Names:
-  disk_single      single scattering, 256^3 flared disk, 256x256 I/Q/U, FP32, 2^L packets
+  disk_single      single scattering, 256^3 flared disk (--grid G: G^3), 256x256 I/Q/U, FP32, 2^L packets
   clumpy_multiple  multiple scattering (20 orders), 128^3 clumpy envelope, 512x512, 2^L packets
   clumpy_wavefront the same packets order by order (live packets regrouped between orders)
   warp_forward     fused forward of the learned warp on 2^L Sobol points
@@ -46,12 +46,13 @@ def main(argv=None) -> int:
     ap.add_argument("--log2-n", type=int, default=20)
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--instances", type=int, default=0, help="batch: the first N instances only (0: all 256)")
+    ap.add_argument("--grid", type=int, default=0, help="disk_single: cells per axis of the disk (0: 256)")
     a = ap.parse_args(argv)
     Q.load()
     n = 1 << a.log2_n
     t0 = time.perf_counter()
     if a.name in ("disk_single", "clumpy_multiple"):
-        prob = S.flared_disk_problem(n=256) if a.name == "disk_single" else S.clumpy_problem(n=128)
+        prob = S.flared_disk_problem(n=a.grid or 256) if a.name == "disk_single" else S.clumpy_problem(n=128)
         sc = Q.Scene(prob)
         fb = Q.default_frac_bits(prob, n)
         buf = sc.accum_buffer("i64")
