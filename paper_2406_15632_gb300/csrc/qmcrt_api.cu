@@ -121,11 +121,11 @@ void make_order(int kind, uint64_t first, uint64_t count, qmcrt::OrderP &O, int 
     for (int pass = 0; pass < 2; ++pass, xbits = 0) {
         for (int tt = 0; tt <= qmcrt::NET_MAX_TT; ++tt) {
             const int bits = m - tt;
-            // the further coordinates take bits only from large blocks: the ray coordinates
-            // keep 22 leading bits between them (measured on the 256^3 disk with R* = 6.4
-            // cells: 2^24 packets 4 % faster, direct order 13 %; blocks of 2^22-2^23 lose
-            // when the ray coordinates drop to 20-21 bits)
-            const int xb = std::min(xbits, std::max(0, (bits - 22) / 2));
+            // the further coordinates take bits only from blocks large enough that the ray
+            // coordinates keep 18 leading bits between them (measured on the 256-instance
+            // finite-star batch, R* = 6.4 cells, blocks of 2^18-2^23, with a warp's thread
+            // bits on the depth coordinate: 8 % faster than keeping 22; keeping 16 the same)
+            const int xb = std::min(xbits, std::max(0, (bits - 18) / 2));
             const int r = bits - 2 * xb;
             const int nb[5] = {(r + 2) / 3, (r + 1) / 3, r / 3, xb, xb};
             const int dims[5] = {0, 1, 2, x0, x1};
