@@ -415,6 +415,7 @@ __device__ __forceinline__ bool walkable(const T p[3], const T d[3])
 // After the ray leaves the grid the rest of the batch repeats the last cell with
 // zero length, so no load leaves the grid.
 constexpr int WALK_UNROLL = 4;
+static_assert(QMCRT_MIN_PAD >= WALK_UNROLL, "a padded walk steps up to WALK_UNROLL - 1 cells past the first sentinel");
 
 template <class T, bool TARGET>
 __device__ __forceinline__ bool grid_walk(const MediumP<T> &G, const T p[3], const T d[3], T target_raw, T &tau_raw,
