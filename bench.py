@@ -47,11 +47,10 @@ def workload_problem():
 
 
 def workload_config(n_packets):
+    """The workload (flared disk of Sec. 5: g 0.5, albedo 0.6, p_l 0.5, observer at 45 deg,
+    point source, Sobol points in aligned 2^26 blocks, FP32 trace), in a few keys."""
     return {"workload": "flared_disk_single_scattering", "grid": "256^3 fp32", "image": "256x256 I/Q/U",
-            "packets_per_step_per_gpu": n_packets, "points": "sobol (Joe-Kuo), consecutive index ranges",
-            "trace_precision": "fp32 (compensated optical depth)", "accumulate": "int64 fixed point",
-            "l2": "flushed between steps (256 MiB write)", "source": "point", "albedo": 0.6, "g": 0.5, "p_l": 0.5,
-            "theta_obs_deg": 45}
+            "packets_per_step_per_gpu": n_packets, "accumulate": "int64 fixed point", "l2": "flushed (256 MiB write)"}
 
 
 def measured_peaks():
@@ -167,6 +166,7 @@ def run_cpu_baseline(target_seconds: float = 12.0):
     return {"value": n / dt, "unit": "packets/s", "cores": threads, "kind": "oracle",
             "sample": f"first {n} packets of the workload (same Sobol points), FP64 C oracle, {threads} threads, "
                       f"{dt:.1f} s",
+            "sample_short": f"first {n} packets, {threads} threads",
             "single_core": {"value": n1 / dt1, "unit": "packets/s", "sample": f"first {n1} packets, 1 thread, "
                                                                               f"{dt1:.1f} s"}}
 
@@ -518,6 +518,81 @@ def run_time_to_error_qmc(prob, workload, ladder=(20, 22, 24, 26), ref_log2=28, 
             "ladder": arms, "time_to_error_ms": summary}
 
 
+def _sig(x, digits=4):
+    """x rounded to `digits` significant digits (None stays None)."""
+    if x is None or isinstance(x, bool) or not isinstance(x, (int, float)) or x == 0 or not math.isfinite(x):
+        return x
+    return round(x, digits - 1 - int(math.floor(math.log10(abs(x)))))
+
+
+def _speedups(tte, num, den, targets=None):
+    """{target: time(num) / time(den)} over the targets where both arms have a time, and
+    the targets where either time was extrapolated beyond its ladder."""
+    out, extrap = {}, []
+    for tgt, row in tte.items():
+        if targets and tgt not in targets:
+            continue
+        a, b = row.get(num, {}), row.get(den, {})
+        if a.get("ms") and b.get("ms"):
+            out[tgt] = _sig(a["ms"] / b["ms"], 3)
+            if a.get("extrapolated") or b.get("extrapolated"):
+                extrap.append(tgt)
+    return out, extrap
+
+
+def summarize(sections):
+    """One or two numbers per detailed section, for the headline line; `extrapolated`
+    lists the time-to-error speedups taken beyond a ladder's last point."""
+    out, extrap = {}, []
+    ms = sections.get("multiple_scattering")
+    if ms:
+        out["multiple_scattering"] = {"packets_per_s": _sig(ms["packets_per_s"]), "frac": _sig(ms["roofline"]["frac"], 3)}
+    b = sections.get("batched")
+    if b:
+        out["batched"] = {"packets_per_s": _sig(b["packets_per_s"]), "vs_each": _sig(b["speedup_at_equal_images"], 3)}
+        if "time_to_error" in b:
+            out["batched"]["tte_speedup"] = _sig(b["time_to_error"].get("speedup"), 3)
+    o = sections.get("observers")
+    if o:
+        out["observers_speedup"] = _sig(o["speedup"], 3)
+    le = sections.get("time_to_error_learned_vs_plain")
+    if le:
+        sp, ex = _speedups(le["time_to_error_ms"], "plain_qmc", "learned_qmc")
+        out["learned_vs_plain_at_rms"] = sp
+        extrap += [f"learned@{t}" for t in ex]
+    d = sections.get("time_to_error_qmc_vs_mc_disk")
+    if d:
+        sp, ex = _speedups(d["time_to_error_ms"], "mc_philox", "sobol", ("0.01", "0.003"))
+        out["sobol_vs_mc_at_rms"] = sp
+        extrap += [f"sobol@{t}" for t in ex]
+    if extrap:
+        out["extrapolated"] = extrap
+    return out
+
+
+def headline(line, sections):
+    """The compact last line: the contract's keys, the roofline, e2e, clocks, the CPU
+    baseline and a summary of the detailed sections (printed on earlier lines)."""
+    h = {k: line[k] for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config", "e2e",
+                              "gpu_launches") if k in line}
+    h["value"] = _sig(h["value"], 6)
+    h["ms_per_step"] = _sig(h["ms_per_step"], 6)
+    h["roofline"] = {k: _sig(line["roofline"].get(k), 4) for k in ("bound", "achieved", "peak", "unit", "frac",
+                                                                    "traffic", "kernel")}
+    h["e2e"] = {k: _sig(v, 6) for k, v in h["e2e"].items()}
+    clk = line.get("clocks") or {}
+    h["clocks"] = {k: clk.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons")}
+    cb = sections.get("cpu_baseline")
+    if cb:
+        h["cpu_baseline"] = {"value": _sig(cb["value"]), "unit": cb["unit"], "cores": cb["cores"], "kind": cb["kind"],
+                             "sample": cb["sample_short"], "one_core": _sig(cb["single_core"]["value"])}
+    s = summarize(sections)
+    if s:
+        h["sections"] = s
+    return h
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -671,16 +746,25 @@ def main():
         "gpu_launches": 2 * args.steps * 1,
         "clocks": clk,
     }
+    # Detailed sections go on their own lines first; the last line of stdout is the
+    # compact headline (a few hundred bytes), which is what a reader of the tail parses.
+    sections = {}
+
+    def section(name, fn):
+        sections[name] = fn()
+        print(json.dumps({"section": name, **sections[name]}), flush=True)
     if world == 1 and not args.no_extras:
-        line["multiple_scattering"] = run_multiple_scattering()
-        line["batched"] = run_batched()
-        line["observers"] = run_observers()
-        line["time_to_error"] = {"learned_vs_plain": run_time_to_error_learned(),
-                                 "qmc_vs_mc_disk": run_time_to_error_disk(),
-                                 "qmc_vs_mc_geometries": run_time_to_error_geometries()}
+        section("multiple_scattering", run_multiple_scattering)
+        section("batched", run_batched)
+        section("observers", run_observers)
+        section("time_to_error_learned_vs_plain", run_time_to_error_learned)
+        section("time_to_error_qmc_vs_mc_disk", run_time_to_error_disk)
+        for k, v in run_time_to_error_geometries().items():
+            sections[f"time_to_error_qmc_vs_mc_{k}"] = v
+            print(json.dumps({"section": f"time_to_error_qmc_vs_mc_{k}", **v}), flush=True)
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = run_cpu_baseline()
-    print(json.dumps(line), flush=True)
+        section("cpu_baseline", run_cpu_baseline)
+    print(json.dumps(headline(line, sections), separators=(",", ":")), flush=True)
     if world > 1:
         dist.destroy_process_group()
     return 0

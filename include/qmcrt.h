@@ -465,8 +465,10 @@ int qmcrt_image_reduce(const qmcrt_image *image, int32_t nx, int32_t ny, int32_t
  * Every call clears the part of the scratch it uses, then traces and reduces on
  * stream.  All calls share the one scratch array: calls whose work overlaps on the
  * GPU (other streams, other host threads) race and corrupt each other's images.
- * The first call on a device looks up the scratch address with that device current;
- * make it before any stream capture.
+ * Every call looks up the scratch's device address with the caller's device current
+ * (after a cudaDeviceReset the array has a new address, so none is cached); the first
+ * lookup on a device may load the library's kernels, so make the first call before
+ * any stream capture.  All arguments are checked before anything is enqueued.
  * Errors: as qmcrt_trace_single; INVALID_ARG for NULL d_image or an image of more than
  * QMCRT_NOALLOC_MAX_PIXELS pixels; CUDA if the scratch address cannot be found.
  */

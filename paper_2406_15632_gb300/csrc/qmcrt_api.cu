@@ -442,6 +442,25 @@ int trace_common(const qmcrt_medium *md, const qmcrt_source *src, const qmcrt_du
                        "trace launch");
 }
 
+// The host-side checks of trace_common without the launch: the status the call would
+// return for these arguments, nothing enqueued.
+int check_trace(const qmcrt_medium *md, const qmcrt_source *src, const qmcrt_dust *du, const qmcrt_observer *ob,
+                const qmcrt_points_desc *pts, const qmcrt_trace_opts *op, const qmcrt_image *im, int multiple)
+{
+    CHECK_STRUCT(md, qmcrt_medium);
+    CHECK_STRUCT(src, qmcrt_source);
+    CHECK_STRUCT(du, qmcrt_dust);
+    CHECK_STRUCT(ob, qmcrt_observer);
+    CHECK_STRUCT(op, qmcrt_trace_opts);
+    CHECK_STRUCT(im, qmcrt_image);
+    if (op->precision == QMCRT_PREC_F64) {
+        qmcrt::TraceP<double> P;
+        return fill_trace<double>(md, src, du, ob, pts, op, im, multiple, P);
+    }
+    qmcrt::TraceP<float> P;
+    return fill_trace<float>(md, src, du, ob, pts, op, im, multiple, P);
+}
+
 cudaError_t launch_observers(const qmcrt::TraceP<float> &P, const qmcrt::ObsSet<float> &S, int block, cudaStream_t s)
 {
     return qmcrt::launch_trace_observers_f32(P, S, block, s);
@@ -519,6 +538,13 @@ int wavefront_run(qmcrt::TraceP<T> P, const qmcrt_points_desc *pts, WarpIO wio, 
 }  // namespace
 
 namespace qmcrt {
+
+int check_trace_single(const qmcrt_medium *md, const qmcrt_source *src, const qmcrt_dust *du,
+                       const qmcrt_observer *ob, const qmcrt_points_desc *pts, const qmcrt_trace_opts *op,
+                       const qmcrt_image *im)
+{
+    return check_trace(md, src, du, ob, pts, op, im, 0);
+}
 
 int set_error(int code, const char *fmt, ...)
 {

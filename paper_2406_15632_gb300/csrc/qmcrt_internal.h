@@ -150,6 +150,12 @@ cudaError_t launch_gemm_bf16(const __nv_bfloat16 *A, const __nv_bfloat16 *B, int
 // Records a message for qmcrt_last_error() on the calling thread; returns code.
 int set_error(int code, const char *fmt, ...);
 
+// The status qmcrt_trace_single would return for these arguments, from its host-side
+// checks alone (nothing is enqueued).
+int check_trace_single(const qmcrt_medium *md, const qmcrt_source *src, const qmcrt_dust *du,
+                       const qmcrt_observer *ob, const qmcrt_points_desc *pts, const qmcrt_trace_opts *op,
+                       const qmcrt_image *im);
+
 // Launchers (return a cudaError_t from the launch).
 cudaError_t launch_trace_batch_f32(const TraceP<float> &p, const NetTables &tab, const qmcrt_instance *inst,
                                    int n_inst, unsigned long long *ws, int block, int ctas, int per_thread,

@@ -6,39 +6,29 @@
 // (QMCRT_NOALLOC_MAX_PIXELS x 3 int64 values = 6 MiB per GPU).  Calls share it: each
 // call clears the part it uses before tracing, and two calls whose work overlaps on
 // the GPU (different streams, or different host threads) corrupt each other's
-// images.  The first call on a device looks up the array's device address with that
-// device current; make that first call before any stream capture.
+// images.  Every call looks up the array's device address with the caller's device
+// current (a cudaDeviceReset gives the array a new address, so nothing is cached);
+// the first lookup on a device may load the library's kernels, so make the first call
+// before any stream capture.
 #include <cstring>
-#include <mutex>
 
 #include "qmcrt.h"
 #include "qmcrt_internal.h"
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-
 static __device__ __align__(256) long long g_noalloc_accum[3 * QMCRT_NOALLOC_MAX_PIXELS];
 
-std::mutex g_setup_mutex;
-void *g_accum_ptr[kMaxDevices];
-
-// Device address of g_noalloc_accum on the current device (looked up once per device).
+// Device address of g_noalloc_accum on the current device.  In host code the array's
+// name stands for a host-side shadow, not a device address: only this address may be
+// handed to a kernel.
 int accum_address(void **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return qmcrt::set_error(QMCRT_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
-    if (dev < 0 || dev >= kMaxDevices) return qmcrt::set_error(QMCRT_ERR_UNSUPPORTED, "device %d beyond %d", dev, kMaxDevices);
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_accum_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_accum);
-        if (e != cudaSuccess || !p)
-            return qmcrt::set_error(QMCRT_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-        g_accum_ptr[dev] = p;
-    }
-    *out = g_accum_ptr[dev];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_accum);
+    if (e != cudaSuccess || !p)
+        return qmcrt::set_error(QMCRT_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    *out = p;
     return QMCRT_OK;
 }
 
@@ -59,9 +49,6 @@ extern "C" int qmcrt_trace_single_noalloc(const qmcrt_medium *medium, const qmcr
     void *accum = nullptr;
     int rc = accum_address(&accum);
     if (rc) return rc;
-    const size_t bytes = (size_t)3 * obs->nx * obs->ny * sizeof(long long);
-    cudaError_t e = cudaMemsetAsync(accum, 0, bytes, (cudaStream_t)stream);
-    if (e != cudaSuccess) return qmcrt::set_error(QMCRT_ERR_CUDA, "clearing the scratch: %s", cudaGetErrorString(e));
     qmcrt_image im;
     memset(&im, 0, sizeof im);
     im.struct_size = sizeof im;
@@ -69,6 +56,13 @@ extern "C" int qmcrt_trace_single_noalloc(const qmcrt_medium *medium, const qmcr
     im.d_accum = accum;
     im.n_images = 1;
     im.frac_bits = frac_bits;
+    // every argument is checked before the first enqueue: a rejected call leaves
+    // nothing on the stream (nor in a graph being captured)
+    rc = qmcrt::check_trace_single(medium, source, dust, obs, pts, opts, &im);
+    if (rc) return rc;
+    const size_t bytes = (size_t)3 * obs->nx * obs->ny * sizeof(long long);
+    const cudaError_t e = cudaMemsetAsync(accum, 0, bytes, (cudaStream_t)stream);
+    if (e != cudaSuccess) return qmcrt::set_error(QMCRT_ERR_CUDA, "clearing the scratch: %s", cudaGetErrorString(e));
     rc = qmcrt_trace_single(medium, source, dust, obs, pts, opts, &im, nullptr, stream);
     if (rc) return rc;
     return qmcrt_image_reduce(&im, obs->nx, obs->ny, 1, scale, d_image, stream);
