@@ -450,6 +450,63 @@ int qmcrt_image_reduce(const qmcrt_image *image, int32_t nx, int32_t ny, int32_t
                        double *d_out, void *stream);
 
 /*
+ * qmcrt_contribution_bound -- *bound = the largest |I|, |Q| or |U| one peel-off
+ * contribution can carry (Sec. 2.2, 3.5, 3.6), for the source (limb weight at most
+ * 1 / (1 - u/3)), dust and options given; multiple != 0 takes opts->max_orders orders and
+ * the roulette (a survivor's weight below rr_threshold grows by 1 / rr_survival), 0 one
+ * order.  Each scattering multiplies I by at most albedo (1 + p_l) (forcing weight <= 1,
+ * M/P11 with |Q| <= I); the peel-off adds the largest HG value (1 + |g|) / (4 pi
+ * (1 - |g|)^2): order k is below limb p_max max(1, thr / surv) (albedo (1 + p_l))^k, and
+ * the bound is its largest value over k <= the orders.
+ * Errors: INVALID_ARG (NULL pointers or wrong struct_size, dust or limb_u out of range,
+ * max_orders outside 1..64 or rr_survival outside (0, 1] when multiple).
+ */
+int qmcrt_contribution_bound(const qmcrt_source *source, const qmcrt_dust *dust, const qmcrt_trace_opts *opts,
+                             int32_t multiple, double *bound);
+
+/*
+ * qmcrt_default_frac_bits -- *frac_bits = the largest F in 0..62 for which an int64
+ * fixed-point image (QMCRT_ACCUM_I64, value = raw 2^-F) cannot overflow when n_packets
+ * packets are added: n_packets x (contributions per packet and pixel: max_orders for
+ * multiple scattering into one image, else 1) x qmcrt_contribution_bound x weight_bound
+ * x 2^F <= 2^62.  weight_bound (>= 1) bounds an extra factor on every packet's weight:
+ * 1 for plain QMC, mix^-3 for a learned warp with uniform mixture mix (|dx/du| <= mix^-3).
+ * Errors: as qmcrt_contribution_bound; INVALID_ARG for NULL frac_bits or weight_bound
+ * not finite or below 1.
+ */
+int qmcrt_default_frac_bits(const qmcrt_source *source, const qmcrt_dust *dust, const qmcrt_trace_opts *opts,
+                            int32_t multiple, uint64_t n_packets, double weight_bound, int32_t *frac_bits);
+
+/* ---- single scattering with host-resident inputs and outputs ---- */
+typedef struct qmcrt_host_io {
+    uint32_t struct_size;
+    int32_t reserved;
+    const float *h_k;   /* host [nz][ny][nx] grid copied in by the call, or NULL to keep the device grid */
+    float *d_k;         /* device [nz][ny][nx] receiving h_k when medium->pad > 0 (then padded into
+                           medium->d_k); unused when pad == 0 (h_k goes straight to medium->d_k) */
+    void *d_accum;      /* device int64 [3][ny][nx]: fixed-point scratch, cleared by the call */
+    double *d_image;    /* device [3][ny][nx]: the reduced image */
+    double *h_image;    /* host [3][ny][nx]: receives the image (pinned memory keeps the call asynchronous) */
+} qmcrt_host_io;
+
+/*
+ * qmcrt_render_single_host -- one end-to-end single-scattering render for a caller whose
+ * inputs and outputs live in host memory (Sec. 3.2-3.6): enqueues on stream the copy of
+ * io->h_k to the device (one cudaMemcpyAsync), its sentinel padding (qmcrt_pad_grid,
+ * when medium->pad > 0), the clearing of io->d_accum, qmcrt_trace_single with fixed-point
+ * accumulation at frac_bits, qmcrt_image_reduce with scale (normally 1/N) into
+ * io->d_image, and the copy of that image to io->h_image (one cudaMemcpyAsync).  The
+ * call returns after enqueuing: synchronize the stream before reading h_image.  The
+ * device buffers are the caller's; the library allocates nothing.
+ * Errors: as qmcrt_trace_single; INVALID_ARG for a NULL or mis-sized io, NULL d_accum,
+ * d_image or h_image, h_k for a sphere medium, a padded medium without d_k or with
+ * d_k == medium->d_k; CUDA for a failed copy.
+ */
+int qmcrt_render_single_host(const qmcrt_medium *medium, const qmcrt_source *source, const qmcrt_dust *dust,
+                             const qmcrt_observer *obs, const qmcrt_points_desc *pts, const qmcrt_trace_opts *opts,
+                             const qmcrt_host_io *io, int32_t frac_bits, double scale, void *stream);
+
+/*
  * qmcrt_trace_single_noalloc -- qmcrt_trace_single followed by qmcrt_image_reduce for
  * one image, for callers that cannot allocate device memory: code embedded in a host
  * application that owns every device allocation through its own pool, or code that

@@ -103,6 +103,11 @@ class qmcrt_adam(C.Structure):
                 ("beta2", C.c_double), ("eps", C.c_double)]
 
 
+class qmcrt_host_io(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("reserved", C.c_int32), ("h_k", C.c_void_p), ("d_k", C.c_void_p),
+                ("d_accum", C.c_void_p), ("d_image", C.c_void_p), ("h_image", C.c_void_p)]
+
+
 def _new(cls, **kw):
     s = cls()
     s.struct_size = C.sizeof(cls)
@@ -159,6 +164,13 @@ _SIGS = [
     ("qmcrt_trace_single_noalloc", C.c_int, [_P(qmcrt_medium), _P(qmcrt_source), _P(qmcrt_dust),
                                              _P(qmcrt_observer), _P(qmcrt_points_desc), _P(qmcrt_trace_opts),
                                              C.c_int32, C.c_double, C.c_void_p, C.c_void_p]),
+    ("qmcrt_contribution_bound", C.c_int, [_P(qmcrt_source), _P(qmcrt_dust), _P(qmcrt_trace_opts), C.c_int32,
+                                           _P(C.c_double)]),
+    ("qmcrt_default_frac_bits", C.c_int, [_P(qmcrt_source), _P(qmcrt_dust), _P(qmcrt_trace_opts), C.c_int32,
+                                          C.c_uint64, C.c_double, _P(C.c_int32)]),
+    ("qmcrt_render_single_host", C.c_int, [_P(qmcrt_medium), _P(qmcrt_source), _P(qmcrt_dust),
+                                           _P(qmcrt_observer), _P(qmcrt_points_desc), _P(qmcrt_trace_opts),
+                                           _P(qmcrt_host_io), C.c_int32, C.c_double, C.c_void_p]),
 ]
 EXPORTED = [s[0] for s in _SIGS]
 
@@ -403,6 +415,27 @@ def qmcrt_trace_single_noalloc(medium, source, dust, obs, pts, opts, frac_bits: 
                                              C.c_void_p(stream)))
 
 
+def qmcrt_contribution_bound(source, dust, opts, multiple: bool) -> float:
+    out = C.c_double(0.0)
+    _check(load().qmcrt_contribution_bound(C.byref(source), C.byref(dust), C.byref(opts), int(bool(multiple)),
+                                           C.byref(out)))
+    return out.value
+
+
+def qmcrt_default_frac_bits(source, dust, opts, multiple: bool, n_packets: int, weight_bound: float = 1.0) -> int:
+    out = C.c_int32(0)
+    _check(load().qmcrt_default_frac_bits(C.byref(source), C.byref(dust), C.byref(opts), int(bool(multiple)),
+                                          int(n_packets), float(weight_bound), C.byref(out)))
+    return out.value
+
+
+def qmcrt_render_single_host(medium, source, dust, obs, pts, opts, io, frac_bits: int, scale: float,
+                             stream: int = 0) -> None:
+    _check(load().qmcrt_render_single_host(C.byref(medium), C.byref(source), C.byref(dust), C.byref(obs),
+                                           C.byref(pts), C.byref(opts), C.byref(io), frac_bits, scale,
+                                           C.c_void_p(stream)))
+
+
 # --- marshalling helpers ------------------------------------------------------------------
 
 def _torch():
@@ -435,32 +468,28 @@ def generate_points(kind: str, dims: int, first: int, count: int, fmt: str = "f6
     return out
 
 
-def contribution_bound(prob: scenes.Problem) -> float:
-    """Upper bound on |I|, |Q|, |U| of one peel-off contribution.
+def _bound_structs(prob: scenes.Problem):
+    """The source, dust and options descriptors of a problem (no device memory)."""
+    source = _new(qmcrt_source, kind=SOURCE_POINT if prob.source == "point" else SOURCE_SPHERE, radius=prob.star_r,
+                  limb_u=prob.limb_u, order=ORDER_DIRECT if prob.emit_order == "direct" else ORDER_INVERSE)
+    dust = _new(qmcrt_dust, albedo=prob.albedo, g=prob.g, p_l=prob.p_l)
+    opts = _new(qmcrt_trace_opts, precision=0, tau_min=prob.tau_min, max_orders=max(prob.max_orders, 1),
+                force_mode=FORCE[prob.force], rr_threshold=prob.rr_threshold, rr_survival=prob.rr_survival,
+                per_order=1 if prob.per_order else 0)
+    return source, dust, opts
 
-    The packet weight starts at the source weight (limb-darkening factor at most
-    1 / (1 - u/3)).  Each scattering multiplies I by the albedo, by the forcing weight
-    (at most 1) and by 1 + (P12/P11)(Q/I) <= 1 + p_l, since |Q| <= I holds for the
-    carried Stokes vector; the peel-off of order k adds the phase function (at most
-    (1 + |g|) / (4 pi (1 - |g|)^2)) and once more at most 1 + p_l.  Roulette resets a
-    weight below the threshold to at most threshold / survival.  So a contribution of
-    order k is below limb * p_max * max(1, thr / surv) * (albedo (1 + p_l))^k, taken
-    at its largest k <= max_orders."""
-    g = abs(prob.g)
-    p_max = (1 + g) / ((1 - g) ** 2) / (4 * math.pi)
-    limb = 1.0 / (1.0 - prob.limb_u / 3.0) if prob.source == "sphere" else 1.0
-    step = prob.albedo * (1 + prob.p_l)
-    growth = max(step ** k for k in range(1, max(prob.max_orders, 1) + 1))
-    rr = max(1.0, prob.rr_threshold / prob.rr_survival) if prob.rr_threshold > 0 else 1.0
-    return limb * p_max * growth * rr
+
+def contribution_bound(prob: scenes.Problem) -> float:
+    """Upper bound on |I|, |Q|, |U| of one peel-off contribution of the problem
+    (qmcrt_contribution_bound; multiple scattering when max_orders > 1)."""
+    return qmcrt_contribution_bound(*_bound_structs(prob), prob.max_orders > 1)
 
 
 def default_frac_bits(prob: scenes.Problem, n_contributions: int, weight_bound: float = 1.0) -> int:
-    """Largest fixed-point scale that cannot overflow: n * bound * 2^F < 2^62.
-    weight_bound multiplies the bound (mix^-3 for a warp with a uniform mixture)."""
-    n = max(int(n_contributions), 1) * max(prob.max_orders if not prob.per_order else 1, 1)
-    need = math.log2(n * contribution_bound(prob) * weight_bound)
-    return int(max(0, min(62, math.floor(62 - need))))
+    """Largest fixed-point scale that cannot overflow for n packets of the problem
+    (qmcrt_default_frac_bits); weight_bound multiplies every weight (mix^-3 for a warp
+    with a uniform mixture)."""
+    return qmcrt_default_frac_bits(*_bound_structs(prob), prob.max_orders > 1, n_contributions, weight_bound)
 
 
 class Scene:
@@ -665,19 +694,22 @@ class LearnedTracer:
 
 
 class HostRenderer:
-    """The end-to-end call for host-resident inputs: each call copies the density grid
-    from (pinned) host memory to the device, traces a packet range, reduces the image
-    and copies it back to host memory, all on one stream.  Device buffers are allocated
-    once, at construction."""
+    """The end-to-end call for host-resident inputs: each call enqueues, through
+    qmcrt_render_single_host, the copy of the density grid from (pinned) host memory,
+    its padding, the trace of a packet range, the reduction and the copy of the image
+    back to host memory, all on one stream.  Device buffers are allocated once, at
+    construction."""
 
-    def __init__(self, prob: scenes.Problem, max_packets: int, *, precision: str = "f32", accum: str = "i64",
+    def __init__(self, prob: scenes.Problem, max_packets: int, *, precision: str = "f32",
                  frac_bits: int | None = None):
         torch = _torch()
+        if prob.max_orders > 1:
+            raise QmcrtError(ERR_UNSUPPORTED, "HostRenderer renders single scattering")
         self.scene = Scene(prob)
-        self.precision, self.accum = precision, accum
+        self.precision = precision
         self.frac_bits = default_frac_bits(prob, max_packets) if frac_bits is None else frac_bits
-        self.buf = self.scene.accum_buffer(accum)
-        self.out = torch.empty((prob.n_images, 3, prob.ny, prob.nx), dtype=torch.float64, device="cuda")
+        self.buf = self.scene.accum_buffer("i64")
+        self.out = torch.empty((1, 3, prob.ny, prob.nx), dtype=torch.float64, device="cuda")
 
     def input_bytes(self) -> int:
         return 0 if self.scene.grid is None else self.scene.grid.numel() * 4
@@ -686,15 +718,13 @@ class HostRenderer:
         return self.out.numel() * 8
 
     def __call__(self, host_grid, first: int, count: int, host_out, stream=None) -> None:
-        if self.scene.grid is not None:
-            self.scene.grid.copy_(host_grid, non_blocking=True)
-            self.scene.repad(stream)
-        self.buf.zero_()
-        self.scene.trace(first, count, self.buf, accum=self.accum, frac_bits=self.frac_bits, precision=self.precision,
-                         stream=stream)
-        self.scene.reduce(self.buf, 1.0 / count, accum=self.accum, frac_bits=self.frac_bits, out=self.out,
-                          stream=stream)
-        host_out.copy_(self.out, non_blocking=True)
+        sc, p = self.scene, self.scene.prob
+        io = _new(qmcrt_host_io, h_k=None if sc.grid is None else host_grid.data_ptr(),
+                  d_k=None if sc.grid is None else sc.grid.data_ptr(), d_accum=self.buf.data_ptr(),
+                  d_image=self.out.data_ptr(), h_image=host_out.data_ptr())
+        pts = points_desc(p.generator, p.dims, first, count, "f64", p.seed, p.total_n)
+        qmcrt_render_single_host(sc.medium, sc.source, sc.dust, sc.obs, pts, sc.opts(self.precision), io,
+                                 self.frac_bits, 1.0 / count, _stream(stream))
 
 
 class Batch:

@@ -41,7 +41,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 STRUCTS = ["qmcrt_points_desc", "qmcrt_medium", "qmcrt_source", "qmcrt_dust", "qmcrt_observer", "qmcrt_image",
            "qmcrt_trace_opts", "qmcrt_instance", "qmcrt_batch_config", "qmcrt_gemm_epilogue",
-           "qmcrt_warp", "qmcrt_adam"]
+           "qmcrt_warp", "qmcrt_adam", "qmcrt_host_io"]
 
 
 def test_struct_layout_matches_the_c_compiler(tmp_path):
@@ -200,14 +200,73 @@ def test_sobol_byte_table_gives_the_oracle_points():
         assert np.array_equal(got[lo:lo + n], ref.astype(np.uint64))
 
 
-def test_default_frac_bits_never_overflows():
+def test_default_frac_bits_never_overflows_and_is_the_largest_such_scale(lib):
+    """The library's scale F: n x (contributions per pixel and packet) x bound x 2^F stays
+    below 2^62, and F + 1 would not (F is the largest safe scale); F never grows with n."""
     from paper_2406_15632_gb300 import scenes as S
 
-    for prob, n in ((S.flared_disk_problem(n=8), 1 << 28), (S.homogeneous_sphere_problem(), 1 << 16),
-                    (S.clumpy_problem(n=8), 1 << 24)):
-        fb = Q.default_frac_bits(prob, n)
+    cases = ((S.flared_disk_problem(n=8), 1 << 28, 1.0), (S.homogeneous_sphere_problem(), 1 << 16, 1.0),
+             (S.clumpy_problem(n=8), 1 << 24, 1.0), (S.clumpy_problem(n=8, per_order=True), 1 << 24, 1.0),
+             (S.clumpy_problem(n=8), 1 << 22, 1000.0),
+             (S.finite_star_disk_problem(n=8), 1 << 23, 1.0))
+    for prob, n, wb in cases:
+        fb = Q.default_frac_bits(prob, n, wb)
+        per = prob.max_orders if prob.max_orders > 1 and not prob.per_order else 1
+        total = n * per * Q.contribution_bound(prob) * wb
         assert 0 <= fb <= 62
-        assert n * Q.contribution_bound(prob) * prob.max_orders * 2.0 ** fb < 2.0 ** 63
+        assert total * 2.0 ** fb <= 2.0 ** 62
+        assert fb == 62 or total * 2.0 ** (fb + 1) > 2.0 ** 62
+        assert Q.default_frac_bits(prob, 4 * n, wb) <= fb
+
+
+def test_contribution_bound_and_frac_bits_validation(lib):
+    d = _descs()
+    out = C.c_double()
+    assert Q.qmcrt_contribution_bound(d["source"], d["dust"], d["opts"], False) > 0
+    for over in (dict(dust__g=1.0), dict(dust__albedo=-0.5), dict(dust__p_l=2.0)):
+        b = _descs(**over)
+        _expect(Q.ERR_INVALID_ARG, Q.qmcrt_contribution_bound, b["source"], b["dust"], b["opts"], False)
+    b = _descs(opts__max_orders=0)
+    _expect(Q.ERR_INVALID_ARG, Q.qmcrt_contribution_bound, b["source"], b["dust"], b["opts"], True)
+    b = _descs()
+    b["dust"].struct_size = 8
+    _expect(Q.ERR_INVALID_ARG, Q.qmcrt_contribution_bound, b["source"], b["dust"], b["opts"], False)
+    assert lib.qmcrt_contribution_bound(C.byref(d["source"]), C.byref(d["dust"]), C.byref(d["opts"]), 0,
+                                        None) == Q.ERR_INVALID_ARG
+    for wb in (0.5, float("inf"), float("nan")):
+        _expect(Q.ERR_INVALID_ARG, Q.qmcrt_default_frac_bits, d["source"], d["dust"], d["opts"], False, 1 << 20, wb)
+    del out
+
+
+def test_render_single_host_validation(lib):
+    """The host-buffer render rejects bad buffers before anything is enqueued (these
+    calls never reach the GPU)."""
+    d = _descs()
+    io = Q._new(Q.qmcrt_host_io, h_k=None, d_k=None, d_accum=0x1000, d_image=0x2000, h_image=0x3000)
+
+    def call(dd, io_):
+        Q.qmcrt_render_single_host(dd["medium"], dd["source"], dd["dust"], dd["obs"], dd["pts"], dd["opts"], io_,
+                                   40, 1.0, 0)
+    for field in ("d_accum", "d_image", "h_image"):
+        bad = Q.qmcrt_host_io.from_buffer_copy(io)
+        setattr(bad, field, None)
+        _expect(Q.ERR_INVALID_ARG, call, d, bad)
+    bad = Q.qmcrt_host_io.from_buffer_copy(io)
+    bad.struct_size = 16
+    _expect(Q.ERR_INVALID_ARG, call, d, bad)
+    bad = Q.qmcrt_host_io.from_buffer_copy(io)
+    bad.h_k = 0x4000  # a grid for a sphere medium
+    _expect(Q.ERR_INVALID_ARG, call, d, bad)
+    g = _descs(medium__kind=0, medium__d_k=0x5000, medium__nx=4, medium__ny=4, medium__nz=4, medium__pad=8)
+    for a in range(3):
+        g["medium"].lo[a], g["medium"].hi[a] = -1.0, 1.0
+    bad = Q.qmcrt_host_io.from_buffer_copy(io)
+    bad.h_k = 0x4000  # a padded grid needs d_k
+    _expect(Q.ERR_INVALID_ARG, call, g, bad)
+    bad.d_k = 0x5000  # ... distinct from the padded grid
+    _expect(Q.ERR_INVALID_ARG, call, g, bad)
+    for over in BAD_TRACE[:8]:
+        _expect(Q.ERR_INVALID_ARG, call, _descs(**over), io)
 
 
 @pytest.mark.parametrize("g,albedo,p_l", [(0.6, 0.7, 0.5), (-0.4, 1.0, 1.0), (0.0, 0.9, 0.3)])
