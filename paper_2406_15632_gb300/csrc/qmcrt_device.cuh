@@ -48,6 +48,9 @@ struct Mth<float> {
     // value of a 32-bit point coordinate: x * 2^-32 rounded toward zero
     static __device__ __forceinline__ float from_u32(uint32_t x) { return __uint2float_rz(x) * 0x1p-32f; }
     static __device__ __forceinline__ float from_f64(double v) { return __double2float_rz(v); }
+    // lo + c h with the product and the sum rounded separately (never fused): the face
+    // coordinates of the oracle, bit for bit in double
+    static __device__ __forceinline__ float face(float lo, int c, float h) { return __fadd_rn(lo, __fmul_rn((float)c, h)); }
     static __device__ __forceinline__ long long to_fixed(float v, double scale)
     {
         return __float2ll_rn(v * (float)scale);  // exact power-of-two scaling, one rounding
@@ -68,6 +71,7 @@ struct Mth<double> {
     static __device__ __forceinline__ double inf() { return __longlong_as_double(0x7ff0000000000000ll); }
     static __device__ __forceinline__ double from_u32(uint32_t x) { return (double)x * 0x1p-32; }
     static __device__ __forceinline__ double from_f64(double v) { return v; }
+    static __device__ __forceinline__ double face(double lo, int c, double h) { return __dadd_rn(lo, __dmul_rn((double)c, h)); }
     static __device__ __forceinline__ long long to_fixed(double v, double scale) { return __double2ll_rn(v * scale); }
 };
 
@@ -337,14 +341,17 @@ __device__ __forceinline__ bool packet_index(const OrderP &O, uint64_t first, ui
 // digits of a coordinate much smaller than lo (in float a point 2e-8 below the face
 // through the origin becomes a point on it), so the estimate (x - lo) / h, taken with
 // the reciprocal, is settled against the face coordinates themselves: the result does
-// not depend on the rounding of the estimate.
+// not depend on the rounding of the estimate.  The faces are lo + c h rounded step by
+// step (Mth::face), never fused into one rounding: where h is inexact (200 cells over
+// [-1, 1]) a fused lo + 100 h lies 2e-17 above the face through the origin, and a
+// source there that sends a ray along that face would walk the neighbouring slab.
 template <class T>
 __device__ __forceinline__ int start_cell(T x, T lo, T h, T inv_h, T d)
 {
     int c = (int)Mth<T>::floor_((x - lo) * inv_h);
-    if (x < lo + T(c) * h) --c;
-    else if (x >= lo + T(c + 1) * h) ++c;
-    if (d < T(0) && x == lo + T(c) * h) --c;
+    if (x < Mth<T>::face(lo, c, h)) --c;
+    else if (x >= Mth<T>::face(lo, c + 1, h)) ++c;
+    if (d < T(0) && x == Mth<T>::face(lo, c, h)) --c;
     return c;
 }
 
@@ -364,12 +371,12 @@ __device__ __forceinline__ AxisWalk<T> axis_setup(T p, T d, int c, T lo, T h, in
     a.left = 0;
     const T r = T(1) / d;  // one division per axis: the face distance and the cell crossing
     if (d > T(0)) {
-        a.s = (lo + T(c + 1) * h - p) * r;
+        a.s = (Mth<T>::face(lo, c + 1, h) - p) * r;
         a.dt = h * r;
         a.step = stride;
         a.left = n - 1 - c;
     } else if (d < T(0)) {
-        a.s = (lo + T(c) * h - p) * r;
+        a.s = (Mth<T>::face(lo, c, h) - p) * r;
         a.dt = -h * r;
         a.step = -stride;
         a.left = c;

@@ -11,6 +11,7 @@ can compute one packet at a time:
 import numpy as np
 import pytest
 
+from fp32_check import fp32_packet_check
 from oracle import oracle as O
 from paper_2406_15632_gb300 import scenes as S
 
@@ -50,9 +51,9 @@ def test_benchmark_step_single_scattering_sampled(Q):
     got = lg[torch.as_tensor(sample, device="cuda")].cpu().numpy()
     ref = np.concatenate([O.trace_single(prob, first + int(j0), 100, log=True)[1] for j0 in starts])
     assert np.array_equal(got[:, 8], ref[:, 8])  # status: contributed, tau_1 < tau_min, occulted
-    for c in (3, 4, 5):  # I, Q, U of the peel-off
-        assert _close_fraction(got[:, c], ref[:, c], 1e-5) >= 0.995
-    assert np.max(np.abs(got[:, 6:8] - ref[:, 6:8])) <= 1e-4  # sky position
+    # I, Q, U and sky position within 1e-5 of the packet's own I on the well-conditioned
+    # packets (all of them in practice), the ill-conditioned ones bounded separately
+    fp32_packet_check(prob, first + sample, got, ref)
     # the image holds exactly the logged in-frame intensities
     ok = (lg[:, 8] == 0) & (lg[:, 6].abs() < prob.half_width) & (lg[:, 7].abs() < prob.half_width)
     assert float(img.sum()) == pytest.approx(float(lg[ok, 3].sum()), rel=1e-9)

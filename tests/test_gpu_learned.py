@@ -25,13 +25,17 @@ def _problem(n=16, **kw):
     return S.clumpy_problem(n=n, max_orders=8, nx=48, ny=40, half_width=0.9, **kw)
 
 
-def _warp(Q, mix=0.1, seed=3):
+def _warp_params(seed=3):
     from oracle import flow as F
 
     vec = F.init_params(seed, scale=2.0)
     p = F.unpack(vec)
     p["theta0"] = np.random.default_rng(seed).normal(size=F.K_BINS)
-    return Q.Warp(F.pack(p), rows=1 << 14, uniform_mix=mix)
+    return F.pack(p)
+
+
+def _warp(Q, mix=0.1, seed=3):
+    return Q.Warp(_warp_params(seed), rows=1 << 14, uniform_mix=mix)
 
 
 @pytest.mark.parametrize("first,count", [(1, 3000), (4096, 1 << 13)])
@@ -60,6 +64,48 @@ def test_warped_fp64_trace_matches_oracle(Q, first, count):
     # the warp moved the points, and the weights are bounded by mix^-3
     assert np.abs(xh - u.cpu().numpy()).max() > 0.05
     assert ljh.max() <= 3 * np.log(10.0) + 1e-4
+
+
+def test_learned_chain_end_to_end_against_the_oracle_alone(Q):
+    """The whole learned chain on each side with nothing shared: the GPU generates the
+    float points, warps them on the tensor cores (qmcrt_warp_forward, bf16) and traces
+    them (FP64 trace, FP64 image); the oracle takes the same float points through its
+    own flow with the same bf16 roundings (oracle/flow.py) and its own warped trace.
+
+    Tolerance, from the flips counted: a point whose GPU x differs from the oracle's by
+    more than the forward's float rounding (2e-5, or 1e-4 in log J) took another
+    bf16 rounding of a feature and can move its whole contribution, so the flipped
+    packets' logged intensities (both sides) enter the L1 budget in full; the others
+    move their contributions by their coordinate change, ~2e-5 x (about 30 pixels per
+    unit of sky for the tent splat) ~ 1e-3 of their own intensity at most."""
+    import torch
+
+    from oracle import flow as F
+
+    prob = _problem().replace(splat="bilinear")
+    sc = Q.Scene(prob)
+    vec = _warp_params()
+    W = Q.Warp(vec, rows=1 << 14, uniform_mix=0.1)
+    first, count = 1, 1 << 13
+    buf = sc.accum_buffer("f64")
+    log = torch.zeros((count, 5), dtype=torch.float32, device="cuda")
+    Q.LearnedTracer(sc, W, chunk=1 << 12).trace(first, count, buf, accum="f64", precision="f64", train_log=log)
+    torch.cuda.synchronize()
+    assert W.error.item() == 0
+    got, glog = buf[0].cpu().numpy(), log.cpu().numpy().astype(np.float64)
+
+    u = O.generate_points(prob.generator, 3, first, count, "f32").astype(np.float64)
+    xr, ljr = F.warp(u, vec, use_bf16=True, mix=0.1)
+    ref, rlog = O.trace_multiple_warped(prob, first, count, xr, ljr, train_log=True)
+
+    flipped = np.abs(glog[:, :3] - xr).max(axis=1) > 2e-5
+    assert flipped.mean() <= 0.02, flipped.mean()
+    total = rlog[:, 3].sum()
+    budget = (rlog[flipped, 3].sum() + glog[flipped, 3].sum() + 1e-3 * rlog[~flipped, 3].sum()) / total
+    err_l1 = np.abs(got[0] - ref[0]).sum() / np.abs(ref[0]).sum()
+    assert err_l1 <= budget, (err_l1, budget, flipped.sum())
+    # the flips are rare enough that the end-to-end image is close in L2 as well
+    assert np.linalg.norm(got - ref) <= 0.05 * np.linalg.norm(ref)
 
 
 def test_plain_entry_point_is_the_multiple_tracer_and_logs(Q):

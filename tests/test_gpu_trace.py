@@ -6,18 +6,22 @@ Tolerances, derived from the arithmetic:
     distances on the GPU) and by libm ulps, ~1e-15 per operation over a few hundred
     operations per packet.  Pixel-boundary flips need a position error of ~1e-15 and
     do not occur at these sizes.
-  * FP32 path: per packet, intensity and polarization within 1e-5 of max(I, mean I)
-    and the sky position within 1e-5 (units of the medium) for >= 99.9 % of packets
-    (the reasons for both qualifications are in _fp32_packet_check).  Images
-    binned with the tent (bilinear) splat are continuous in position and agree to
-    relative L2 <= 1e-5; with nearest-pixel binning a packet near a pixel edge can
-    change pixels, so that image is compared through the packet log instead.
+  * FP32 path: per packet, intensity, polarization and sky position within 1e-5 of the
+    packet's own I (and of the medium's size) for >= 99.99 % of the well-conditioned
+    packets; nearly empty rays and packets scattering in cells of low extinction are
+    ill-conditioned in float arithmetic and bounded separately (fp32_check.py says
+    how and why).  Images binned with the tent (bilinear) splat are continuous in
+    position and agree to relative L2 <= 1e-5; with nearest-pixel binning a packet
+    near a pixel edge can change pixels, so that image is compared through the packet
+    log instead.  The clumpy envelope's optically thick cells are the stated exception
+    (FP32_PACKET_OPTS, FP32_IMAGE_TOL).
 """
 import math
 
 import numpy as np
 import pytest
 
+from fp32_check import fp32_packet_check
 from oracle import oracle as O
 from paper_2406_15632_gb300 import scenes as S
 
@@ -74,6 +78,8 @@ SINGLE_CASES = {
     "clumpy_single": S.clumpy_problem(n=32, max_orders=1, nx=64, ny=64),
     "random_grid_kscale": S.Problem(grid=S.random_grid(7, seed=4), kscale=0.37, albedo=0.7, g=-0.3, p_l=0.8,
                                     theta_obs=2.0, phi_obs=4.0, half_width=1.3, nx=33, ny=29),
+    # the paper's third geometry (Sec. 5): 200^3 fractal cloud, observer at 60 degrees
+    "fractal_cloud": S.fractal_cloud_problem(),
 }
 
 
@@ -100,39 +106,24 @@ def test_trace_single_fp64_packet_log(Q, first):
     assert np.allclose(lg[:, :8], ref[:, :8], rtol=1e-11, atol=1e-13)
 
 
-def _fp32_packet_check(lg, ref, tol=1e-5, frac=0.999):
-    """FP32 packet log against the FP64 oracle log.  Intensity and polarization are
-    compared in units of max(I, mean I): a packet far fainter than the mean is
-    dominated by a short segment clipping one dense cell, whose length moves by
-    ~(path / segment) x 1e-7 when the direction is rounded to float, and it carries no
-    weight in the image.  A fraction frac of packets must lie within tol in
-    intensity, polarization and sky position, and every packet within 1e-3: the rest
-    scatter in cells of very low density, where a rounding of 1e-7 in optical depth
-    moves the scattering point by 1e-7 / k and with it the light that reaches the
-    observer."""
-    assert np.mean(lg[:, 8] != ref[:, 8]) < 1e-3
-    ok = np.where((ref[:, 8] == 0) & (lg[:, 8] == 0))[0]
-    I = ref[ok, 3]
-    scale = np.maximum(I, I.mean())
-    err = np.max(np.abs(lg[ok, 3:6] - ref[ok, 3:6]), axis=1) / scale
-    dxy = np.max(np.abs(lg[ok, 6:8] - ref[ok, 6:8]), axis=1)
-    good = (err <= tol) & (dxy <= tol)
-    w = int(np.argmax(err))
-    msg = (f"within {tol:g}: {good.mean():.5f}; worst intensity packet {ok[w]} err {err[w]:.3e}; "
-           f"worst sky offset {dxy.max():.3e}")
-    assert good.mean() >= frac, msg
-    assert err.max() <= 1e-3 and dxy.max() <= 1e-3, msg
-    return good.mean()
+# The optically thick exception, stated per medium: the clumpy envelope on 32^3 has
+# cells of optical depth up to 7.7 (k up to 124), where float face positions (~1e-7 of
+# the medium) shift a dense cell's depth by k x 1e-7 ~ 1e-5; there 99.8 % of the
+# well-conditioned packets meet 1e-5 of their own intensity (measured 99.87 %, all
+# within 4e-4), and a few packets that scatter in a gap between clumps and escape
+# outshine thousands, so the ill-conditioned share is not bounded.  (The fractal cloud,
+# with cells of optical depth up to 39, is compared by image only.)
+FP32_PACKET_OPTS = {"clumpy_single": dict(frac=0.998, ill_share=None)}
 
 
 @pytest.mark.parametrize("name", ["disk_sobol", "disk_halton", "star_inverse", "star_direct", "random_grid_kscale",
                                   "sphere_polarized", "clumpy_single"])
 def test_trace_single_fp32_packets_within_1e5(Q, name):
     prob = SINGLE_CASES[name]
-    N = 1 << 14
+    N = 1 << 15
     _, lg = gpu_image(Q, prob, N, precision="f32", log=True)
     _, ref = O.trace_single(prob, 1, N, log=True)
-    _fp32_packet_check(lg, ref)
+    fp32_packet_check(prob, np.arange(1, N + 1), lg, ref, **FP32_PACKET_OPTS.get(name, {}))
 
 
 # Relative L2 error of FP32 images against the FP64 oracle (tent splat, 2^16 packets).
@@ -141,7 +132,10 @@ def test_trace_single_fp32_packets_within_1e5(Q, name):
 # shift optical depths by ~k x 1e-7 per dense boundary, and a packet that scatters just
 # beyond dense clumps carries the shift, divided by the low density where it stops,
 # into its sky position; a handful of such bright packets dominate the image norm.
-FP32_IMAGE_TOL = {"disk_bilinear": 1e-5, "sphere_polarized": 1e-5, "star_inverse": 1e-5, "clumpy_single": 5e-3}
+# The fractal cloud (200^3, cells of optical depth up to 39) carries the same conditioning
+# (measured 1.0e-4 at 2^15 packets).
+FP32_IMAGE_TOL = {"disk_bilinear": 1e-5, "sphere_polarized": 1e-5, "star_inverse": 1e-5, "clumpy_single": 5e-3,
+                  "fractal_cloud": 5e-4}
 
 
 @pytest.mark.parametrize("name", list(FP32_IMAGE_TOL))
@@ -183,6 +177,8 @@ MULTI_CASES = {
                                         emit_order="direct", generator="sobol_owen", seed=2),
     "clumpy_faure": MULTI.replace(per_order=False, generator="faure"),
     "sphere_isotropic": S.homogeneous_sphere_problem(sphere_k=0.8, max_orders=12, g=0.0, p_l=0.3, per_order=True),
+    # the fractal cloud of Sec. 5 with four orders (the paper's multiple-scattering runs)
+    "fractal_4_orders": S.fractal_cloud_problem(max_orders=4, per_order=True, nx=64, ny=64),
 }
 
 
@@ -294,9 +290,38 @@ def test_full_size_single_scattering_sampled(Q):
     rng = np.random.default_rng(1)
     sample = np.unique(rng.integers(0, N, 3000))
     ref = np.concatenate([O.trace_single(prob, 1 + int(j), 1, log=True)[1] for j in sample])
-    _fp32_packet_check(lg[sample], ref, frac=0.995)
+    fp32_packet_check(prob, 1 + sample, lg[sample], ref)
     ok = lg[:, 8] == 0
     sx, sy = lg[ok, 6], lg[ok, 7]
     inside = (np.abs(sx) < 1) & (np.abs(sy) < 1)
     assert img[0, 0].sum() == pytest.approx(lg[ok, 3][inside].sum(), rel=1e-9)
     torch.cuda.synchronize()
+
+
+def test_host_buffer_render_equals_the_device_path(Q):
+    """qmcrt_render_single_host (the end-to-end call for host-resident grids and images):
+    the image equals the device-resident path's bit for bit, follows a changed host grid
+    on the next call, and needs no grid for the analytic sphere."""
+    import torch
+
+    prob = DISK32
+    N = 1 << 14
+    R = Q.HostRenderer(prob, N)
+    host_grid = torch.from_numpy(prob.grid.copy()).pin_memory()
+    host_out = torch.full((1, 3, prob.ny, prob.nx), float("nan"), dtype=torch.float64).pin_memory()
+    R(host_grid, 1, N, host_out)
+    torch.cuda.synchronize()
+    ref = Q.render(prob, N, 1, frac_bits=R.frac_bits).cpu()
+    assert torch.equal(host_out, ref)
+    assert R.input_bytes() == prob.grid.nbytes and R.output_bytes() == host_out.numel() * 8
+    host_grid.mul_(0.5)  # another grid: the next call copies it in
+    R(host_grid, 1, N, host_out)
+    torch.cuda.synchronize()
+    half = prob.replace(grid=(prob.grid * np.float32(0.5)).astype(np.float32))
+    assert torch.equal(host_out, Q.render(half, N, 1, frac_bits=R.frac_bits).cpu())
+    sph = SINGLE_CASES["sphere_c1"]
+    Rs = Q.HostRenderer(sph, 4096)
+    out_s = torch.zeros((1, 3, sph.ny, sph.nx), dtype=torch.float64).pin_memory()
+    Rs(None, 1, 4096, out_s)
+    torch.cuda.synchronize()
+    assert torch.equal(out_s, Q.render(sph, 4096, 1, frac_bits=Rs.frac_bits).cpu())
