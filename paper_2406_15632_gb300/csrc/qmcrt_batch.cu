@@ -73,6 +73,7 @@ __device__ __forceinline__ void set_instance(TraceP<T> &P, const TraceP<T> &base
     P.obs.ey[0] = (T)(-ct * cp);
     P.obs.ey[1] = (T)(-ct * sp);
     P.obs.ey[2] = (T)st;
+    for (int a = 0; a < 3; ++a) P.obs.inv_k[a] = T(1) / P.obs.k[a];
     // dust
     P.dust.albedo = (T)I.albedo;
     P.dust.g = (T)I.g;

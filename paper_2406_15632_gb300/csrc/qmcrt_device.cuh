@@ -361,15 +361,16 @@ struct AxisWalk {
     int step, left;
 };
 
+// r = 1 / d, computed once per direction by the caller (the forced step's two walks
+// share it; a launch's observer direction has it precomputed on the host).
 template <class T>
-__device__ __forceinline__ AxisWalk<T> axis_setup(T p, T d, int c, T lo, T h, int n, int stride)
+__device__ __forceinline__ AxisWalk<T> axis_setup(T p, T d, T r, int c, T lo, T h, int n, int stride)
 {
     AxisWalk<T> a;
     a.s = Mth<T>::inf();
     a.dt = T(0);
     a.step = 0;
     a.left = 0;
-    const T r = T(1) / d;  // one division per axis: the face distance and the cell crossing
     if (d > T(0)) {
         a.s = (Mth<T>::face(lo, c + 1, h) - p) * r;
         a.dt = h * r;
@@ -425,8 +426,8 @@ constexpr int WALK_UNROLL = 4;
 static_assert(QMCRT_MIN_PAD >= WALK_UNROLL, "a padded walk steps up to WALK_UNROLL - 1 cells past the first sentinel");
 
 template <class T, bool TARGET>
-__device__ __forceinline__ bool grid_walk(const MediumP<T> &G, const T p[3], const T d[3], T target_raw, T &tau_raw,
-                                          T &t_out)
+__device__ __forceinline__ bool grid_walk(const MediumP<T> &G, const T p[3], const T d[3], const T r[3], T target_raw,
+                                          T &tau_raw, T &t_out)
 {
     const int cx = start_cell(p[0], G.lo[0], G.h[0], G.inv_h[0], d[0]);
     const int cy = start_cell(p[1], G.lo[1], G.h[1], G.inv_h[1], d[1]);
@@ -435,9 +436,9 @@ __device__ __forceinline__ bool grid_walk(const MediumP<T> &G, const T p[3], con
     t_out = T(0);
     if (!walkable(p, d)) return false;
     if (cx < 0 || cx >= G.n[0] || cy < 0 || cy >= G.n[1] || cz < 0 || cz >= G.n[2]) return false;
-    AxisWalk<T> X = axis_setup(p[0], d[0], cx, G.lo[0], G.h[0], G.n[0], G.stride[0]);
-    AxisWalk<T> Y = axis_setup(p[1], d[1], cy, G.lo[1], G.h[1], G.n[1], G.stride[1]);
-    AxisWalk<T> Z = axis_setup(p[2], d[2], cz, G.lo[2], G.h[2], G.n[2], G.stride[2]);
+    AxisWalk<T> X = axis_setup(p[0], d[0], r[0], cx, G.lo[0], G.h[0], G.n[0], G.stride[0]);
+    AxisWalk<T> Y = axis_setup(p[1], d[1], r[1], cy, G.lo[1], G.h[1], G.n[1], G.stride[1]);
+    AxisWalk<T> Z = axis_setup(p[2], d[2], r[2], cz, G.lo[2], G.h[2], G.n[2], G.stride[2]);
     if (X.step == 0 && Y.step == 0 && Z.step == 0) return false;
     int idx = cx * G.stride[0] + cy * G.stride[1] + cz * G.stride[2];
     const float *__restrict__ K = G.k;
@@ -525,8 +526,8 @@ __device__ __forceinline__ bool grid_walk(const MediumP<T> &G, const T p[3], con
 // total; the march tests the batch sum against the remaining depth and only then
 // looks for the stopping cell inside the batch.
 template <class T, bool TARGET>
-__device__ __forceinline__ bool grid_walk_padded(const MediumP<T> &G, const T p[3], const T d[3], T target_raw,
-                                                 T &tau_raw, T &t_out)
+__device__ __forceinline__ bool grid_walk_padded(const MediumP<T> &G, const T p[3], const T d[3], const T r[3],
+                                                 T target_raw, T &tau_raw, T &t_out)
 {
     const int cx = start_cell(p[0], G.lo[0], G.h[0], G.inv_h[0], d[0]);
     const int cy = start_cell(p[1], G.lo[1], G.h[1], G.inv_h[1], d[1]);
@@ -535,16 +536,22 @@ __device__ __forceinline__ bool grid_walk_padded(const MediumP<T> &G, const T p[
     t_out = T(0);
     if (!walkable(p, d)) return false;
     if (cx < 0 || cx >= G.n[0] || cy < 0 || cy >= G.n[1] || cz < 0 || cz >= G.n[2]) return false;
-    AxisWalk<T> X = axis_setup(p[0], d[0], cx, G.lo[0], G.h[0], G.n[0], G.stride[0]);
-    AxisWalk<T> Y = axis_setup(p[1], d[1], cy, G.lo[1], G.h[1], G.n[1], G.stride[1]);
-    AxisWalk<T> Z = axis_setup(p[2], d[2], cz, G.lo[2], G.h[2], G.n[2], G.stride[2]);
+    AxisWalk<T> X = axis_setup(p[0], d[0], r[0], cx, G.lo[0], G.h[0], G.n[0], G.stride[0]);
+    AxisWalk<T> Y = axis_setup(p[1], d[1], r[1], cy, G.lo[1], G.h[1], G.n[1], G.stride[1]);
+    AxisWalk<T> Z = axis_setup(p[2], d[2], r[2], cz, G.lo[2], G.h[2], G.n[2], G.stride[2]);
     if (X.step == 0 && Y.step == 0 && Z.step == 0) return false;
-    int idx = (cx + G.pad) * G.stride[0] + (cy + G.pad) * G.stride[1] + (cz + G.pad) * G.stride[2];
-    const float *__restrict__ K = G.k;
+    // Cells are addressed by unsigned 32-bit byte offsets from the grid's base (a load needs
+    // no index scaling per cell); the host admits padded grids of at most 2^30 cells, so
+    // every offset the walk reaches is below 2^32 (steps are added modulo 2^32).
+    unsigned idx = 4u * (unsigned)((cx + G.pad) * G.stride[0] + (cy + G.pad) * G.stride[1] + (cz + G.pad) * G.stride[2]);
+    X.step *= 4;
+    Y.step *= 4;
+    Z.step *= 4;
+    const char *__restrict__ K = (const char *)G.k;
     T t = T(0), acc = TARGET ? target_raw : T(0), comp = T(0), t_last = T(0);
     for (;;) {
         T L[WALK_UNROLL];
-        int cell[WALK_UNROLL];
+        unsigned cell[WALK_UNROLL];
 #pragma unroll
         for (int u = 0; u < WALK_UNROLL; ++u) {
             cell[u] = idx;
@@ -568,7 +575,7 @@ __device__ __forceinline__ bool grid_walk_padded(const MediumP<T> &G, const T p[
         unsigned sign = 0u;
 #pragma unroll
         for (int u = 0; u < WALK_UNROLL; ++u) {
-            kf[u] = __ldg(K + cell[u]);
+            kf[u] = __ldg((const float *)(K + cell[u]));
             sign |= __float_as_uint(kf[u]);
         }
         T dtau[WALK_UNROLL];
@@ -632,24 +639,41 @@ __device__ __forceinline__ T sphere_exit(const T p[3], const T d[3], T r)
     return Mth<T>::max_(-b + Mth<T>::sqrt_(disc), T(0));
 }
 
-// Optical depth from p along d to the edge of the medium.
+// The reciprocals 1 / d of a direction's components (the walks' face distances).
 template <class T>
-__device__ __forceinline__ T tau_to_edge(const MediumP<T> &G, const T p[3], const T d[3])
+__device__ __forceinline__ void reciprocals(const T d[3], T r[3])
+{
+    r[0] = T(1) / d[0];
+    r[1] = T(1) / d[1];
+    r[2] = T(1) / d[2];
+}
+
+// Optical depth from p along d (r = 1 / d) to the edge of the medium.
+template <class T>
+__device__ __forceinline__ T tau_to_edge(const MediumP<T> &G, const T p[3], const T d[3], const T r[3])
 {
     if (G.kind == QMCRT_MEDIUM_SPHERE) {
         if (dot3(p, p) > G.sph_r * G.sph_r) return T(0);
         return G.sph_k * sphere_exit(p, d, G.sph_r);
     }
     T raw, t;
-    if (G.pad) grid_walk_padded<T, false>(G, p, d, T(0), raw, t);
-    else grid_walk<T, false>(G, p, d, T(0), raw, t);
+    if (G.pad) grid_walk_padded<T, false>(G, p, d, r, T(0), raw, t);
+    else grid_walk<T, false>(G, p, d, r, T(0), raw, t);
     return raw * G.kscale;
 }
 
-// Move pos along d through optical depth tau; false if the ray leaves first (pos is
-// then the far end of the last nonempty segment).
 template <class T>
-__device__ __forceinline__ bool march(const MediumP<T> &G, T pos[3], const T d[3], T tau)
+__device__ __forceinline__ T tau_to_edge(const MediumP<T> &G, const T p[3], const T d[3])
+{
+    T r[3];
+    reciprocals(d, r);
+    return tau_to_edge(G, p, d, r);
+}
+
+// Move pos along d (r = 1 / d) through optical depth tau; false if the ray leaves first
+// (pos is then the far end of the last nonempty segment).
+template <class T>
+__device__ __forceinline__ bool march(const MediumP<T> &G, T pos[3], const T d[3], const T r[3], T tau)
 {
     T t;
     bool hit;
@@ -659,8 +683,8 @@ __device__ __forceinline__ bool march(const MediumP<T> &G, T pos[3], const T d[3
         t = hit ? tau / G.sph_k : s;
     } else {
         T raw;
-        hit = G.pad ? grid_walk_padded<T, true>(G, pos, d, tau * G.inv_kscale, raw, t)
-                    : grid_walk<T, true>(G, pos, d, tau * G.inv_kscale, raw, t);
+        hit = G.pad ? grid_walk_padded<T, true>(G, pos, d, r, tau * G.inv_kscale, raw, t)
+                    : grid_walk<T, true>(G, pos, d, r, tau * G.inv_kscale, raw, t);
     }
     pos[0] += t * d[0];
     pos[1] += t * d[1];
@@ -668,15 +692,25 @@ __device__ __forceinline__ bool march(const MediumP<T> &G, T pos[3], const T d[3
     return hit;
 }
 
+template <class T>
+__device__ __forceinline__ bool march(const MediumP<T> &G, T pos[3], const T d[3], T tau)
+{
+    T r[3];
+    reciprocals(d, r);
+    return march(G, pos, d, r, tau);
+}
+
 // Forced scattering (Sec. 3.2): weight 1 - e^{-tau_1}, depth -ln[1 - w (1 - e^{-tau_1})].
 template <class T>
 __device__ __forceinline__ bool forced_step(const TraceP<T> &P, T pos[3], const T d[3], T w, T &W1)
 {
-    const T tau1 = tau_to_edge(P.med, pos, d);
+    T r[3];  // both walks run along d
+    reciprocals(d, r);
+    const T tau1 = tau_to_edge(P.med, pos, d, r);
     if (!(tau1 >= P.tau_min)) return false;
     W1 = -Mth<T>::expm1_(-tau1);
     const T tau = -Mth<T>::log1p_(-w * W1);
-    march(P.med, pos, d, tau);
+    march(P.med, pos, d, r, tau);
     return true;
 }
 
@@ -833,7 +867,7 @@ __device__ __forceinline__ bool peel_unpolarized(const TraceP<T> &P, const ObsP<
     x = dot3(pos, O.ex);
     y = dot3(pos, O.ey);
     if (occulted(P, O, pos)) return false;
-    const T tau_obs = tau_to_edge(P.med, pos, O.k);
+    const T tau_obs = tau_to_edge(P.med, pos, O.k, O.inv_k);
     const T mu = dot3(d, O.k);
     const T f = W0 * Mth<T>::exp_(-tau_obs) * hg_p11(P.dust, mu) * T(0.07957747154594767);  // 1/(4 pi)
     const T dx = dot3(d, O.ex), dy = dot3(d, O.ey);
@@ -852,7 +886,7 @@ __device__ __forceinline__ bool peel_polarized(const TraceP<T> &P, const ObsP<T>
     x = dot3(pos, O.ex);
     y = dot3(pos, O.ey);
     if (occulted(P, O, pos)) return false;
-    const T tau_obs = tau_to_edge(P.med, pos, O.k);
+    const T tau_obs = tau_to_edge(P.med, pos, O.k, O.inv_k);
     const T mu = dot3(n, O.k);
     const T inv1pm2 = T(1) / (T(1) + mu * mu);
     const T r12 = -P.dust.p_l * (T(1) - mu * mu) * inv1pm2;

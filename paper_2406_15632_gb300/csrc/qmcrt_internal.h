@@ -57,6 +57,7 @@ struct DustP {
 template <class T>
 struct ObsP {
     T k[3], ex[3], ey[3];  // direction toward the observer and sky axes
+    T inv_k[3];            // 1 / k (the peel-off walk's face distances), rounded as the device rounds T(1) / k
     T hw;                  // half width of the image
     T pix_x, pix_y;        // pixels per unit sky length: n / (2 hw)
     int nx, ny, splat;
