@@ -298,10 +298,24 @@ def run_batched():
     t_seq = e0.elapsed_time(e1)
     same = bool(torch.equal(B.accum, ref))
     n = B.packets()
+    # time to error: both forms give the same image per instance, so at each instance's
+    # budget they reach the same error; that error is estimated per instance from two
+    # independently Owen-scrambled batches (the replicate spread, no reference)
+    reps = []
+    for seed in (1, 2):
+        R = Q.Batch(prob.replace(generator="sobol_owen", seed=seed), inst, scene=sc, **cfg)
+        R.run()
+        torch.cuda.synchronize()
+        reps.append(R.out[:, 0].clone())
+        del R
+    per = [_replicate_error([reps[0][i], reps[1][i]]) for i in range(len(inst))]
     return {"workload": "flared disk 256^3, finite star R*=0.05 u=0.6 inverse order, 256 instances",
             "packets": n, "graph_ms": t_graph, "sequential_ms": t_seq, "packets_per_s": n / (t_graph / 1e3),
             "sequential_packets_per_s": n / (t_seq / 1e3), "speedup_at_equal_images": t_seq / t_graph,
-            "identical_images": same, "config": cfg, "tuned_over": best.get("tried")}
+            "identical_images": same, "config": cfg, "tuned_over": best.get("tried"),
+            "time_to_error": {"per_instance_rms_median": statistics.median(per), "per_instance_rms_max": max(per),
+                              "error": "RMS relative of each instance's I image from two Owen-scrambled batches",
+                              "batched_ms": t_graph, "separate_ms": t_seq, "speedup": t_seq / t_graph}}
 
 
 def _timed(fn):
@@ -367,33 +381,52 @@ def _ladder(render, ladder, ref, ref_err):
     return rows
 
 
-def _tte_summary(arms, targets, overhead_ms=None):
+def _tte_summary(arms, targets, overhead_ms=None, key="rms_minus_reference"):
     """Per target error and arm: render time at that error (log-log interpolation on the
     ladder, or extrapolation along its last two points, flagged) plus the arm's fixed
-    overhead (training), in ms."""
+    overhead (training), in ms.  key: the ladder rows' error column."""
     overhead_ms = overhead_ms or {}
     out = {}
     for tgt in targets:
         row = {}
         for name, rows in arms.items():
-            pts = [(r["ms"], r["rms_minus_reference"]) for r in rows if r["rms_minus_reference"] > 0]
+            pts = [(r["ms"], r[key]) for r in rows if r[key] > 0]
             t, extrap = _time_at(pts, tgt) if len(pts) >= 2 else (None, True)
             row[name] = {"ms": None if t is None else t + overhead_ms.get(name, 0.0), "extrapolated": extrap}
         out[f"{tgt:g}"] = row
     return out
 
 
-def run_time_to_error_learned(ladder=(20, 22, 24, 26, 28), ref_log2=28, ref_seeds=tuple(range(101, 109)),
-                              n_log_log2=20, epochs=2, batch_log2=16, lr=2e-2, mix=0.1, weight="l2"):
+SOBOL_BLOCK_LOG2 = 31  # a Sobol point set has 2^32 points: renders above 2^31 packets use several scrambles
+
+
+def _replicate_error(imgs):
+    """RMS relative error of one render, estimated from R independent randomized renders
+    (Owen scrambles or PRNG seeds): sqrt(sum_r ||A_r - mean||^2 / (R - 1)) / ||mean||, no
+    reference image needed (the replicates' mean is unbiased, their spread the error)."""
+    import torch
+
+    stack = torch.stack(imgs)
+    mean = stack.mean(0)
+    var = ((stack - mean) ** 2).sum() / (len(imgs) - 1)
+    return float(var.sqrt() / mean.norm())
+
+
+def run_time_to_error_learned(ladder=(20, 22, 24, 26, 28), mc_ladder=None, replicates=2, n_log_log2=20, epochs=2,
+                              batch_log2=16, lr=2e-2, mix=0.1, weight="l2", targets=(0.05, 0.03, 1e-2, 1e-3),
+                              chunk_log2=22):
     """Clumpy envelope (128^3, total radial tau 5, 20 orders, roulette at 1e-4, 512x512
-    I/Q/U): wall time to a fixed RMS error of the I image for plain QMC (Sobol), the
-    learned proposal (warp trained on the tracer's own log of 2^20 plain packets, each
+    I/Q/U): wall time to a fixed RMS error of the I image for plain QMC, the learned
+    proposal (warp trained on the tracer's own log of 2^n_log_log2 plain packets, each
     weighted by the L2 norm of its in-image contributions -- the density that minimises
     the summed pixel variance is proportional to that norm; logging and training time
-    are added to every ladder point) and Philox MC.  All arms
-    accumulate in FP64.  The reference is the mean of four Owen-scrambled Sobol images
-    of 2^ref_log2 packets with independent seeds; its own estimated error is
-    subtracted in quadrature from each measured error."""
+    are added to every ladder point) and Philox MC, all on the wavefront tracer with FP64
+    accumulation.  Every arm is randomized (Owen-scrambled Sobol with independent seeds,
+    the learned warp applied to those points; Philox keys) and its error at N packets is
+    estimated from `replicates` independent renders of N packets (_replicate_error): no
+    converged reference is needed, so the ladder can reach the 1e-3 target.  A render
+    of N > 2^31 packets is N / 2^31 independently scrambled point sets of 2^31 points
+    (the upper half of each 2^32-point Sobol set), averaged."""
     import torch
 
     from paper_2406_15632_gb300 import qmcrt as Q
@@ -401,52 +434,75 @@ def run_time_to_error_learned(ladder=(20, 22, 24, 26, 28), ref_log2=28, ref_seed
 
     prob = S.clumpy_problem(n=128)
     sc = Q.Scene(prob)
-    ref, ref_err, ref_n = _reference_image(Q, prob, sc.grid, ref_log2, ref_seeds, "f64")
-    mc_sc = Q.Scene(prob.replace(generator="philox", seed=7), grid_device=sc.grid)
-    plain = Q.LearnedTracer(sc, None, wavefront=True)
-    mc = Q.LearnedTracer(mc_sc, None, wavefront=True)
+    chunk = 1 << chunk_log2
+    scenes = {}
 
-    # training: log 2^20 plain packets (points 1 .. 2^20), minibatch Adam on the log
-    # (2^20 to 2^23 logged packets, one to four epochs, learning rates 3e-3 to 3e-2 all
-    # gave the same error at equal packets, within 3 %: the smallest budget is kept)
+    def scene(gen, seed):
+        if (gen, seed) not in scenes:
+            scenes[(gen, seed)] = Q.Scene(prob.replace(generator=gen, seed=seed), grid_device=sc.grid)
+        return scenes[(gen, seed)]
+
+    # training: log 2^n_log_log2 plain packets (unscrambled Sobol, points 1 ..), minibatch
+    # Adam on the log (2^20 to 2^23 logged packets, one to four epochs, learning rates
+    # 3e-3 to 3e-2 all gave the same error at equal packets, within 3 %)
     n_log = 1 << n_log_log2
     log = torch.zeros((n_log, 5), dtype=torch.float32, device="cuda")
-    _, ms_log = _timed(lambda: plain.trace(1, n_log, sc.accum_buffer("f64"), train_log=log))
+    logger = Q.LearnedTracer(sc, None, chunk=min(chunk, n_log), wavefront=True)
+    _, ms_log = _timed(lambda: logger.trace(1, n_log, sc.accum_buffer("f64"), train_log=log))
+    del logger
     W = Q.Warp(seed=2, uniform_mix=mix)
     xs, ws = log[:, :3].contiguous(), log[:, 4 if weight == "l2" else 3].contiguous()
     losses, ms_train = _timed(lambda: W.train(xs, ws, epochs=epochs, batch=1 << batch_log2, lr=lr))
-    learned = Q.LearnedTracer(sc, W, wavefront=True)
+    del log, xs, ws
 
-    def renderer(tracer, s):
-        buf = s.accum_buffer("f64")
-        out = torch.empty((1, 3, prob.ny, prob.nx), dtype=torch.float64, device="cuda")
+    out = torch.empty((1, 3, prob.ny, prob.nx), dtype=torch.float64, device="cuda")
+    tracers = {}
 
-        def render(n):
-            def go():
-                buf.zero_()
-                tracer.trace(n, n, buf)  # points n .. 2n-1: past the training log for n >= 2^20
-                s.reduce(buf, 1.0 / n, accum="f64", out=out)
-            _, ms = _timed(go)
-            return out[0, 0].clone(), ms
-        return render
+    def render(arm, rep, n):
+        """One randomized render of n packets (replicate rep) and its wall time in ms."""
+        gen = "philox" if arm == "mc_philox" else "sobol_owen"
+        blocks = max(1, n >> SOBOL_BLOCK_LOG2) if gen == "sobol_owen" else 1
+        per = n // blocks
+        parts = [scene(gen, 1000 * (rep + 1) + 7 * b + (11 if arm == "mc_philox" else 0)) for b in range(blocks)]
+        if arm not in tracers:  # one tracer (workspace) per arm, pointed at each scene in turn
+            tracers[arm] = Q.LearnedTracer(sc, W if arm == "learned_qmc" else None, chunk=chunk, wavefront=True)
+        tr = tracers[arm]
+        buf = sc.accum_buffer("f64")
 
-    for r in (renderer(plain, sc), renderer(learned, sc), renderer(mc, mc_sc)):
-        r(1 << 16)  # warm
-    arms = {"plain_qmc": _ladder(renderer(plain, sc), ladder, ref, ref_err),
-            "learned_qmc": _ladder(renderer(learned, sc), ladder, ref, ref_err),
-            "mc_philox": _ladder(renderer(mc, mc_sc), ladder, ref, ref_err)}
+        def go():
+            buf.zero_()
+            for s in parts:
+                tr.scene = s  # same grid, this point set's generator and seed
+                tr.trace(per, per, buf)  # points per .. 2 per - 1: one whole net block
+            sc.reduce(buf, 1.0 / n, accum="f64", out=out)
+        _, ms = _timed(go)
+        return out[0, 0].clone(), ms
+
+    arms_ladder = {"plain_qmc": ladder, "learned_qmc": ladder, "mc_philox": mc_ladder or ladder}
+    for arm in arms_ladder:
+        render(arm, 0, 1 << 16)  # warm
+    arms = {}
+    for arm, lad in arms_ladder.items():
+        rows = []
+        for lg in lad:
+            imgs, mss = [], []
+            for r in range(replicates):
+                img, ms = render(arm, r, 1 << lg)
+                imgs.append(img)
+                mss.append(ms)
+            rows.append({"log2_n": lg, "ms": statistics.median(mss), "rms": _replicate_error(imgs)})
+        arms[arm] = rows
+        tracers.clear()
     overhead = {"learned_qmc": ms_log + ms_train}
-    targets = (0.05, 0.03, 1e-2, 1e-3)
-    summary = _tte_summary(arms, targets, overhead)
+    summary = _tte_summary(arms, targets, overhead, key="rms")
     for tgt, row in summary.items():
         p, l, m = (row[k]["ms"] for k in ("plain_qmc", "learned_qmc", "mc_philox"))
         row["learned_speedup_vs_plain"] = p / l if p and l else None
         row["plain_qmc_speedup_vs_mc"] = m / p if p and m else None
     return {"workload": "clumpy envelope 128^3 (radial tau 5, sigma 1 clumps), point source, 20 orders, forced, "
                         "roulette 1e-4, g 0.6, albedo 0.7, 512x512 I/Q/U, FP32 trace, FP64 accumulate",
-            "error": "RMS relative of the I image (L1 relative also listed), against the reference",
-            "reference": {"packets": ref_n, "generator": "sobol_owen", "seeds": list(ref_seeds),
-                          "estimated_rms_error": ref_err},
+            "error": f"RMS relative of the I image, estimated from {replicates} independent randomized renders "
+                     "(Owen-scrambled Sobol seeds, Philox keys) at each N",
             "training": {"logged_packets": n_log, "log_ms": ms_log, "train_ms": ms_train, "epochs": epochs,
                          "batch": 1 << batch_log2, "lr": lr, "uniform_mix": mix, "sample_weight": weight,
                          "loss_first": losses[0], "loss_last": sum(losses[-8:]) / len(losses[-8:]),
@@ -633,6 +689,9 @@ def main():
     ap.add_argument("--packets", type=int, default=PACKETS_PER_STEP)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and time-to-error sections")
+    ap.add_argument("--tte-c5", action="store_true",
+                    help="only the learned-vs-plain time to error at the clumpy workload's 1e-3 target (a long run: "
+                         "ladders to 2^35 packets, training on 2^22 logged packets); prints that section")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -652,6 +711,11 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     B.build()
     Q.load()
+    if args.tte_c5:
+        res = run_time_to_error_learned(ladder=(20, 22, 24, 26, 28, 30, 32, 34, 35), mc_ladder=(20, 22, 24, 26, 28, 30),
+                                        n_log_log2=22, chunk_log2=24)
+        print(json.dumps({"section": "time_to_error_learned_vs_plain_c5", **res}), flush=True)
+        return 0
     prob = workload_problem()
     n = args.packets
     total_ranges = (1 << 32) // n - 1
