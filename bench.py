@@ -33,6 +33,8 @@ if ROOT not in sys.path:
 METRIC = "packets/s and wall time to fixed image RMS error (QMC, learned vs plain), 1 GB300"
 PACKETS_PER_STEP = 1 << 26
 OPS_PER_CELL = 10          # algorithmic ALU operations per grid-cell visit (see design notes)
+OPS_PER_PACKET = 150       # setup and transcendentals of one packet's single scattering (emission,
+                           # forced depth, peel-off phase function and Stokes, binning)
 SMS, LANES_PER_SM = 152, 128
 KERNEL_SOURCES = ["paper_2406_15632_gb300/csrc/qmcrt_device.cuh", "paper_2406_15632_gb300/csrc/qmcrt_trace_single.cu",
                   "paper_2406_15632_gb300/csrc/qmcrt_api.cu"]  # the kernel and the host side of its packet order
@@ -794,7 +796,7 @@ def main():
     peak_ops = SMS * LANES_PER_SM * max_mhz * 1e6
     cpp = cells_per_packet()
     kern_avg_s = kern_total / args.steps / 1e3
-    achieved_ops = n * cpp * OPS_PER_CELL / kern_avg_s
+    achieved_ops = n * (cpp * OPS_PER_CELL + OPS_PER_PACKET) / kern_avg_s
     traffic = profiled_traffic()
     line = {
         "metric": METRIC, "value": value, "unit": "packets/s", "n_gpus": world, "steps": args.steps,
@@ -803,7 +805,8 @@ def main():
         "roofline": {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
                      "frac": achieved_ops / peak_ops, "traffic": traffic,
                      "kernel": "k_trace_single<float>", "kernel_ms": kern_avg_s * 1e3,
-                     "per_unit": f"{OPS_PER_CELL} ops per cell visit x {cpp:.2f} cells per packet",
+                     "per_unit": f"{OPS_PER_CELL} ops per cell visit x {cpp:.2f} cells per packet + "
+                                 f"{OPS_PER_PACKET} ops of setup per packet",
                      "peak_basis": f"{SMS} SMs x {LANES_PER_SM} lanes x {max_mhz:.0f} MHz (measured max clock)"},
         "e2e": {"value": e2e_value, "unit": "packets/s", "h2d_bytes_per_step": R.input_bytes(),
                 "d2h_bytes_per_step": R.output_bytes()},
