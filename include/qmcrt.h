@@ -88,8 +88,7 @@ typedef struct qmcrt_medium {
     const float *d_k;  /* grid: device [nz][ny][nx] extinction kappa*rho per unit length, x fastest;
                           with pad > 0 the [nz+2pad][ny+2pad][nx+2pad] array of qmcrt_pad_grid */
     int32_t nx, ny, nz; /* cells of the grid proper (without padding) */
-    int32_t pad;        /* 0, or >= QMCRT_MIN_PAD sentinel layers (faster walk; the padded grid then
-                           holds at most 2^30 cells) */
+    int32_t pad;        /* 0, or >= QMCRT_MIN_PAD sentinel layers (faster walk) */
     double lo[3], hi[3]; /* grid box; every packet starts inside it */
     double kscale;       /* multiplier on every cell (opacity at another wavelength) */
     double sphere_r;     /* sphere medium: radius */

@@ -306,8 +306,7 @@ int fill_trace(const qmcrt_medium *md, const qmcrt_source *src, const qmcrt_dust
         if (md->pad != 0 && md->pad < QMCRT_MIN_PAD)
             return fail(QMCRT_ERR_INVALID_ARG, "pad %d: 0 or at least %d", md->pad, QMCRT_MIN_PAD);
         const int px = md->nx + 2 * md->pad, py = md->ny + 2 * md->pad, pz = md->nz + 2 * md->pad;
-        if (md->pad > 0 && (double)px * py * pz > 1073741824.0)  // the walk's 32-bit byte offsets
-            return fail(QMCRT_ERR_INVALID_ARG, "padded grid larger than 2^30 cells");
+        if ((double)px * py * pz > 2147483647.0) return fail(QMCRT_ERR_INVALID_ARG, "padded grid larger than 2^31 cells");
         P.med.pad = md->pad;
         P.med.stride[0] = 1;
         P.med.stride[1] = px;

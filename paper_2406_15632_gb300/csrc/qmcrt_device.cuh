@@ -540,14 +540,10 @@ __device__ __forceinline__ bool grid_walk_padded(const MediumP<T> &G, const T p[
     AxisWalk<T> Y = axis_setup(p[1], d[1], r[1], cy, G.lo[1], G.h[1], G.n[1], G.stride[1]);
     AxisWalk<T> Z = axis_setup(p[2], d[2], r[2], cz, G.lo[2], G.h[2], G.n[2], G.stride[2]);
     if (X.step == 0 && Y.step == 0 && Z.step == 0) return false;
-    // Cells are addressed by unsigned 32-bit byte offsets from the grid's base (a load needs
-    // no index scaling per cell); the host admits padded grids of at most 2^30 cells, so
-    // every offset the walk reaches is below 2^32 (steps are added modulo 2^32).
-    unsigned idx = 4u * (unsigned)((cx + G.pad) * G.stride[0] + (cy + G.pad) * G.stride[1] + (cz + G.pad) * G.stride[2]);
-    X.step *= 4;
-    Y.step *= 4;
-    Z.step *= 4;
-    const char *__restrict__ K = (const char *)G.k;
+    // Cells are addressed by an unsigned 32-bit element index (one wide multiply-add per
+    // load; padded grids hold at most 2^31 cells, and steps are added modulo 2^32).
+    unsigned idx = (unsigned)((cx + G.pad) * G.stride[0] + (cy + G.pad) * G.stride[1] + (cz + G.pad) * G.stride[2]);
+    const float *__restrict__ K = G.k;
     T t = T(0), acc = TARGET ? target_raw : T(0), comp = T(0), t_last = T(0);
     for (;;) {
         T L[WALK_UNROLL];
@@ -575,7 +571,7 @@ __device__ __forceinline__ bool grid_walk_padded(const MediumP<T> &G, const T p[
         unsigned sign = 0u;
 #pragma unroll
         for (int u = 0; u < WALK_UNROLL; ++u) {
-            kf[u] = __ldg((const float *)(K + cell[u]));
+            kf[u] = __ldg(K + cell[u]);
             sign |= __float_as_uint(kf[u]);
         }
         T dtau[WALK_UNROLL];
