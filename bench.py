@@ -85,9 +85,9 @@ def profiled_traffic():
     return float(m_bytes.group(1))
 
 
-def cells_per_packet(workload="flared_disk_single_scattering"):
+def cells_per_packet(workload="flared_disk_single_scattering", key="cells_per_packet"):
     with open(COUNTS) as f:
-        return json.load(f)[workload]["cells_per_packet"]
+        return json.load(f)[workload][key]
 
 
 class ClockSampler:
@@ -794,7 +794,9 @@ def main():
     clk = clocks.summary()
     max_mhz = peaks.get("sm_max_mhz", 2070.0)
     peak_ops = SMS * LANES_PER_SM * max_mhz * 1e6
-    cpp = cells_per_packet()
+    # the tracer skips, from one lookup of the bound map, the rays that cannot scatter:
+    # its algorithmic work is the oracle's count of the other rays' walks
+    cpp = cells_per_packet(key="cells_per_packet_scattering_rays")
     kern_avg_s = kern_total / args.steps / 1e3
     achieved_ops = n * (cpp * OPS_PER_CELL + OPS_PER_PACKET) / kern_avg_s
     traffic = profiled_traffic()
@@ -805,8 +807,8 @@ def main():
         "roofline": {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
                      "frac": achieved_ops / peak_ops, "traffic": traffic,
                      "kernel": "k_trace_single<float>", "kernel_ms": kern_avg_s * 1e3,
-                     "per_unit": f"{OPS_PER_CELL} ops per cell visit x {cpp:.2f} cells per packet + "
-                                 f"{OPS_PER_PACKET} ops of setup per packet",
+                     "per_unit": f"{OPS_PER_CELL} ops per cell visit x {cpp:.2f} cells per packet (oracle count "
+                                 f"of the walks of rays with tau_1 >= tau_min) + {OPS_PER_PACKET} ops of setup per packet",
                      "peak_basis": f"{SMS} SMs x {LANES_PER_SM} lanes x {max_mhz:.0f} MHz (measured max clock)"},
         "e2e": {"value": e2e_value, "unit": "packets/s", "h2d_bytes_per_step": R.input_bytes(),
                 "d2h_bytes_per_step": R.output_bytes()},

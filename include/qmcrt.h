@@ -30,7 +30,7 @@
 extern "C" {
 #endif
 
-#define QMCRT_ABI_VERSION 1
+#define QMCRT_ABI_VERSION 2
 
 /* ---- status codes ---- */
 #define QMCRT_OK 0
@@ -93,6 +93,11 @@ typedef struct qmcrt_medium {
     double kscale;       /* multiplier on every cell (opacity at another wavelength) */
     double sphere_r;     /* sphere medium: radius */
     double sphere_k;     /* sphere medium: extinction per unit length */
+    const double *d_sky; /* grid, optional (NULL): device map of qmcrt_sky_bound for this grid; rays that
+                            leave the origin in a direction whose bound (times kscale) is below tau_min / 2
+                            are known not to scatter without walking the grid (same result) */
+    int32_t sky_m;       /* texels per face edge of d_sky (1..4096) */
+    int32_t sky_reserved;
 } qmcrt_medium;
 
 /* ---- source (Sec. 3.2, 3.3) ---- */
@@ -450,6 +455,24 @@ int qmcrt_image_reduce(const qmcrt_image *image, int32_t nx, int32_t ny, int32_t
                        double *d_out, void *stream);
 
 /*
+ * qmcrt_sky_bound -- for a point source at the origin (Sec. 3.2): d_map, device double
+ * [6][m][m], receives per cube-map texel an upper bound on the optical depth (kappa rho
+ * without kscale) of every ray from the origin whose direction falls in the texel.  Face
+ * f = 2 a + (d_a < 0) for the direction's major axis a (ties to the lower axis); u, v are
+ * the other two components (increasing axis order) over |d_a|; texel (iu, iv) =
+ * (floor((u + 1) m / 2), floor((v + 1) m / 2)).  Each cell with kappa rho > 0 adds kappa rho
+ * times its diagonal to every texel its box subtends from the origin (widened by one texel),
+ * so the bound holds for the float directions of the FP32 tracer too.  d_k: device
+ * [nz][ny][nx] grid (not padded); lo, hi: host [3], the grid box.  Pass the map in
+ * qmcrt_medium.d_sky: the first forced step of a packet emitted at the origin then skips
+ * its walks when 2 x bound x kscale < tau_min, which is exactly when the walk's tau_1 would
+ * fall below tau_min.  Rebuild the map whenever the grid changes.
+ * Errors: INVALID_ARG (NULL pointers, empty grid or box, m outside 1..4096), CUDA.
+ */
+int qmcrt_sky_bound(const float *d_k, int32_t nx, int32_t ny, int32_t nz, const double *lo, const double *hi,
+                    int32_t m, double *d_map, void *stream);
+
+/*
  * qmcrt_contribution_bound -- *bound = the largest |I|, |Q| or |U| one peel-off
  * contribution can carry (Sec. 2.2, 3.5, 3.6), for the source (limb weight at most
  * 1 / (1 - u/3)), dust and options given; multiple != 0 takes opts->max_orders orders and
@@ -493,7 +516,8 @@ typedef struct qmcrt_host_io {
  * qmcrt_render_single_host -- one end-to-end single-scattering render for a caller whose
  * inputs and outputs live in host memory (Sec. 3.2-3.6): enqueues on stream the copy of
  * io->h_k to the device (one cudaMemcpyAsync), its sentinel padding (qmcrt_pad_grid,
- * when medium->pad > 0), the clearing of io->d_accum, qmcrt_trace_single with fixed-point
+ * when medium->pad > 0) and bound map (qmcrt_sky_bound into medium->d_sky, when given),
+ * the clearing of io->d_accum, qmcrt_trace_single with fixed-point
  * accumulation at frac_bits, qmcrt_image_reduce with scale (normally 1/N) into
  * io->d_image, and the copy of that image to io->h_image (one cudaMemcpyAsync).  The
  * call returns after enqueuing: synchronize the stream before reading h_image.  The

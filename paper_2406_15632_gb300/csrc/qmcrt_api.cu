@@ -308,6 +308,11 @@ int fill_trace(const qmcrt_medium *md, const qmcrt_source *src, const qmcrt_dust
         const int px = md->nx + 2 * md->pad, py = md->ny + 2 * md->pad, pz = md->nz + 2 * md->pad;
         if ((double)px * py * pz > 2147483647.0) return fail(QMCRT_ERR_INVALID_ARG, "padded grid larger than 2^31 cells");
         P.med.pad = md->pad;
+        if (md->d_sky) {
+            if (md->sky_m < 1 || md->sky_m > 4096) return fail(QMCRT_ERR_INVALID_ARG, "sky_m outside 1..4096");
+            P.med.sky = md->d_sky;
+            P.med.sky_m = md->sky_m;
+        }
         P.med.stride[0] = 1;
         P.med.stride[1] = px;
         P.med.stride[2] = px * py;
@@ -791,6 +796,19 @@ int qmcrt_gemm_bf16(const void *d_A, const void *d_B, int32_t M, int32_t N, int3
                                                static_cast<const __nv_bfloat16 *>(d_B), M, N, K, splits, ep,
                                                (cudaStream_t)stream),
                        "gemm launch");
+}
+
+int qmcrt_sky_bound(const float *d_k, int32_t nx, int32_t ny, int32_t nz, const double *lo, const double *hi,
+                    int32_t m, double *d_map, void *stream)
+{
+    g_last_error.clear();
+    if (!d_k || !lo || !hi || !d_map) return fail(QMCRT_ERR_INVALID_ARG, "NULL pointer");
+    if (nx < 1 || ny < 1 || nz < 1) return fail(QMCRT_ERR_INVALID_ARG, "grid has zero cells");
+    for (int a = 0; a < 3; ++a)
+        if (!(hi[a] > lo[a])) return fail(QMCRT_ERR_INVALID_ARG, "grid box axis %d is empty", a);
+    if (m < 1 || m > 4096) return fail(QMCRT_ERR_INVALID_ARG, "m outside 1..4096");
+    return cuda_status(qmcrt::launch_sky_bound(d_k, nx, ny, nz, lo, hi, m, d_map, (cudaStream_t)stream),
+                       "sky_bound launch");
 }
 
 int qmcrt_pad_grid(const float *d_k, int32_t nx, int32_t ny, int32_t nz, int32_t pad, float *d_padded, void *stream)

@@ -696,10 +696,38 @@ __device__ __forceinline__ bool march(const MediumP<T> &G, T pos[3], const T d[3
     return march(G, pos, d, r, tau);
 }
 
+// The bound of qmcrt_sky_bound on the optical depth (without kscale) of the ray from the
+// origin along d: one cube-map texel (face of the major axis, ties to the lower axis).
+template <class T>
+__device__ __forceinline__ double sky_bound(const MediumP<T> &G, const T d[3])
+{
+    const T ax = Mth<T>::max_(d[0], -d[0]), ay = Mth<T>::max_(d[1], -d[1]), az = Mth<T>::max_(d[2], -d[2]);
+    int a;
+    T w, u, v;
+    if (ax >= ay && ax >= az) {
+        a = 0; w = ax; u = d[1]; v = d[2];
+    } else if (ay >= az) {
+        a = 1; w = ay; u = d[0]; v = d[2];
+    } else {
+        a = 2; w = az; u = d[0]; v = d[1];
+    }
+    const int m = G.sky_m;
+    const int f = 2 * a + (d[a] < T(0) ? 1 : 0);
+    const int iu = min(m - 1, max(0, (int)Mth<T>::floor_((u / w + T(1)) * T(0.5) * T(m))));
+    const int iv = min(m - 1, max(0, (int)Mth<T>::floor_((v / w + T(1)) * T(0.5) * T(m))));
+    return __ldg(G.sky + ((size_t)f * m + iv) * m + iu);
+}
+
 // Forced scattering (Sec. 3.2): weight 1 - e^{-tau_1}, depth -ln[1 - w (1 - e^{-tau_1})].
+// A ray from the origin whose direction's bound (qmcrt_sky_bound, with a factor of two
+// for the float walk's rounding) lies below tau_min cannot reach it: the packet is skipped
+// as the walk would skip it, without walking.
 template <class T>
 __device__ __forceinline__ bool forced_step(const TraceP<T> &P, T pos[3], const T d[3], T w, T &W1)
 {
+    if (P.med.sky && pos[0] == T(0) && pos[1] == T(0) && pos[2] == T(0) &&
+        2.0 * sky_bound(P.med, d) * (double)P.med.kscale < (double)P.tau_min)
+        return false;
     T r[3];  // both walks run along d
     reciprocals(d, r);
     const T tau1 = tau_to_edge(P.med, pos, d, r);

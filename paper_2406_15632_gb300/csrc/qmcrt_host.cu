@@ -134,6 +134,11 @@ int qmcrt_render_single_host(const qmcrt_medium *medium, const qmcrt_source *sou
                                 const_cast<float *>(medium->d_k), stream);
             if (rc) return rc;
         }
+        if (medium->d_sky) {  // the bound map follows the new grid
+            rc = qmcrt_sky_bound(medium->pad > 0 ? io->d_k : medium->d_k, medium->nx, medium->ny, medium->nz,
+                                 medium->lo, medium->hi, medium->sky_m, const_cast<double *>(medium->d_sky), stream);
+            if (rc) return rc;
+        }
     }
     e = cudaMemsetAsync(io->d_accum, 0, 3 * pixels * sizeof(long long), s);
     if (e != cudaSuccess) return qmcrt::set_error(QMCRT_ERR_CUDA, "clearing the accumulator: %s", cudaGetErrorString(e));

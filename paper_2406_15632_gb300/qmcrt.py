@@ -32,6 +32,7 @@ PREC = {"f32": 0, "f64": 1}
 FORCE = {"all": 0, "first": 1}
 MAX_DIMS = 256
 MIN_PAD = 8
+SKY_M = 512  # texels per cube-face edge of the bound map of rays from a point source
 
 
 class QmcrtError(RuntimeError):
@@ -48,7 +49,8 @@ class qmcrt_points_desc(C.Structure):
 class qmcrt_medium(C.Structure):
     _fields_ = [("struct_size", C.c_uint32), ("kind", C.c_int32), ("d_k", C.c_void_p), ("nx", C.c_int32),
                 ("ny", C.c_int32), ("nz", C.c_int32), ("pad", C.c_int32), ("lo", C.c_double * 3),
-                ("hi", C.c_double * 3), ("kscale", C.c_double), ("sphere_r", C.c_double), ("sphere_k", C.c_double)]
+                ("hi", C.c_double * 3), ("kscale", C.c_double), ("sphere_r", C.c_double), ("sphere_k", C.c_double),
+                ("d_sky", C.c_void_p), ("sky_m", C.c_int32), ("sky_reserved", C.c_int32)]
 
 
 class qmcrt_source(C.Structure):
@@ -161,6 +163,8 @@ _SIGS = [
                                   C.c_void_p, C.c_uint64, C.c_void_p]),
     ("qmcrt_warp_adam", C.c_int, [_P(qmcrt_warp), C.c_void_p, C.c_void_p, C.c_void_p, _P(qmcrt_adam), C.c_void_p]),
     ("qmcrt_pad_grid", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
+    ("qmcrt_sky_bound", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, _P(C.c_double), _P(C.c_double),
+                                  C.c_int32, C.c_void_p, C.c_void_p]),
     ("qmcrt_trace_single_noalloc", C.c_int, [_P(qmcrt_medium), _P(qmcrt_source), _P(qmcrt_dust),
                                              _P(qmcrt_observer), _P(qmcrt_points_desc), _P(qmcrt_trace_opts),
                                              C.c_int32, C.c_double, C.c_void_p, C.c_void_p]),
@@ -187,7 +191,7 @@ def load(path: str = LIB_PATH):
                 f = getattr(L, name)
                 f.restype = res
                 f.argtypes = args
-            if L.qmcrt_abi_version() != 1:
+            if L.qmcrt_abi_version() != 2:
                 raise QmcrtError(ERR_UNSUPPORTED, "ABI version mismatch")
             _lib = L
     return _lib
@@ -369,6 +373,11 @@ def qmcrt_pad_grid(d_k: int, nx: int, ny: int, nz: int, pad: int, d_padded: int,
 MAX_OBSERVERS = 16
 
 
+def qmcrt_sky_bound(d_k: int, nx: int, ny: int, nz: int, lo, hi, m: int, d_map: int, stream: int = 0) -> None:
+    _check(load().qmcrt_sky_bound(C.c_void_p(d_k), nx, ny, nz, (C.c_double * 3)(*lo), (C.c_double * 3)(*hi), m,
+                                  C.c_void_p(d_map), C.c_void_p(stream)))
+
+
 def qmcrt_wavefront_workspace_bytes(max_packets: int, precision: str = "f32") -> int:
     return int(load().qmcrt_wavefront_workspace_bytes(max_packets, PREC[precision]))
 
@@ -493,13 +502,17 @@ def default_frac_bits(prob: scenes.Problem, n_contributions: int, weight_bound: 
 
 
 class Scene:
-    """The descriptor structs of one problem, with its grid resident on the device."""
+    """The descriptor structs of one problem, with its grid resident on the device: the
+    sentinel-padded copy the fast walk reads (pad > 0) and, for a point source, the bound
+    map of rays from the origin (qmcrt_sky_bound, sky texels per cube-face edge; 0: none)."""
 
-    def __init__(self, prob: scenes.Problem, grid_device=None, device="cuda", pad: int = MIN_PAD):
+    def __init__(self, prob: scenes.Problem, grid_device=None, device="cuda", pad: int = MIN_PAD,
+                 sky: int = SKY_M):
         torch = _torch()
         self.prob = prob
         self.pad = pad
         self.padded = None
+        self.sky = None
         if prob.grid is not None:
             if grid_device is None:
                 grid_device = torch.as_tensor(prob.grid, dtype=torch.float32).to(device).contiguous()
@@ -509,10 +522,13 @@ class Scene:
             if pad:
                 self.padded = torch.empty((nz + 2 * pad, ny + 2 * pad, nx + 2 * pad), dtype=torch.float32,
                                           device=device)
-                self.repad()
                 d_k = self.padded.data_ptr()
             self.medium = _new(qmcrt_medium, kind=MEDIUM_GRID, d_k=d_k, nx=nx, ny=ny, nz=nz, pad=pad,
                                kscale=prob.kscale)
+            if sky and prob.source == "point":
+                self.sky = torch.empty((6, sky, sky), dtype=torch.float64, device=device)
+                self.medium.d_sky = self.sky.data_ptr()
+                self.medium.sky_m = sky
         else:
             self.grid = None
             self.medium = _new(qmcrt_medium, kind=MEDIUM_SPHERE, d_k=None, kscale=prob.kscale,
@@ -526,12 +542,18 @@ class Scene:
         self.dust = _new(qmcrt_dust, albedo=prob.albedo, g=prob.g, p_l=prob.p_l)
         self.obs = _new(qmcrt_observer, splat=SPLAT[prob.splat], theta=prob.theta_obs, phi=prob.phi_obs,
                         half_width=prob.half_width, nx=prob.nx, ny=prob.ny)
+        self.repad()
 
     def repad(self, stream=None) -> None:
-        """Refresh the padded copy after the grid changed."""
+        """Refresh the padded copy and the bound map after the grid changed."""
+        if self.grid is None:
+            return
+        nz, ny, nx = self.grid.shape
         if self.padded is not None:
-            nz, ny, nx = self.grid.shape
             qmcrt_pad_grid(self.grid.data_ptr(), nx, ny, nz, self.pad, self.padded.data_ptr(), _stream(stream))
+        if self.sky is not None:
+            qmcrt_sky_bound(self.grid.data_ptr(), nx, ny, nz, self.prob.lo, self.prob.hi, self.sky.shape[-1],
+                            self.sky.data_ptr(), _stream(stream))
 
     def opts(self, precision: str = "f32", block_size: int = 0) -> qmcrt_trace_opts:
         p = self.prob
@@ -698,14 +720,16 @@ class HostRenderer:
     qmcrt_render_single_host, the copy of the density grid from (pinned) host memory,
     its padding, the trace of a packet range, the reduction and the copy of the image
     back to host memory, all on one stream.  Device buffers are allocated once, at
-    construction."""
+    construction.  A grid that arrives anew with every call gets no bound map by default
+    (sky=0): rebuilding it (tens of ms on a 256^3 grid) costs more than it saves on one
+    trace of 2^26 packets."""
 
     def __init__(self, prob: scenes.Problem, max_packets: int, *, precision: str = "f32",
-                 frac_bits: int | None = None):
+                 frac_bits: int | None = None, sky: int = 0):
         torch = _torch()
         if prob.max_orders > 1:
             raise QmcrtError(ERR_UNSUPPORTED, "HostRenderer renders single scattering")
-        self.scene = Scene(prob)
+        self.scene = Scene(prob, sky=sky)
         self.precision = precision
         self.frac_bits = default_frac_bits(prob, max_packets) if frac_bits is None else frac_bits
         self.buf = self.scene.accum_buffer("i64")

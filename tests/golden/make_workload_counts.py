@@ -23,6 +23,9 @@ def main():
     _, log = O.trace_single(prob, 1, N, log=True)
     out["flared_disk_single_scattering"] = {
         "cells_per_packet": float(log[:, 9].mean()),
+        # the walks a tracer must take when rays whose tau_1 lies below tau_min are known
+        # not to scatter without walking them (they count as no cells)
+        "cells_per_packet_scattering_rays": float((log[:, 9] * (log[:, 8] != 1)).mean()),
         "packets": N,
         "contributing_fraction": float((log[:, 8] == 0).mean()),
         "note": "256^3 flared disk, point source, Sobol indices 1..2^18, all three walks per packet",

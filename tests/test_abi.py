@@ -36,7 +36,7 @@ def test_library_exports_every_declared_symbol(lib):
     for name in declared_functions():
         assert hasattr(lib, name), name
     assert sorted(Q.EXPORTED) == sorted(declared_functions())
-    assert lib.qmcrt_abi_version() == 1
+    assert lib.qmcrt_abi_version() == 2
 
 
 STRUCTS = ["qmcrt_points_desc", "qmcrt_medium", "qmcrt_source", "qmcrt_dust", "qmcrt_observer", "qmcrt_image",
@@ -298,6 +298,23 @@ def test_contribution_bound_holds_through_scattering_and_peel_off(g, albedo, p_l
     for k in range(1, K + 1):
         assert worst[k] <= Q.contribution_bound(prob.replace(max_orders=k)) * (1 + 1e-12), k
     assert worst[1] >= 0.05 * Q.contribution_bound(prob.replace(max_orders=1))
+
+
+def test_sky_bound_validation(lib):
+    lo, hi = [-1.0] * 3, [1.0] * 3
+    _expect(Q.ERR_INVALID_ARG, Q.qmcrt_sky_bound, 0, 4, 4, 4, lo, hi, 16, 0x2000)
+    _expect(Q.ERR_INVALID_ARG, Q.qmcrt_sky_bound, 0x1000, 4, 4, 4, lo, hi, 16, 0)
+    _expect(Q.ERR_INVALID_ARG, Q.qmcrt_sky_bound, 0x1000, 0, 4, 4, lo, hi, 16, 0x2000)
+    _expect(Q.ERR_INVALID_ARG, Q.qmcrt_sky_bound, 0x1000, 4, 4, 4, lo, [1.0, -1.0, 1.0], 16, 0x2000)
+    for m in (0, 4097):
+        _expect(Q.ERR_INVALID_ARG, Q.qmcrt_sky_bound, 0x1000, 4, 4, 4, lo, hi, m, 0x2000)
+    # a trace rejects a bound map of impossible size
+    g = _descs(medium__kind=0, medium__d_k=0x5000, medium__nx=4, medium__ny=4, medium__nz=4, medium__d_sky=0x6000,
+               medium__sky_m=0)
+    for a in range(3):
+        g["medium"].lo[a], g["medium"].hi[a] = -1.0, 1.0
+    _expect(Q.ERR_INVALID_ARG, Q.qmcrt_trace_single, g["medium"], g["source"], g["dust"], g["obs"], g["pts"],
+            g["opts"], g["img"], 0, 0)
 
 
 def test_batch_validation(lib):
