@@ -94,10 +94,12 @@ typedef struct qmcrt_medium {
     double sphere_r;     /* sphere medium: radius */
     double sphere_k;     /* sphere medium: extinction per unit length */
     const double *d_sky; /* grid, optional (NULL): device map of qmcrt_sky_bound for this grid; rays that
-                            leave the origin in a direction whose bound (times kscale) is below tau_min / 2
-                            are known not to scatter without walking the grid (same result) */
+                            start within sky_r of the origin in a direction whose bound (times kscale) is
+                            below tau_min / 2 are known not to scatter without walking the grid (same
+                            result) */
     int32_t sky_m;       /* texels per face edge of d_sky (1..4096) */
     int32_t sky_reserved;
+    double sky_r;        /* the radius d_sky was built for (0 for a point source, the star's radius) */
 } qmcrt_medium;
 
 /* ---- source (Sec. 3.2, 3.3) ---- */
@@ -455,22 +457,25 @@ int qmcrt_image_reduce(const qmcrt_image *image, int32_t nx, int32_t ny, int32_t
                        double *d_out, void *stream);
 
 /*
- * qmcrt_sky_bound -- for a point source at the origin (Sec. 3.2): d_map, device double
- * [6][m][m], receives per cube-map texel an upper bound on the optical depth (kappa rho
- * without kscale) of every ray from the origin whose direction falls in the texel.  Face
+ * qmcrt_sky_bound -- for a source at the origin (Sec. 3.2, 3.3: a point, radius 0, or a
+ * star of that radius): d_map, device double [6][m][m], receives per cube-map texel an upper
+ * bound on the optical depth (kappa rho without kscale) of every ray that starts within
+ * `radius` of the origin and whose direction falls in the texel.  Face
  * f = 2 a + (d_a < 0) for the direction's major axis a (ties to the lower axis); u, v are
  * the other two components (increasing axis order) over |d_a|; texel (iu, iv) =
  * (floor((u + 1) m / 2), floor((v + 1) m / 2)).  Each cell with kappa rho > 0 adds kappa rho
- * times its diagonal to every texel its box subtends from the origin (widened by one texel),
- * so the bound holds for the float directions of the FP32 tracer too.  d_k: device
- * [nz][ny][nx] grid (not padded); lo, hi: host [3], the grid box.  Pass the map in
- * qmcrt_medium.d_sky: the first forced step of a packet emitted at the origin then skips
- * its walks when 2 x bound x kscale < tau_min, which is exactly when the walk's tau_1 would
- * fall below tau_min.  Rebuild the map whenever the grid changes.
- * Errors: INVALID_ARG (NULL pointers, empty grid or box, m outside 1..4096), CUDA.
+ * times its diagonal to every texel its box, grown by the radius on every side, subtends
+ * from the origin (widened by one texel, so the bound holds for the float directions of the
+ * FP32 tracer too).  d_k: device [nz][ny][nx] grid (not padded); lo, hi: host [3], the grid
+ * box.  Pass the map in qmcrt_medium.d_sky with sky_r = radius: a forced step that starts
+ * within that radius of the origin then skips its walks when 2 x bound x kscale < tau_min,
+ * which is exactly when the walk's tau_1 would fall below tau_min.  Rebuild the map
+ * whenever the grid changes.
+ * Errors: INVALID_ARG (NULL pointers, empty grid or box, m outside 1..4096, radius
+ * negative or not finite), CUDA.
  */
 int qmcrt_sky_bound(const float *d_k, int32_t nx, int32_t ny, int32_t nz, const double *lo, const double *hi,
-                    int32_t m, double *d_map, void *stream);
+                    double radius, int32_t m, double *d_map, void *stream);
 
 /*
  * qmcrt_contribution_bound -- *bound = the largest |I|, |Q| or |U| one peel-off

@@ -310,8 +310,12 @@ int fill_trace(const qmcrt_medium *md, const qmcrt_source *src, const qmcrt_dust
         P.med.pad = md->pad;
         if (md->d_sky) {
             if (md->sky_m < 1 || md->sky_m > 4096) return fail(QMCRT_ERR_INVALID_ARG, "sky_m outside 1..4096");
+            if (!(md->sky_r >= 0) || !std::isfinite(md->sky_r)) return fail(QMCRT_ERR_INVALID_ARG, "sky_r must be >= 0");
             P.med.sky = md->d_sky;
             P.med.sky_m = md->sky_m;
+            // a start point counts as within R if |p|^2 <= R^2 (1 + 1e-5), which takes in the
+            // float rounding of a point on the star's surface; the map is built for R (1 + 1e-4)
+            P.med.sky_r2 = (T)(md->sky_r * md->sky_r * (1.0 + 1e-5));
         }
         P.med.stride[0] = 1;
         P.med.stride[1] = px;
@@ -799,7 +803,7 @@ int qmcrt_gemm_bf16(const void *d_A, const void *d_B, int32_t M, int32_t N, int3
 }
 
 int qmcrt_sky_bound(const float *d_k, int32_t nx, int32_t ny, int32_t nz, const double *lo, const double *hi,
-                    int32_t m, double *d_map, void *stream)
+                    double radius, int32_t m, double *d_map, void *stream)
 {
     g_last_error.clear();
     if (!d_k || !lo || !hi || !d_map) return fail(QMCRT_ERR_INVALID_ARG, "NULL pointer");
@@ -807,7 +811,9 @@ int qmcrt_sky_bound(const float *d_k, int32_t nx, int32_t ny, int32_t nz, const 
     for (int a = 0; a < 3; ++a)
         if (!(hi[a] > lo[a])) return fail(QMCRT_ERR_INVALID_ARG, "grid box axis %d is empty", a);
     if (m < 1 || m > 4096) return fail(QMCRT_ERR_INVALID_ARG, "m outside 1..4096");
-    return cuda_status(qmcrt::launch_sky_bound(d_k, nx, ny, nz, lo, hi, m, d_map, (cudaStream_t)stream),
+    if (!(radius >= 0) || !std::isfinite(radius)) return fail(QMCRT_ERR_INVALID_ARG, "radius must be >= 0");
+    return cuda_status(qmcrt::launch_sky_bound(d_k, nx, ny, nz, lo, hi, radius * (1.0 + 1e-4), m, d_map,
+                                               (cudaStream_t)stream),
                        "sky_bound launch");
 }
 

@@ -696,8 +696,9 @@ __device__ __forceinline__ bool march(const MediumP<T> &G, T pos[3], const T d[3
     return march(G, pos, d, r, tau);
 }
 
-// The bound of qmcrt_sky_bound on the optical depth (without kscale) of the ray from the
-// origin along d: one cube-map texel (face of the major axis, ties to the lower axis).
+// The bound of qmcrt_sky_bound on the optical depth (without kscale) of a ray along d that
+// starts within the map's radius of the origin: one cube-map texel (face of the major
+// axis, ties to the lower axis).
 template <class T>
 __device__ __forceinline__ double sky_bound(const MediumP<T> &G, const T d[3])
 {
@@ -719,13 +720,13 @@ __device__ __forceinline__ double sky_bound(const MediumP<T> &G, const T d[3])
 }
 
 // Forced scattering (Sec. 3.2): weight 1 - e^{-tau_1}, depth -ln[1 - w (1 - e^{-tau_1})].
-// A ray from the origin whose direction's bound (qmcrt_sky_bound, with a factor of two
-// for the float walk's rounding) lies below tau_min cannot reach it: the packet is skipped
-// as the walk would skip it, without walking.
+// A ray from within the bound map's radius whose direction's bound (qmcrt_sky_bound, with
+// a factor of two for the float walk's rounding) lies below tau_min cannot reach it: the
+// packet is skipped as the walk would skip it, without walking.
 template <class T>
 __device__ __forceinline__ bool forced_step(const TraceP<T> &P, T pos[3], const T d[3], T w, T &W1)
 {
-    if (P.med.sky && pos[0] == T(0) && pos[1] == T(0) && pos[2] == T(0) &&
+    if (P.med.sky && dot3(pos, pos) <= P.med.sky_r2 &&
         2.0 * sky_bound(P.med, d) * (double)P.med.kscale < (double)P.tau_min)
         return false;
     T r[3];  // both walks run along d

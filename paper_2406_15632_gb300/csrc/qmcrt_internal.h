@@ -37,8 +37,9 @@ struct MediumP {
     T inv_h[3];        // 1 / h: the first estimate of a start cell
     T kscale, inv_kscale;
     T sph_r, sph_k;    // analytic sphere: radius, kscale * extinction
-    const double *sky; // optional bound map for rays from the origin (qmcrt_sky_bound), sky_m texels per edge
-    int sky_m;
+    const double *sky; // optional bound map (qmcrt_sky_bound), sky_m texels per edge, for rays that start
+    int sky_m;         // within sky_r2 = R^2 of the origin
+    T sky_r2;
 };
 
 template <class T>
@@ -176,8 +177,8 @@ cudaError_t launch_warp_forward_fused(const float *params, const __nv_bfloat16 *
 cudaError_t launch_generate_points(const PointsP &p, uint64_t first, uint64_t count, int format, void *out,
                                    cudaStream_t s);
 cudaError_t launch_pad_grid(const float *k, int nx, int ny, int nz, int pad, float *out, cudaStream_t s);
-cudaError_t launch_sky_bound(const float *k, int nx, int ny, int nz, const double lo[3], const double hi[3], int m,
-                             double *map, cudaStream_t s);
+cudaError_t launch_sky_bound(const float *k, int nx, int ny, int nz, const double lo[3], const double hi[3],
+                             double radius, int m, double *map, cudaStream_t s);
 cudaError_t launch_image_reduce(const void *acc, int mode, double frac_scale, size_t elems, int replicas,
                                 double scale, double *out, cudaStream_t s);
 cudaError_t launch_trace_single_f32(const TraceP<float> &p, int block, cudaStream_t s);

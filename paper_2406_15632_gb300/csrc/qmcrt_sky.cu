@@ -1,9 +1,9 @@
-// qmcrt_sky.cu -- qmcrt_sky_bound: for rays leaving the origin (a point source), an upper
-// bound on the optical depth of every ray whose direction falls in each texel of a cube
-// map.  A packet whose direction's bound is below the forcing threshold tau_min cannot
-// scatter (Sec. 3.2: rays with tau_1 < tau_min are skipped), so the tracer decides that
-// from one lookup instead of walking its ray through the grid; the decision, and hence the
-// image, is the walk's.
+// qmcrt_sky_bound: for rays that start within a radius R of the origin (a point source,
+// R = 0, or the surface of a star of radius R), an upper bound on the optical depth of every
+// ray whose direction falls in each texel of a cube map.  A packet whose direction's bound
+// is below the forcing threshold tau_min cannot scatter (Sec. 3.2: rays with tau_1 < tau_min
+// are skipped), so the tracer decides that from one lookup instead of walking its ray
+// through the grid; the decision, and hence the image, is the walk's.
 //
 // Cube map: face f = 2 a + (d_a < 0) for the major axis a of the direction (ties to the
 // lower axis); on it u, v are the other two components (in increasing axis order) divided
@@ -16,16 +16,18 @@ namespace qmcrt {
 namespace {
 
 // Every cell with kappa rho > 0 adds kappa rho times its longest chord (the diagonal) to
-// the texels of all directions from the origin that pass through it: on each face, the
-// box of (u, v) the cell subtends, widened by one texel on every side (the tracer's float
-// directions and cell faces differ from these double values by far less than a texel).
+// the texels of all directions from the origin that pass through its box grown by R on
+// every side: on each face, the box of (u, v) that grown box subtends, widened by one texel
+// on every side (the tracer's float directions and cell faces differ from these double
+// values by far less than a texel).  A ray p + t d with |p| <= R that meets the cell at t
+// has t d in the cell shifted by -p, inside the grown box: its direction is splatted.
 // A cell that reaches the major axis' zero plane subtends directions up to the face's
 // edge on the side where its other coordinates lie.  A ray crosses each cell at most once,
 // over at most the diagonal, so the sum over the cells it crosses -- all of them splatted
 // onto its texel -- bounds its optical depth.
 __global__ void __launch_bounds__(256) k_sky_bound(const float *__restrict__ k, int nx, int ny, int nz, double lo0,
                                                    double lo1, double lo2, double h0, double h1, double h2, int m,
-                                                   double chord, double *map)
+                                                   double chord, double grow, double *map)
 {
     const long long cells = (long long)nx * ny * nz;
     const double lo[3] = {lo0, lo1, lo2}, h[3] = {h0, h1, h2};
@@ -36,8 +38,8 @@ __global__ void __launch_bounds__(256) k_sky_bound(const float *__restrict__ k, 
         const int idx[3] = {(int)(c % nx), (int)((c / nx) % ny), (int)(c / ((long long)nx * ny))};
         double b0[3], b1[3];
         for (int a = 0; a < 3; ++a) {
-            b0[a] = lo[a] + idx[a] * h[a];
-            b1[a] = lo[a] + (idx[a] + 1) * h[a];
+            b0[a] = lo[a] + idx[a] * h[a] - grow;
+            b1[a] = lo[a] + (idx[a] + 1) * h[a] + grow;
         }
         const double add = (double)kc * chord;
         for (int f = 0; f < 6; ++f) {
@@ -72,8 +74,8 @@ __global__ void __launch_bounds__(256) k_sky_bound(const float *__restrict__ k, 
 
 }  // namespace
 
-cudaError_t launch_sky_bound(const float *k, int nx, int ny, int nz, const double lo[3], const double hi[3], int m,
-                             double *map, cudaStream_t s)
+cudaError_t launch_sky_bound(const float *k, int nx, int ny, int nz, const double lo[3], const double hi[3],
+                             double radius, int m, double *map, cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(map, 0, (size_t)6 * m * m * sizeof(double), s);
     if (e != cudaSuccess) return e;
@@ -81,7 +83,7 @@ cudaError_t launch_sky_bound(const float *k, int nx, int ny, int nz, const doubl
     const double chord = sqrt(h0 * h0 + h1 * h1 + h2 * h2);
     const long long cells = (long long)nx * ny * nz;
     const unsigned grid = (unsigned)min((cells + 255) / 256, 152LL * 32);
-    k_sky_bound<<<grid, 256, 0, s>>>(k, nx, ny, nz, lo[0], lo[1], lo[2], h0, h1, h2, m, chord, map);
+    k_sky_bound<<<grid, 256, 0, s>>>(k, nx, ny, nz, lo[0], lo[1], lo[2], h0, h1, h2, m, chord, radius, map);
     return cudaGetLastError();
 }
 

@@ -50,7 +50,7 @@ class qmcrt_medium(C.Structure):
     _fields_ = [("struct_size", C.c_uint32), ("kind", C.c_int32), ("d_k", C.c_void_p), ("nx", C.c_int32),
                 ("ny", C.c_int32), ("nz", C.c_int32), ("pad", C.c_int32), ("lo", C.c_double * 3),
                 ("hi", C.c_double * 3), ("kscale", C.c_double), ("sphere_r", C.c_double), ("sphere_k", C.c_double),
-                ("d_sky", C.c_void_p), ("sky_m", C.c_int32), ("sky_reserved", C.c_int32)]
+                ("d_sky", C.c_void_p), ("sky_m", C.c_int32), ("sky_reserved", C.c_int32), ("sky_r", C.c_double)]
 
 
 class qmcrt_source(C.Structure):
@@ -164,7 +164,7 @@ _SIGS = [
     ("qmcrt_warp_adam", C.c_int, [_P(qmcrt_warp), C.c_void_p, C.c_void_p, C.c_void_p, _P(qmcrt_adam), C.c_void_p]),
     ("qmcrt_pad_grid", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
     ("qmcrt_sky_bound", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, _P(C.c_double), _P(C.c_double),
-                                  C.c_int32, C.c_void_p, C.c_void_p]),
+                                  C.c_double, C.c_int32, C.c_void_p, C.c_void_p]),
     ("qmcrt_trace_single_noalloc", C.c_int, [_P(qmcrt_medium), _P(qmcrt_source), _P(qmcrt_dust),
                                              _P(qmcrt_observer), _P(qmcrt_points_desc), _P(qmcrt_trace_opts),
                                              C.c_int32, C.c_double, C.c_void_p, C.c_void_p]),
@@ -373,9 +373,10 @@ def qmcrt_pad_grid(d_k: int, nx: int, ny: int, nz: int, pad: int, d_padded: int,
 MAX_OBSERVERS = 16
 
 
-def qmcrt_sky_bound(d_k: int, nx: int, ny: int, nz: int, lo, hi, m: int, d_map: int, stream: int = 0) -> None:
-    _check(load().qmcrt_sky_bound(C.c_void_p(d_k), nx, ny, nz, (C.c_double * 3)(*lo), (C.c_double * 3)(*hi), m,
-                                  C.c_void_p(d_map), C.c_void_p(stream)))
+def qmcrt_sky_bound(d_k: int, nx: int, ny: int, nz: int, lo, hi, radius: float, m: int, d_map: int,
+                    stream: int = 0) -> None:
+    _check(load().qmcrt_sky_bound(C.c_void_p(d_k), nx, ny, nz, (C.c_double * 3)(*lo), (C.c_double * 3)(*hi),
+                                  float(radius), m, C.c_void_p(d_map), C.c_void_p(stream)))
 
 
 def qmcrt_wavefront_workspace_bytes(max_packets: int, precision: str = "f32") -> int:
@@ -503,8 +504,9 @@ def default_frac_bits(prob: scenes.Problem, n_contributions: int, weight_bound: 
 
 class Scene:
     """The descriptor structs of one problem, with its grid resident on the device: the
-    sentinel-padded copy the fast walk reads (pad > 0) and, for a point source, the bound
-    map of rays from the origin (qmcrt_sky_bound, sky texels per cube-face edge; 0: none)."""
+    sentinel-padded copy the fast walk reads (pad > 0) and the bound map of rays from the
+    source (qmcrt_sky_bound over the source's radius, sky texels per cube-face edge; 0:
+    none)."""
 
     def __init__(self, prob: scenes.Problem, grid_device=None, device="cuda", pad: int = MIN_PAD,
                  sky: int = SKY_M):
@@ -525,10 +527,11 @@ class Scene:
                 d_k = self.padded.data_ptr()
             self.medium = _new(qmcrt_medium, kind=MEDIUM_GRID, d_k=d_k, nx=nx, ny=ny, nz=nz, pad=pad,
                                kscale=prob.kscale)
-            if sky and prob.source == "point":
+            if sky:
                 self.sky = torch.empty((6, sky, sky), dtype=torch.float64, device=device)
                 self.medium.d_sky = self.sky.data_ptr()
                 self.medium.sky_m = sky
+                self.medium.sky_r = prob.star_r if prob.source == "sphere" else 0.0
         else:
             self.grid = None
             self.medium = _new(qmcrt_medium, kind=MEDIUM_SPHERE, d_k=None, kscale=prob.kscale,
@@ -552,8 +555,8 @@ class Scene:
         if self.padded is not None:
             qmcrt_pad_grid(self.grid.data_ptr(), nx, ny, nz, self.pad, self.padded.data_ptr(), _stream(stream))
         if self.sky is not None:
-            qmcrt_sky_bound(self.grid.data_ptr(), nx, ny, nz, self.prob.lo, self.prob.hi, self.sky.shape[-1],
-                            self.sky.data_ptr(), _stream(stream))
+            qmcrt_sky_bound(self.grid.data_ptr(), nx, ny, nz, self.prob.lo, self.prob.hi, self.medium.sky_r,
+                            self.sky.shape[-1], self.sky.data_ptr(), _stream(stream))
 
     def opts(self, precision: str = "f32", block_size: int = 0) -> qmcrt_trace_opts:
         p = self.prob
