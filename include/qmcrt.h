@@ -460,22 +460,29 @@ int qmcrt_image_reduce(const qmcrt_image *image, int32_t nx, int32_t ny, int32_t
  * qmcrt_sky_bound -- for a source at the origin (Sec. 3.2, 3.3: a point, radius 0, or a
  * star of that radius): d_map, device double [6][m][m], receives per cube-map texel an upper
  * bound on the optical depth (kappa rho without kscale) of every ray that starts within
- * `radius` of the origin and whose direction falls in the texel.  Face
- * f = 2 a + (d_a < 0) for the direction's major axis a (ties to the lower axis); u, v are
- * the other two components (increasing axis order) over |d_a|; texel (iu, iv) =
- * (floor((u + 1) m / 2), floor((v + 1) m / 2)).  Each cell with kappa rho > 0 adds kappa rho
- * times its diagonal to every texel its box, grown by the radius on every side, subtends
- * from the origin (widened by one texel, so the bound holds for the float directions of the
- * FP32 tracer too).  d_k: device [nz][ny][nx] grid (not padded); lo, hi: host [3], the grid
- * box.  Pass the map in qmcrt_medium.d_sky with sky_r = radius: a forced step that starts
- * within that radius of the origin then skips its walks when 2 x bound x kscale < tau_min,
- * which is exactly when the walk's tau_1 would fall below tau_min.  Rebuild the map
- * whenever the grid changes.
+ * `radius` of the origin and whose direction falls in the texel.  Face f = 2 a + (d_a < 0)
+ * for the direction's major axis a (ties to the lower axis); u, v are the other two
+ * components (increasing axis order) over |d_a|; texel (iu, iv) = (floor((u + 1) m / 2),
+ * floor((v + 1) m / 2)).  Construction: such a ray stays within radius + t alpha of the
+ * texel's centre ray (alpha: the texel's angular radius), hence, while that is at most D
+ * smallest cell edges (D = 1 + ceil(radius / h_min)), within D cells of the centre ray's
+ * cell at equal t; the map holds the integral, along the centre ray, of the grid maximised
+ * over (2 D + 1)^3 neighbourhoods (times 1 + 1e-6).  A texel whose cone is wider than that
+ * (too coarse a map for the grid: m below about 1.2 x the cells per axis) holds +inf.
+ * d_k: device [nz][ny][nx] grid (not padded); lo, hi: host [3], the grid box; d_workspace:
+ * device, 256-byte aligned, >= qmcrt_sky_workspace_bytes (two grids grown by D layers).
+ * Pass the map in qmcrt_medium.d_sky with sky_r = radius: a forced step that starts within
+ * that radius of the origin then skips its walks when 2 x bound x kscale < tau_min, which
+ * is exactly when the walk's tau_1 would fall below tau_min.  Rebuild the map whenever the
+ * grid changes.
  * Errors: INVALID_ARG (NULL pointers, empty grid or box, m outside 1..4096, radius
- * negative or not finite), CUDA.
+ * negative or not finite, a small or misaligned workspace), CUDA.
  */
+uint64_t qmcrt_sky_workspace_bytes(int32_t nx, int32_t ny, int32_t nz, const double *lo, const double *hi,
+                                   double radius);
 int qmcrt_sky_bound(const float *d_k, int32_t nx, int32_t ny, int32_t nz, const double *lo, const double *hi,
-                    double radius, int32_t m, double *d_map, void *stream);
+                    double radius, int32_t m, double *d_map, void *d_workspace, uint64_t workspace_bytes,
+                    void *stream);
 
 /*
  * qmcrt_contribution_bound -- *bound = the largest |I|, |Q| or |U| one peel-off
@@ -515,6 +522,8 @@ typedef struct qmcrt_host_io {
     void *d_accum;      /* device int64 [3][ny][nx]: fixed-point scratch, cleared by the call */
     double *d_image;    /* device [3][ny][nx]: the reduced image */
     double *h_image;    /* host [3][ny][nx]: receives the image (pinned memory keeps the call asynchronous) */
+    void *d_sky_ws;     /* device workspace of qmcrt_sky_bound (needed when medium->d_sky is given) */
+    uint64_t sky_ws_bytes;
 } qmcrt_host_io;
 
 /*

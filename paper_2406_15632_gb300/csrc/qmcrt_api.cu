@@ -802,17 +802,34 @@ int qmcrt_gemm_bf16(const void *d_A, const void *d_B, int32_t M, int32_t N, int3
                        "gemm launch");
 }
 
+uint64_t qmcrt_sky_workspace_bytes(int32_t nx, int32_t ny, int32_t nz, const double *lo, const double *hi,
+                                   double radius)
+{
+    if (nx < 1 || ny < 1 || nz < 1 || !lo || !hi || !(radius >= 0) || !std::isfinite(radius)) return 0;
+    for (int a = 0; a < 3; ++a)
+        if (!(hi[a] > lo[a])) return 0;
+    return qmcrt::sky_workspace_bytes(nx, ny, nz, qmcrt::sky_dilation(lo, hi, nx, ny, nz, radius * (1.0 + 1e-4)));
+}
+
 int qmcrt_sky_bound(const float *d_k, int32_t nx, int32_t ny, int32_t nz, const double *lo, const double *hi,
-                    double radius, int32_t m, double *d_map, void *stream)
+                    double radius, int32_t m, double *d_map, void *d_workspace, uint64_t workspace_bytes,
+                    void *stream)
 {
     g_last_error.clear();
-    if (!d_k || !lo || !hi || !d_map) return fail(QMCRT_ERR_INVALID_ARG, "NULL pointer");
+    if (!d_k || !lo || !hi || !d_map || !d_workspace) return fail(QMCRT_ERR_INVALID_ARG, "NULL pointer");
     if (nx < 1 || ny < 1 || nz < 1) return fail(QMCRT_ERR_INVALID_ARG, "grid has zero cells");
     for (int a = 0; a < 3; ++a)
         if (!(hi[a] > lo[a])) return fail(QMCRT_ERR_INVALID_ARG, "grid box axis %d is empty", a);
     if (m < 1 || m > 4096) return fail(QMCRT_ERR_INVALID_ARG, "m outside 1..4096");
     if (!(radius >= 0) || !std::isfinite(radius)) return fail(QMCRT_ERR_INVALID_ARG, "radius must be >= 0");
-    return cuda_status(qmcrt::launch_sky_bound(d_k, nx, ny, nz, lo, hi, radius * (1.0 + 1e-4), m, d_map,
+    if (((uintptr_t)d_workspace & 255) != 0) return fail(QMCRT_ERR_INVALID_ARG, "workspace not 256-byte aligned");
+    const uint64_t need = qmcrt_sky_workspace_bytes(nx, ny, nz, lo, hi, radius);
+    if (workspace_bytes < need)
+        return fail(QMCRT_ERR_INVALID_ARG, "workspace of %llu bytes, need %llu", (unsigned long long)workspace_bytes,
+                    (unsigned long long)need);
+    // the map is built for a radius slightly above the one the trace tests start points
+    // against (|p|^2 <= R^2 (1 + 1e-5)), which absorbs the float rounding of a surface point
+    return cuda_status(qmcrt::launch_sky_bound(d_k, nx, ny, nz, lo, hi, radius * (1.0 + 1e-4), m, d_map, d_workspace,
                                                (cudaStream_t)stream),
                        "sky_bound launch");
 }

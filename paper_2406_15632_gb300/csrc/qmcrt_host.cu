@@ -137,7 +137,7 @@ int qmcrt_render_single_host(const qmcrt_medium *medium, const qmcrt_source *sou
         if (medium->d_sky) {  // the bound map follows the new grid
             rc = qmcrt_sky_bound(medium->pad > 0 ? io->d_k : medium->d_k, medium->nx, medium->ny, medium->nz,
                                  medium->lo, medium->hi, medium->sky_r, medium->sky_m,
-                                 const_cast<double *>(medium->d_sky), stream);
+                                 const_cast<double *>(medium->d_sky), io->d_sky_ws, io->sky_ws_bytes, stream);
             if (rc) return rc;
         }
     }

@@ -178,7 +178,9 @@ cudaError_t launch_generate_points(const PointsP &p, uint64_t first, uint64_t co
                                    cudaStream_t s);
 cudaError_t launch_pad_grid(const float *k, int nx, int ny, int nz, int pad, float *out, cudaStream_t s);
 cudaError_t launch_sky_bound(const float *k, int nx, int ny, int nz, const double lo[3], const double hi[3],
-                             double radius, int m, double *map, cudaStream_t s);
+                             double radius, int m, double *map, void *ws, cudaStream_t s);
+int sky_dilation(const double lo[3], const double hi[3], int nx, int ny, int nz, double radius);
+uint64_t sky_workspace_bytes(int nx, int ny, int nz, int D);
 cudaError_t launch_image_reduce(const void *acc, int mode, double frac_scale, size_t elems, int replicas,
                                 double scale, double *out, cudaStream_t s);
 cudaError_t launch_trace_single_f32(const TraceP<float> &p, int block, cudaStream_t s);

@@ -107,7 +107,8 @@ class qmcrt_adam(C.Structure):
 
 class qmcrt_host_io(C.Structure):
     _fields_ = [("struct_size", C.c_uint32), ("reserved", C.c_int32), ("h_k", C.c_void_p), ("d_k", C.c_void_p),
-                ("d_accum", C.c_void_p), ("d_image", C.c_void_p), ("h_image", C.c_void_p)]
+                ("d_accum", C.c_void_p), ("d_image", C.c_void_p), ("h_image", C.c_void_p), ("d_sky_ws", C.c_void_p),
+                ("sky_ws_bytes", C.c_uint64)]
 
 
 def _new(cls, **kw):
@@ -163,8 +164,10 @@ _SIGS = [
                                   C.c_void_p, C.c_uint64, C.c_void_p]),
     ("qmcrt_warp_adam", C.c_int, [_P(qmcrt_warp), C.c_void_p, C.c_void_p, C.c_void_p, _P(qmcrt_adam), C.c_void_p]),
     ("qmcrt_pad_grid", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
+    ("qmcrt_sky_workspace_bytes", C.c_uint64, [C.c_int32, C.c_int32, C.c_int32, _P(C.c_double), _P(C.c_double),
+                                               C.c_double]),
     ("qmcrt_sky_bound", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, _P(C.c_double), _P(C.c_double),
-                                  C.c_double, C.c_int32, C.c_void_p, C.c_void_p]),
+                                  C.c_double, C.c_int32, C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p]),
     ("qmcrt_trace_single_noalloc", C.c_int, [_P(qmcrt_medium), _P(qmcrt_source), _P(qmcrt_dust),
                                              _P(qmcrt_observer), _P(qmcrt_points_desc), _P(qmcrt_trace_opts),
                                              C.c_int32, C.c_double, C.c_void_p, C.c_void_p]),
@@ -373,10 +376,15 @@ def qmcrt_pad_grid(d_k: int, nx: int, ny: int, nz: int, pad: int, d_padded: int,
 MAX_OBSERVERS = 16
 
 
-def qmcrt_sky_bound(d_k: int, nx: int, ny: int, nz: int, lo, hi, radius: float, m: int, d_map: int,
-                    stream: int = 0) -> None:
+def qmcrt_sky_workspace_bytes(nx: int, ny: int, nz: int, lo, hi, radius: float) -> int:
+    return load().qmcrt_sky_workspace_bytes(nx, ny, nz, (C.c_double * 3)(*lo), (C.c_double * 3)(*hi), float(radius))
+
+
+def qmcrt_sky_bound(d_k: int, nx: int, ny: int, nz: int, lo, hi, radius: float, m: int, d_map: int, d_ws: int,
+                    ws_bytes: int, stream: int = 0) -> None:
     _check(load().qmcrt_sky_bound(C.c_void_p(d_k), nx, ny, nz, (C.c_double * 3)(*lo), (C.c_double * 3)(*hi),
-                                  float(radius), m, C.c_void_p(d_map), C.c_void_p(stream)))
+                                  float(radius), m, C.c_void_p(d_map), C.c_void_p(d_ws), ws_bytes,
+                                  C.c_void_p(stream)))
 
 
 def qmcrt_wavefront_workspace_bytes(max_packets: int, precision: str = "f32") -> int:
@@ -528,15 +536,19 @@ class Scene:
             self.medium = _new(qmcrt_medium, kind=MEDIUM_GRID, d_k=d_k, nx=nx, ny=ny, nz=nz, pad=pad,
                                kscale=prob.kscale)
             if sky is None:
-                # by default a point source only: over a finite star's ball the bound is loose
-                # (12 % of the disk's unscatterable rays certified) and the grown cells make the
-                # map costly to build (0.27 s on the 256^3 disk)
-                sky = SKY_M if prob.source == "point" else 0
+                # by default a point source only (over a finite star's ball the bound is loose:
+                # steep rays from its edge reach the disk's dense inner rim), with at least
+                # 1.25 texels per cell along a face so that a texel's cone stays within a cell
+                sky = max(SKY_M, 1 << math.ceil(math.log2(1.25 * max(nx, ny, nz)))) if prob.source == "point" else 0
+                sky = min(sky, 4096)
             if sky:
+                r = prob.star_r if prob.source == "sphere" else 0.0
                 self.sky = torch.empty((6, sky, sky), dtype=torch.float64, device=device)
+                self.sky_ws_bytes = qmcrt_sky_workspace_bytes(nx, ny, nz, prob.lo, prob.hi, r)
+                self.sky_ws = torch.empty(self.sky_ws_bytes // 8 + 32, dtype=torch.float64, device=device)
                 self.medium.d_sky = self.sky.data_ptr()
                 self.medium.sky_m = sky
-                self.medium.sky_r = prob.star_r if prob.source == "sphere" else 0.0
+                self.medium.sky_r = r
         else:
             self.grid = None
             self.medium = _new(qmcrt_medium, kind=MEDIUM_SPHERE, d_k=None, kscale=prob.kscale,
@@ -561,7 +573,8 @@ class Scene:
             qmcrt_pad_grid(self.grid.data_ptr(), nx, ny, nz, self.pad, self.padded.data_ptr(), _stream(stream))
         if self.sky is not None:
             qmcrt_sky_bound(self.grid.data_ptr(), nx, ny, nz, self.prob.lo, self.prob.hi, self.medium.sky_r,
-                            self.sky.shape[-1], self.sky.data_ptr(), _stream(stream))
+                            self.sky.shape[-1], self.sky.data_ptr(), self.sky_ws.data_ptr(), self.sky_ws_bytes,
+                            _stream(stream))
 
     def opts(self, precision: str = "f32", block_size: int = 0) -> qmcrt_trace_opts:
         p = self.prob
@@ -728,12 +741,12 @@ class HostRenderer:
     qmcrt_render_single_host, the copy of the density grid from (pinned) host memory,
     its padding, the trace of a packet range, the reduction and the copy of the image
     back to host memory, all on one stream.  Device buffers are allocated once, at
-    construction.  A grid that arrives anew with every call gets no bound map by default
-    (sky=0): rebuilding it (tens of ms on a 256^3 grid) costs more than it saves on one
-    trace of 2^26 packets."""
+    construction.  The bound map of rays from the source (for a point source) is rebuilt
+    from every new grid inside the call (2 ms on the 256^3 disk against the 4 ms it saves on
+    a trace of 2^26 packets); sky=0 walks every ray instead."""
 
     def __init__(self, prob: scenes.Problem, max_packets: int, *, precision: str = "f32",
-                 frac_bits: int | None = None, sky: int = 0):
+                 frac_bits: int | None = None, sky: int | None = None):
         torch = _torch()
         if prob.max_orders > 1:
             raise QmcrtError(ERR_UNSUPPORTED, "HostRenderer renders single scattering")
@@ -753,7 +766,9 @@ class HostRenderer:
         sc, p = self.scene, self.scene.prob
         io = _new(qmcrt_host_io, h_k=None if sc.grid is None else host_grid.data_ptr(),
                   d_k=None if sc.grid is None else sc.grid.data_ptr(), d_accum=self.buf.data_ptr(),
-                  d_image=self.out.data_ptr(), h_image=host_out.data_ptr())
+                  d_image=self.out.data_ptr(), h_image=host_out.data_ptr(),
+                  d_sky_ws=None if sc.sky is None else sc.sky_ws.data_ptr(),
+                  sky_ws_bytes=0 if sc.sky is None else sc.sky_ws_bytes)
         pts = points_desc(p.generator, p.dims, first, count, "f64", p.seed, p.total_n)
         qmcrt_render_single_host(sc.medium, sc.source, sc.dust, sc.obs, pts, sc.opts(self.precision), io,
                                  self.frac_bits, 1.0 / count, _stream(stream))

@@ -302,14 +302,16 @@ def test_contribution_bound_holds_through_scattering_and_peel_off(g, albedo, p_l
 
 def test_sky_bound_validation(lib):
     lo, hi = [-1.0] * 3, [1.0] * 3
-    _expect(Q.ERR_INVALID_ARG, Q.qmcrt_sky_bound, 0, 4, 4, 4, lo, hi, 0.0, 16, 0x2000)
-    _expect(Q.ERR_INVALID_ARG, Q.qmcrt_sky_bound, 0x1000, 4, 4, 4, lo, hi, 0.0, 16, 0)
-    _expect(Q.ERR_INVALID_ARG, Q.qmcrt_sky_bound, 0x1000, 0, 4, 4, lo, hi, 0.0, 16, 0x2000)
-    _expect(Q.ERR_INVALID_ARG, Q.qmcrt_sky_bound, 0x1000, 4, 4, 4, lo, [1.0, -1.0, 1.0], 0.0, 16, 0x2000)
-    for r in (-0.1, float("nan")):
-        _expect(Q.ERR_INVALID_ARG, Q.qmcrt_sky_bound, 0x1000, 4, 4, 4, lo, hi, r, 16, 0x2000)
-    for m in (0, 4097):
-        _expect(Q.ERR_INVALID_ARG, Q.qmcrt_sky_bound, 0x1000, 4, 4, 4, lo, hi, 0.0, m, 0x2000)
+    ws = Q.qmcrt_sky_workspace_bytes(4, 4, 4, lo, hi, 0.0)
+    assert ws == 2 * ((6 ** 3 * 4 + 255) // 256 * 256)  # two grids grown by one layer
+    assert Q.qmcrt_sky_workspace_bytes(4, 4, 4, lo, hi, 0.6) > ws  # a star grows them further
+    assert Q.qmcrt_sky_workspace_bytes(0, 4, 4, lo, hi, 0.0) == 0
+    good = [0x1000, 4, 4, 4, lo, hi, 0.0, 16, 0x2000, 0x4000, ws]
+    for i, bad in ((0, 0), (8, 0), (9, 0), (9, 0x4010), (10, ws - 1), (1, 0), (5, [1.0, -1.0, 1.0]), (6, -0.1),
+                   (6, float("nan")), (7, 0), (7, 4097)):
+        a = list(good)
+        a[i] = bad
+        _expect(Q.ERR_INVALID_ARG, Q.qmcrt_sky_bound, *a)
     # a trace rejects a bound map of impossible size
     g = _descs(medium__kind=0, medium__d_k=0x5000, medium__nx=4, medium__ny=4, medium__nz=4, medium__d_sky=0x6000,
                medium__sky_m=0)

