@@ -151,7 +151,7 @@ def write_tables() -> str:
     lines.append("}")
     lines.append(f"#define QMCRT_GEN_SOBOL_BYTE_DIMS {SOBOL_BYTE_DIMS}")
     lines.append("#define QMCRT_GEN_SOBOL_BYTE_INIT { \\")
-    for per in sobol_byte_table(V):
+    for per in sobol_byte_table(V, SOBOL_BYTE_DIMS):
         lines.append("  { \\")
         for row in per:
             lines.append("    {" + ",".join(f"0x{v:08x}u" for v in row) + "}, \\")
