@@ -132,3 +132,34 @@ def test_batched_finite_star_is_unchanged_by_the_map(Q):
         torch.cuda.synchronize()
         outs.append(B.accum.clone())
     assert torch.equal(outs[0], outs[1])
+
+
+def test_edge_cases_of_the_map(Q):
+    """An empty grid (every ray skipped, nothing scattered), a single dense cell beside the
+    source (rays through it walked, the rest skipped), tau_min = 0 (nothing may be skipped)
+    and a coarse map whose texel cones are too wide for the grid (infinite bounds: every ray
+    walked): each image equals the one traced without the map."""
+    import torch
+
+    one = np.zeros((16, 16, 16), dtype=np.float32)
+    one[8, 8, 9] = 40.0  # the cell just above-right of the origin (a grid vertex)
+    cases = [S.flared_disk_problem(n=16).replace(grid=np.zeros((16, 16, 16), dtype=np.float32)),
+             S.Problem(grid=one, nx=24, ny=24),
+             S.flared_disk_problem(n=32, nx=24, ny=24, tau_min=0.0),
+             S.flared_disk_problem(n=64, nx=24, ny=24)]
+    for prob, sky in zip(cases, (64, 64, 64, 8)):
+        N = 1 << 13
+        fb = Q.default_frac_bits(prob, N)
+        imgs = []
+        for m in (0, sky):
+            sc = Q.Scene(prob, sky=m)
+            buf = sc.accum_buffer("i64")
+            sc.trace(1, N, buf, frac_bits=fb)
+            imgs.append(buf)
+        torch.cuda.synchronize()
+        assert torch.equal(imgs[0], imgs[1])
+        if sky == 8:  # 8 texels per face edge over 64 cells: every texel's cone is too wide
+            assert torch.isinf(Q.Scene(prob, sky=8).sky).all()
+    sc = Q.Scene(cases[0], sky=64)
+    torch.cuda.synchronize()
+    assert torch.all(sc.sky == 0)
