@@ -538,7 +538,8 @@ typedef struct qmcrt_host_io {
  * device buffers are the caller's; the library allocates nothing.
  * Errors: as qmcrt_trace_single; INVALID_ARG for a NULL or mis-sized io, NULL d_accum,
  * d_image or h_image, h_k for a sphere medium, a padded medium without d_k or with
- * d_k == medium->d_k; CUDA for a failed copy.
+ * d_k == medium->d_k, a medium with a bound map without a large enough, 256-byte aligned
+ * d_sky_ws; CUDA for a failed copy.
  */
 int qmcrt_render_single_host(const qmcrt_medium *medium, const qmcrt_source *source, const qmcrt_dust *dust,
                              const qmcrt_observer *obs, const qmcrt_points_desc *pts, const qmcrt_trace_opts *opts,

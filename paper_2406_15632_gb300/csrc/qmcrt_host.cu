@@ -111,6 +111,14 @@ int qmcrt_render_single_host(const qmcrt_medium *medium, const qmcrt_source *sou
         return qmcrt::set_error(QMCRT_ERR_INVALID_ARG, "a padded grid needs d_k to receive h_k");
     if (copy_grid && medium->pad > 0 && io->d_k == medium->d_k)
         return qmcrt::set_error(QMCRT_ERR_INVALID_ARG, "d_k must not be the padded grid medium->d_k");
+    if (copy_grid && medium->d_sky) {  // the bound map is rebuilt from the new grid: its workspace first
+        const uint64_t need = qmcrt_sky_workspace_bytes(medium->nx, medium->ny, medium->nz, medium->lo, medium->hi,
+                                                        medium->sky_r);
+        if (!io->d_sky_ws || io->sky_ws_bytes < need || ((uintptr_t)io->d_sky_ws & 255) != 0)
+            return qmcrt::set_error(QMCRT_ERR_INVALID_ARG,
+                                    "a grid with a bound map needs d_sky_ws of %llu bytes, 256-byte aligned",
+                                    (unsigned long long)need);
+    }
     qmcrt_image im;
     memset(&im, 0, sizeof im);
     im.struct_size = sizeof im;

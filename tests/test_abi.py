@@ -265,6 +265,17 @@ def test_render_single_host_validation(lib):
     _expect(Q.ERR_INVALID_ARG, call, g, bad)
     bad.d_k = 0x5000  # ... distinct from the padded grid
     _expect(Q.ERR_INVALID_ARG, call, g, bad)
+    # a bound map is rebuilt from the new grid: its workspace is checked before anything runs
+    g2 = _descs(medium__kind=0, medium__d_k=0x5000, medium__nx=4, medium__ny=4, medium__nz=4, medium__pad=8,
+                medium__d_sky=0x6000, medium__sky_m=16)
+    for a in range(3):
+        g2["medium"].lo[a], g2["medium"].hi[a] = -1.0, 1.0
+    ok = Q.qmcrt_host_io.from_buffer_copy(io)
+    ok.h_k, ok.d_k = 0x4000, 0x7000
+    for ws, nbytes in ((None, 0), (0x8000, 16), (0x8010, 1 << 20)):
+        b = Q.qmcrt_host_io.from_buffer_copy(ok)
+        b.d_sky_ws, b.sky_ws_bytes = ws, nbytes
+        _expect(Q.ERR_INVALID_ARG, call, g2, b)
     for over in BAD_TRACE[:8]:
         _expect(Q.ERR_INVALID_ARG, call, _descs(**over), io)
 
