@@ -272,11 +272,12 @@ def default_threads() -> int:
 
 def trace_single(prob, first: int, count: int, log: bool = False, nthreads: int | None = None):
     """Raw image sums [3][ny][nx] (not divided by N) of packets first..first+count-1,
-    and optionally the per-packet log [count][10]: scattering x, y, z, peel-off I, Q, U,
-    sky x, y, status, grid cells visited."""
+    and optionally the per-packet log [count][11]: scattering x, y, z, peel-off I, Q, U,
+    sky x, y, status, grid cells visited, and of those the cells the march to the scattering
+    point visited."""
     h = _Holder(prob)
     img = np.zeros((3, prob.ny, prob.nx), dtype=np.float64)
-    lg = np.zeros((count, 10), dtype=np.float64) if log else None
+    lg = np.zeros((count, 11), dtype=np.float64) if log else None
     rc = lib().or_trace_single(h.ptr, first, count, img.ctypes.data_as(C.POINTER(C.c_double)),
                                lg.ctypes.data_as(C.POINTER(C.c_double)) if log else None,
                                nthreads or default_threads())
@@ -327,10 +328,11 @@ def direct_light(prob, subsamples: int = 4, weight: float = 1.0):
 
 
 def multiple_cells(prob, first: int, count: int):
-    """Grid cells visited per packet by the multiple-scattering tracer (one thread)."""
+    """Grid cells visited per packet by the multiple-scattering tracer (one thread):
+    [count][2], all walks and, of those, the marches of forced steps."""
     h = _Holder(prob)
     img = np.zeros((prob.n_images, 3, prob.ny, prob.nx), dtype=np.float64)
-    cells = np.zeros(count, dtype=np.float64)
+    cells = np.zeros((count, 2), dtype=np.float64)
     dp = C.POINTER(C.c_double)
     rc = lib().or_trace_multiple_cells(h.ptr, first, count, img.ctypes.data_as(dp), cells.ctypes.data_as(dp))
     if rc != 0:

@@ -479,6 +479,7 @@ static int or_start_cell(double x, double lo, double h, double dir)
 /* Cells visited by the walks of the packet being traced on this thread (a count of the
  * algorithm's work, reported in the packet log). */
 static _Thread_local long long or_cells_visited;
+static _Thread_local long long or_cells_marched; /* of those, visited by forced-step marches */
 
 static int or_grid_walk(const or_medium *M, const double p[3], const double d[3], double target,
                         double *tau_sum, double *t_hit, double *t_last)
@@ -808,13 +809,15 @@ static int or_forced_step(const or_problem *Pr, double pos[3], const double dir[
     double W1 = -expm1(-tau1);
     double tau = -log1p(-w * W1);
     double q[3];
+    const long long before = or_cells_visited;
     or_march(&Pr->medium, pos, dir, tau, q); /* a miss only by rounding: q = last nonempty end */
+    or_cells_marched += or_cells_visited - before;
     for (int a = 0; a < 3; ++a) pos[a] = q[a];
     *W1_out = W1;
     return 1;
 }
 
-#define OR_LOG_COLS 10
+#define OR_LOG_COLS 11
 
 typedef struct {
     const or_problem *Pr;
@@ -835,6 +838,7 @@ static void or_trace_single_range(const or_problem *Pr, uint64_t first, uint64_t
         uint64_t i = first + j;
         double pos[3], dir[3], eref[3], wgt, W1 = 0, tau1 = 0, S[3], out[3], x = 0, y = 0;
         or_cells_visited = 0;
+        or_cells_marched = 0;
         double w = or_emit_single(&Pr->source, &Pr->points, i, pos, dir, eref, &wgt);
         int status = 0;
         out[0] = out[1] = out[2] = 0;
@@ -852,6 +856,7 @@ static void or_trace_single_range(const or_problem *Pr, uint64_t first, uint64_t
             r[3] = out[0]; r[4] = out[1]; r[5] = out[2];
             r[6] = x; r[7] = y; r[8] = status;
             r[9] = (double)or_cells_visited;
+            r[10] = (double)or_cells_marched;
         }
     }
 }
@@ -902,6 +907,7 @@ static void or_trace_multiple_range(const or_problem *Pr, uint64_t first, uint64
         uint64_t i = first + j;
         double pos[3], n[3], a[3], wgt, w, total = 0.0, total2 = 0.0;
         or_cells_visited = 0;
+        or_cells_marched = 0;
         double x0 = or_point_f64(&Pr->points, i, 0), x1 = or_point_f64(&Pr->points, i, 1);
         if (wx) {
             /* Learned proposal: the first-order coordinates are x = T(u), and the
@@ -965,7 +971,10 @@ static void or_trace_multiple_range(const or_problem *Pr, uint64_t first, uint64
             tlog[5 * j + 3] = total;
             tlog[5 * j + 4] = sqrt(total2);
         }
-        if (cells) cells[j] = (double)or_cells_visited;
+        if (cells) {
+            cells[2 * j] = (double)or_cells_visited;
+            cells[2 * j + 1] = (double)or_cells_marched;
+        }
     }
 }
 
@@ -980,7 +989,8 @@ static void *or_worker(void *arg)
 /* Trace packets first .. first+count-1 on nthreads threads; adds the raw sums
  * (not divided by N) to image; log (optional, single only) gets OR_LOG_COLS doubles per
  * packet: scattering position, peel-off I, Q, U, sky x, y, status (0 ok, 1 tau_1 <
- * tau_min, 2 occulted), grid cells visited by the packet's walks. */
+ * tau_min, 2 occulted), grid cells visited by the packet's walks, and of those the cells
+ * visited by the march to the scattering point (a second pass over cells of the first walk). */
 static int or_trace(const or_problem *Pr, uint64_t first, uint64_t count, double *image, double *log,
                     int nthreads, int multiple, const double *wx, const double *wlogj, double *tlog)
 {
@@ -1089,7 +1099,8 @@ int or_direct_light(const or_problem *Pr, int S, double weight, double *img)
 }
 
 /* Grid cells visited by all walks of each packet of the multiple-scattering tracer
- * (one thread); the image goes to `image`.  The per-unit work figure of the
+ * (one thread), and of those the cells visited by the marches of forced steps:
+ * cells[2 j], cells[2 j + 1]; the image goes to `image`.  The per-unit work figure of the
  * multiple-scattering kernel's roofline. */
 int or_trace_multiple_cells(const or_problem *Pr, uint64_t first, uint64_t count, double *image, double *cells)
 {

@@ -26,6 +26,9 @@ def main():
         # the walks a tracer must take when rays whose tau_1 lies below tau_min are known
         # not to scatter without walking them (they count as no cells)
         "cells_per_packet_scattering_rays": float((log[:, 9] * (log[:, 8] != 1)).mean()),
+        # and when the march to the scattering point does not walk again the cells of the
+        # first walk that lie before it (each cell of the ray is walked once, plus the peel-off)
+        "cells_per_packet_scattering_rays_single_pass": float(((log[:, 9] - log[:, 10]) * (log[:, 8] != 1)).mean()),
         "packets": N,
         "contributing_fraction": float((log[:, 8] == 0).mean()),
         "note": "256^3 flared disk, point source, Sobol indices 1..2^18, all three walks per packet",
@@ -34,7 +37,9 @@ def main():
     n_multi = 1 << 14
     cells = O.multiple_cells(clumpy, n_multi, n_multi)
     out["clumpy_multiple_scattering"] = {
-        "cells_per_packet": float(cells.mean()),
+        "cells_per_packet": float(cells[:, 0].mean()),
+        # without the forced steps' second passes over cells of their first walks
+        "cells_per_packet_single_pass": float((cells[:, 0] - cells[:, 1]).mean()),
         "packets": n_multi,
         "note": "128^3 clumpy envelope, 20 orders, forced, roulette 1e-4, Sobol indices 2^14..2^15-1, "
                 "all walks of all orders per packet",
