@@ -30,7 +30,7 @@
 extern "C" {
 #endif
 
-#define QMCRT_ABI_VERSION 2
+#define QMCRT_ABI_VERSION 3
 
 /* ---- status codes ---- */
 #define QMCRT_OK 0
@@ -134,6 +134,9 @@ typedef struct qmcrt_observer {
     double theta, phi;  /* direction toward the observer, polar and azimuth angles */
     double half_width;  /* the image covers [-hw, hw]^2 of the sky plane */
     int32_t nx, ny;     /* pixels */
+    const uint8_t *d_tail; /* optional (NULL): device map of qmcrt_tail_map for the medium's padded grid and
+                              this direction; peel-off walks toward this observer then stop once the map
+                              bounds the optical depth still ahead by opts->tail_eps */
 } qmcrt_observer;
 /* Sky axes: ex = (-sin phi, cos phi, 0), ey = (-cos theta cos phi, -cos theta sin phi,
  * sin theta); (ex, ey, k) is right-handed.  Stokes Q > 0 along ey, U > 0 along
@@ -168,6 +171,9 @@ typedef struct qmcrt_trace_opts {
     double rr_survival;    /* survival probability (0, 1]; survivors' weight / rr_survival */
     int32_t per_order;     /* 1: image k-1 receives scattering order k */
     int32_t block_size;    /* threads per block, 0 = library default (multiple of 32, <= 1024) */
+    double tail_eps;       /* observers with a d_tail map: the optical depth (with kscale) a peel-off walk
+                              may leave out, >= 0; e^{-tau_obs} then grows by at most that fraction
+                              (0: only what the map bounds by zero) */
 } qmcrt_trace_opts;
 
 /*
@@ -485,6 +491,37 @@ int qmcrt_sky_bound(const float *d_k, int32_t nx, int32_t ny, int32_t nz, const 
                     void *stream);
 
 /*
+ * qmcrt_tail_map -- for an observer direction k (Sec. 3.6: the peel-off walks all run
+ * along k): d_map, device uint8 [nz+2pad][ny+2pad][nx+2pad] (the padded grid's layout,
+ * qmcrt_tail_map_bytes), receives per cell a code c bounding the optical depth (kappa rho
+ * without kscale) from any point of the cell along k to the edge of the grid: c = 0, no
+ * depth; 1 <= c <= 254, at most 2^(c - 150); 255, no bound.  Padding cells hold 0.
+ * Construction: the grid's cells are grouped in 4^3 blocks, each holding the largest value
+ * of its cells; slabs of blocks are taken across the axis a of largest |k_a| / h_a, so that
+ * along each other axis the walk's cells move by at most one block width per slab (plus one
+ * cell of rounding), that is over at most three blocks (one where k has no component); a
+ * ray from a block crosses its slab over at most 4 h_a / |k_a| and enters the next slab in
+ * one of those lateral blocks, so the bound of a block is that length (times 1 + 1e-6)
+ * times the largest value among its slab's lateral blocks, plus the largest bound among
+ * the next slab's, summed slab by slab from the side k leaves through (upward roundings).
+ * medium: a grid with pad >= QMCRT_MIN_PAD (d_k the padded array of qmcrt_pad_grid);
+ * obs: theta and phi give k, as the tracer computes it; d_workspace: device, 256-byte
+ * aligned, >= qmcrt_tail_workspace_bytes (two arrays of block values).  Pass the map in
+ * qmcrt_observer.d_tail: a peel-off walk toward that observer checks, with the density
+ * loads of each batch of cells, the code of the batch's first cell and stops after the
+ * batch once 2^(c - 150) kscale <= opts->tail_eps (or c = 0).  Rebuild the map whenever the
+ * grid or the direction changes.  The walk's optical depth then falls short of the full
+ * walk's by at most tail_eps.
+ * Errors: INVALID_ARG (NULL pointers or wrong struct_size, a medium that is not a padded
+ * grid, an empty box, a direction that is not finite, a small or misaligned workspace),
+ * CUDA.
+ */
+uint64_t qmcrt_tail_map_bytes(int32_t nx, int32_t ny, int32_t nz, int32_t pad);
+uint64_t qmcrt_tail_workspace_bytes(int32_t nx, int32_t ny, int32_t nz);
+int qmcrt_tail_map(const qmcrt_medium *medium, const qmcrt_observer *obs, uint8_t *d_map, void *d_workspace,
+                   uint64_t workspace_bytes, void *stream);
+
+/*
  * qmcrt_contribution_bound -- *bound = the largest |I|, |Q| or |U| one peel-off
  * contribution can carry (Sec. 2.2, 3.5, 3.6), for the source (limb weight at most
  * 1 / (1 - u/3)), dust and options given; multiple != 0 takes opts->max_orders orders and
@@ -524,14 +561,17 @@ typedef struct qmcrt_host_io {
     double *h_image;    /* host [3][ny][nx]: receives the image (pinned memory keeps the call asynchronous) */
     void *d_sky_ws;     /* device workspace of qmcrt_sky_bound (needed when medium->d_sky is given) */
     uint64_t sky_ws_bytes;
+    void *d_tail_ws;    /* device workspace of qmcrt_tail_map (needed when obs->d_tail is given) */
+    uint64_t tail_ws_bytes;
 } qmcrt_host_io;
 
 /*
  * qmcrt_render_single_host -- one end-to-end single-scattering render for a caller whose
  * inputs and outputs live in host memory (Sec. 3.2-3.6): enqueues on stream the copy of
  * io->h_k to the device (one cudaMemcpyAsync), its sentinel padding (qmcrt_pad_grid,
- * when medium->pad > 0) and bound map (qmcrt_sky_bound into medium->d_sky, when given),
- * the clearing of io->d_accum, qmcrt_trace_single with fixed-point
+ * when medium->pad > 0), bound map (qmcrt_sky_bound into medium->d_sky, when given) and
+ * tail map (qmcrt_tail_map into obs->d_tail, when given), the clearing of io->d_accum,
+ * qmcrt_trace_single with fixed-point
  * accumulation at frac_bits, qmcrt_image_reduce with scale (normally 1/N) into
  * io->d_image, and the copy of that image to io->h_image (one cudaMemcpyAsync).  The
  * call returns after enqueuing: synchronize the stream before reading h_image.  The
@@ -539,7 +579,7 @@ typedef struct qmcrt_host_io {
  * Errors: as qmcrt_trace_single; INVALID_ARG for a NULL or mis-sized io, NULL d_accum,
  * d_image or h_image, h_k for a sphere medium, a padded medium without d_k or with
  * d_k == medium->d_k, a medium with a bound map without a large enough, 256-byte aligned
- * d_sky_ws; CUDA for a failed copy.
+ * d_sky_ws, an observer with a tail map without such a d_tail_ws; CUDA for a failed copy.
  */
 int qmcrt_render_single_host(const qmcrt_medium *medium, const qmcrt_source *source, const qmcrt_dust *dust,
                              const qmcrt_observer *obs, const qmcrt_points_desc *pts, const qmcrt_trace_opts *opts,

@@ -24,7 +24,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["qmcrt_api.cu", "qmcrt_points.cu", "qmcrt_trace_single.cu", "qmcrt_trace_multiple.cu",
            "qmcrt_noalloc.cu", "qmcrt_batch.cu", "qmcrt_mlp.cu", "qmcrt_flow.cu", "qmcrt_warp_fused.cu",
            "qmcrt_trace_observers.cu", "qmcrt_direct.cu", "qmcrt_wavefront.cu", "qmcrt_host.cu",
-           "qmcrt_sky.cu"]
+           "qmcrt_sky.cu", "qmcrt_tail.cu"]
 
 
 def _joe_kuo():

@@ -275,6 +275,23 @@ int make_obs(const qmcrt_observer *ob, qmcrt::ObsP<T> &O)
     O.nx = ob->nx;
     O.ny = ob->ny;
     O.splat = ob->splat;
+    O.tail = nullptr;
+    O.tail_thr = 0;
+    return QMCRT_OK;
+}
+
+// The observer's tail map (qmcrt_tail_map), if given: valid on a padded grid only; the
+// threshold code follows from the tolerance and the medium's kscale.
+template <class T>
+int attach_tail(const qmcrt_medium *md, const qmcrt_observer *ob, const qmcrt_trace_opts *op, qmcrt::ObsP<T> &O)
+{
+    if (!ob->d_tail) return QMCRT_OK;
+    if (md->kind != QMCRT_MEDIUM_GRID || md->pad < QMCRT_MIN_PAD)
+        return fail(QMCRT_ERR_INVALID_ARG, "a tail map needs a padded grid medium");
+    if (!(op->tail_eps >= 0) || !std::isfinite(op->tail_eps))
+        return fail(QMCRT_ERR_INVALID_ARG, "tail_eps must be finite and >= 0");
+    O.tail = ob->d_tail;
+    O.tail_thr = qmcrt::tail_threshold(op->tail_eps, md->kscale);
     return QMCRT_OK;
 }
 
@@ -360,6 +377,7 @@ int fill_trace(const qmcrt_medium *md, const qmcrt_source *src, const qmcrt_dust
     // observer
     {
         int rc = make_obs(ob, P.obs);
+        if (!rc) rc = attach_tail(md, ob, op, P.obs);
         if (rc) return rc;
     }
     // options
@@ -496,6 +514,7 @@ int observers_common(const qmcrt_medium *md, const qmcrt_source *src, const qmcr
     S.stack = (size_t)im->n_images * 3 * P.acc.plane;
     for (int o = 0; o < n_obs; ++o) {
         if ((rc = make_obs(&obs[o], S.o[o]))) return rc;
+        if ((rc = attach_tail(md, &obs[o], op, S.o[o]))) return rc;
         if (obs[o].nx != obs[0].nx || obs[o].ny != obs[0].ny || obs[o].splat != obs[0].splat)
             return fail(QMCRT_ERR_INVALID_ARG, "observer %d: nx, ny and splat must equal observer 0's", o);
     }
@@ -832,6 +851,51 @@ int qmcrt_sky_bound(const float *d_k, int32_t nx, int32_t ny, int32_t nz, const 
     return cuda_status(qmcrt::launch_sky_bound(d_k, nx, ny, nz, lo, hi, radius * (1.0 + 1e-4), m, d_map, d_workspace,
                                                (cudaStream_t)stream),
                        "sky_bound launch");
+}
+
+uint64_t qmcrt_tail_map_bytes(int32_t nx, int32_t ny, int32_t nz, int32_t pad)
+{
+    if (nx < 1 || ny < 1 || nz < 1 || pad < 0) return 0;
+    return (uint64_t)(nx + 2 * pad) * (ny + 2 * pad) * (nz + 2 * pad);
+}
+
+uint64_t qmcrt_tail_workspace_bytes(int32_t nx, int32_t ny, int32_t nz)
+{
+    if (nx < 1 || ny < 1 || nz < 1) return 0;
+    return qmcrt::tail_workspace_bytes(nx, ny, nz);
+}
+
+int qmcrt_tail_map(const qmcrt_medium *medium, const qmcrt_observer *obs, uint8_t *d_map, void *d_workspace,
+                   uint64_t workspace_bytes, void *stream)
+{
+    g_last_error.clear();
+    if (!medium || medium->struct_size != sizeof(qmcrt_medium))
+        return fail(QMCRT_ERR_INVALID_ARG, "medium is NULL or has the wrong struct_size");
+    if (!obs || obs->struct_size != sizeof(qmcrt_observer))
+        return fail(QMCRT_ERR_INVALID_ARG, "obs is NULL or has the wrong struct_size");
+    if (!d_map || !d_workspace) return fail(QMCRT_ERR_INVALID_ARG, "NULL map or workspace");
+    if (medium->kind != QMCRT_MEDIUM_GRID || !medium->d_k || medium->pad < QMCRT_MIN_PAD)
+        return fail(QMCRT_ERR_INVALID_ARG, "a tail map needs a padded grid medium (pad >= %d)", QMCRT_MIN_PAD);
+    const int nx = medium->nx, ny = medium->ny, nz = medium->nz, pad = medium->pad;
+    if (nx < 1 || ny < 1 || nz < 1) return fail(QMCRT_ERR_INVALID_ARG, "grid has zero cells");
+    if ((double)(nx + 2 * pad) * (ny + 2 * pad) * (nz + 2 * pad) > 2147483647.0)
+        return fail(QMCRT_ERR_INVALID_ARG, "padded grid larger than 2^31 cells");
+    for (int a = 0; a < 3; ++a)
+        if (!(medium->hi[a] > medium->lo[a]) || !std::isfinite(medium->hi[a] - medium->lo[a]))
+            return fail(QMCRT_ERR_INVALID_ARG, "grid box axis %d is empty", a);
+    if (!std::isfinite(obs->theta) || !std::isfinite(obs->phi))
+        return fail(QMCRT_ERR_INVALID_ARG, "observer direction not finite");
+    if (((uintptr_t)d_workspace & 255) != 0) return fail(QMCRT_ERR_INVALID_ARG, "workspace not 256-byte aligned");
+    const uint64_t need = qmcrt::tail_workspace_bytes(nx, ny, nz);
+    if (workspace_bytes < need)
+        return fail(QMCRT_ERR_INVALID_ARG, "workspace of %llu bytes, need %llu", (unsigned long long)workspace_bytes,
+                    (unsigned long long)need);
+    // the direction as the tracer computes it (make_obs); its zero components are exact
+    const double st = std::sin(obs->theta), ct = std::cos(obs->theta), sp = std::sin(obs->phi), cp = std::cos(obs->phi);
+    const double k[3] = {st * cp, st * sp, ct};
+    return cuda_status(qmcrt::launch_tail_map(medium->d_k, nx, ny, nz, pad, medium->lo, medium->hi, k, d_map,
+                                              d_workspace, (cudaStream_t)stream),
+                       "tail_map launch");
 }
 
 int qmcrt_pad_grid(const float *d_k, int32_t nx, int32_t ny, int32_t nz, int32_t pad, float *d_padded, void *stream)

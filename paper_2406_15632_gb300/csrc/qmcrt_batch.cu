@@ -74,6 +74,7 @@ __device__ __forceinline__ void set_instance(TraceP<T> &P, const TraceP<T> &base
     P.obs.ey[1] = (T)(-ct * sp);
     P.obs.ey[2] = (T)st;
     for (int a = 0; a < 3; ++a) P.obs.inv_k[a] = T(1) / P.obs.k[a];
+    P.obs.tail = nullptr;  // a tail map holds for one direction only
     // dust
     P.dust.albedo = (T)I.albedo;
     P.dust.g = (T)I.g;

@@ -656,6 +656,32 @@ __device__ __forceinline__ T padded_depth(const float *__restrict__ K, PaddedRay
     return acc - comp;
 }
 
+// The same depth toward an observer with a tail map (qmcrt_tail_map): the code of each
+// batch's first cell, loaded with the batch's densities, bounds the optical depth from that
+// cell to the edge; once it is at most thr the walk ends after the batch, leaving out at
+// most the bound the threshold stands for.
+template <class T>
+__device__ __forceinline__ T padded_depth_tail(const float *__restrict__ K, PaddedRay<T> &R,
+                                               const uint8_t *__restrict__ tail, int thr)
+{
+    T acc = T(0), comp = T(0);
+    for (;;) {
+        const int code = __ldg(tail + R.idx);
+        T L[WALK_UNROLL];
+        float kf[WALK_UNROLL];
+        const unsigned sign = padded_batch(K, R, L, kf);
+        T Bs = T(0);
+#pragma unroll
+        for (int u = 0; u < WALK_UNROLL; ++u) Bs = Mth<T>::fma_(L[u], (T)kf[u], Bs);
+        const T y = Bs - comp;
+        const T s2 = acc + y;
+        comp = (s2 - acc) - y;
+        acc = s2;
+        if ((sign & 0x80000000u) || code <= thr) break;
+    }
+    return acc - comp;
+}
+
 // The same depth, keeping two batch boundaries for a march to the forced depth
 // tau(tau_1) = -ln[1 - w (1 - e^{-tau_1})] along the same ray: a candidate B, and A, the
 // candidate last promoted (initially the start), in mk[ia ^ 1] and mk[ia] (local memory:
@@ -815,6 +841,19 @@ __device__ __forceinline__ T tau_to_edge(const MediumP<T> &G, const T p[3], cons
     if (G.pad) grid_walk_padded<T, false>(G, p, d, r, T(0), raw, t);
     else grid_walk<T, false>(G, p, d, r, T(0), raw, t);
     return Mth<T>::mul_(raw, G.kscale);
+}
+
+// Optical depth from p toward observer O (the peel-off walk), ended early by O's tail map
+// where the observer has one.
+template <class T>
+__device__ __forceinline__ T tau_toward(const MediumP<T> &G, const ObsP<T> &O, const T p[3])
+{
+    if (O.tail && G.kind == QMCRT_MEDIUM_GRID && G.pad) {
+        PaddedRay<T> R;
+        if (!padded_start(G, p, O.k, O.inv_k, R)) return T(0);
+        return Mth<T>::mul_(padded_depth_tail(G.k, R, O.tail, O.tail_thr), G.kscale);
+    }
+    return tau_to_edge(G, p, O.k, O.inv_k);
 }
 
 template <class T>
@@ -1094,7 +1133,7 @@ __device__ __forceinline__ bool peel_unpolarized(const TraceP<T> &P, const ObsP<
     x = dot3(pos, O.ex);
     y = dot3(pos, O.ey);
     if (occulted(P, O, pos)) return false;
-    const T tau_obs = tau_to_edge(P.med, pos, O.k, O.inv_k);
+    const T tau_obs = tau_toward(P.med, O, pos);
     const T mu = dot3(d, O.k);
     const T f = W0 * Mth<T>::exp_(-tau_obs) * hg_p11(P.dust, mu) * T(0.07957747154594767);  // 1/(4 pi)
     const T dx = dot3(d, O.ex), dy = dot3(d, O.ey);
@@ -1113,7 +1152,7 @@ __device__ __forceinline__ bool peel_polarized(const TraceP<T> &P, const ObsP<T>
     x = dot3(pos, O.ex);
     y = dot3(pos, O.ey);
     if (occulted(P, O, pos)) return false;
-    const T tau_obs = tau_to_edge(P.med, pos, O.k, O.inv_k);
+    const T tau_obs = tau_toward(P.med, O, pos);
     const T mu = dot3(n, O.k);
     const T inv1pm2 = T(1) / (T(1) + mu * mu);
     const T r12 = -P.dust.p_l * (T(1) - mu * mu) * inv1pm2;

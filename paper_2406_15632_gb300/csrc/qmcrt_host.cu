@@ -1,7 +1,7 @@
 // qmcrt_host.cu -- host-side entry points around the tracer: the fixed-point scale of an
 // accumulation (from a bound on one peel-off contribution), and single scattering with
-// host-resident inputs and outputs (copies, padding, trace, reduction and the copy back
-// enqueued on one stream).
+// host-resident inputs and outputs (copies, padding, maps, trace, reduction and the copy
+// back enqueued on one stream).
 #include <cmath>
 #include <cstring>
 
@@ -119,6 +119,13 @@ int qmcrt_render_single_host(const qmcrt_medium *medium, const qmcrt_source *sou
                                     "a grid with a bound map needs d_sky_ws of %llu bytes, 256-byte aligned",
                                     (unsigned long long)need);
     }
+    if (copy_grid && obs->d_tail) {  // so is the tail map
+        const uint64_t need = qmcrt_tail_workspace_bytes(medium->nx, medium->ny, medium->nz);
+        if (!io->d_tail_ws || io->tail_ws_bytes < need || ((uintptr_t)io->d_tail_ws & 255) != 0)
+            return qmcrt::set_error(QMCRT_ERR_INVALID_ARG,
+                                    "an observer with a tail map needs d_tail_ws of %llu bytes, 256-byte aligned",
+                                    (unsigned long long)need);
+    }
     qmcrt_image im;
     memset(&im, 0, sizeof im);
     im.struct_size = sizeof im;
@@ -146,6 +153,11 @@ int qmcrt_render_single_host(const qmcrt_medium *medium, const qmcrt_source *sou
             rc = qmcrt_sky_bound(medium->pad > 0 ? io->d_k : medium->d_k, medium->nx, medium->ny, medium->nz,
                                  medium->lo, medium->hi, medium->sky_r, medium->sky_m,
                                  const_cast<double *>(medium->d_sky), io->d_sky_ws, io->sky_ws_bytes, stream);
+            if (rc) return rc;
+        }
+        if (obs->d_tail) {  // and the tail map
+            rc = qmcrt_tail_map(medium, obs, const_cast<uint8_t *>(obs->d_tail), io->d_tail_ws, io->tail_ws_bytes,
+                                stream);
             if (rc) return rc;
         }
     }

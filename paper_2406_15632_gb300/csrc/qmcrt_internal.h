@@ -64,6 +64,8 @@ struct ObsP {
     T hw;                  // half width of the image
     T pix_x, pix_y;        // pixels per unit sky length: n / (2 hw)
     int nx, ny, splat;
+    const uint8_t *tail;   // optional qmcrt_tail_map codes for k on the padded grid (NULL: walk to the edge)
+    int tail_thr;          // a peel-off walk stops after a batch whose first cell's code is <= this
 };
 
 struct AccumP {
@@ -181,6 +183,14 @@ cudaError_t launch_sky_bound(const float *k, int nx, int ny, int nz, const doubl
                              double radius, int m, double *map, void *ws, cudaStream_t s);
 int sky_dilation(const double lo[3], const double hi[3], int nx, int ny, int nz, double radius);
 uint64_t sky_workspace_bytes(int nx, int ny, int nz, int D);
+
+// qmcrt_tail.cu: codes of a tail map (qmcrt_tail_map) for direction k over a padded grid
+constexpr int TAIL_BLOCK = 4;  // cells per block edge
+uint64_t tail_workspace_bytes(int nx, int ny, int nz);
+cudaError_t launch_tail_map(const float *k_padded, int nx, int ny, int nz, int pad, const double lo[3],
+                            const double hi[3], const double dir[3], uint8_t *map, void *ws, cudaStream_t s);
+// Largest code a walk may stop at for a depth tolerance eps (with kscale): 0 when eps is 0.
+int tail_threshold(double eps, double kscale);
 cudaError_t launch_image_reduce(const void *acc, int mode, double frac_scale, size_t elems, int replicas,
                                 double scale, double *out, cudaStream_t s);
 cudaError_t launch_trace_single_f32(const TraceP<float> &p, int block, cudaStream_t s);

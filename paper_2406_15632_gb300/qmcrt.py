@@ -33,6 +33,9 @@ FORCE = {"all": 0, "first": 1}
 MAX_DIMS = 256
 MIN_PAD = 8
 SKY_M = 512  # texels per cube-face edge of the bound map of rays from a point source
+# optical depth a peel-off walk with a tail map may leave out: in FP32 about one rounding of
+# e^{-tau_obs} (2^-24), in FP64 far below the 1e-10 agreement with the oracle
+TAIL_EPS = {"f32": 2.0 ** -24, "f64": 1e-13}
 
 
 class QmcrtError(RuntimeError):
@@ -65,7 +68,7 @@ class qmcrt_dust(C.Structure):
 
 class qmcrt_observer(C.Structure):
     _fields_ = [("struct_size", C.c_uint32), ("splat", C.c_int32), ("theta", C.c_double), ("phi", C.c_double),
-                ("half_width", C.c_double), ("nx", C.c_int32), ("ny", C.c_int32)]
+                ("half_width", C.c_double), ("nx", C.c_int32), ("ny", C.c_int32), ("d_tail", C.c_void_p)]
 
 
 class qmcrt_image(C.Structure):
@@ -76,7 +79,8 @@ class qmcrt_image(C.Structure):
 class qmcrt_trace_opts(C.Structure):
     _fields_ = [("struct_size", C.c_uint32), ("precision", C.c_int32), ("tau_min", C.c_double),
                 ("max_orders", C.c_int32), ("force_mode", C.c_int32), ("rr_threshold", C.c_double),
-                ("rr_survival", C.c_double), ("per_order", C.c_int32), ("block_size", C.c_int32)]
+                ("rr_survival", C.c_double), ("per_order", C.c_int32), ("block_size", C.c_int32),
+                ("tail_eps", C.c_double)]
 
 
 class qmcrt_instance(C.Structure):
@@ -108,7 +112,7 @@ class qmcrt_adam(C.Structure):
 class qmcrt_host_io(C.Structure):
     _fields_ = [("struct_size", C.c_uint32), ("reserved", C.c_int32), ("h_k", C.c_void_p), ("d_k", C.c_void_p),
                 ("d_accum", C.c_void_p), ("d_image", C.c_void_p), ("h_image", C.c_void_p), ("d_sky_ws", C.c_void_p),
-                ("sky_ws_bytes", C.c_uint64)]
+                ("sky_ws_bytes", C.c_uint64), ("d_tail_ws", C.c_void_p), ("tail_ws_bytes", C.c_uint64)]
 
 
 def _new(cls, **kw):
@@ -168,6 +172,10 @@ _SIGS = [
                                                C.c_double]),
     ("qmcrt_sky_bound", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, _P(C.c_double), _P(C.c_double),
                                   C.c_double, C.c_int32, C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p]),
+    ("qmcrt_tail_map_bytes", C.c_uint64, [C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
+    ("qmcrt_tail_workspace_bytes", C.c_uint64, [C.c_int32, C.c_int32, C.c_int32]),
+    ("qmcrt_tail_map", C.c_int, [_P(qmcrt_medium), _P(qmcrt_observer), C.c_void_p, C.c_void_p, C.c_uint64,
+                                 C.c_void_p]),
     ("qmcrt_trace_single_noalloc", C.c_int, [_P(qmcrt_medium), _P(qmcrt_source), _P(qmcrt_dust),
                                              _P(qmcrt_observer), _P(qmcrt_points_desc), _P(qmcrt_trace_opts),
                                              C.c_int32, C.c_double, C.c_void_p, C.c_void_p]),
@@ -194,7 +202,7 @@ def load(path: str = LIB_PATH):
                 f = getattr(L, name)
                 f.restype = res
                 f.argtypes = args
-            if L.qmcrt_abi_version() != 2:
+            if L.qmcrt_abi_version() != 3:
                 raise QmcrtError(ERR_UNSUPPORTED, "ABI version mismatch")
             _lib = L
     return _lib
@@ -387,6 +395,19 @@ def qmcrt_sky_bound(d_k: int, nx: int, ny: int, nz: int, lo, hi, radius: float, 
                                   C.c_void_p(stream)))
 
 
+def qmcrt_tail_map_bytes(nx: int, ny: int, nz: int, pad: int) -> int:
+    return int(load().qmcrt_tail_map_bytes(nx, ny, nz, pad))
+
+
+def qmcrt_tail_workspace_bytes(nx: int, ny: int, nz: int) -> int:
+    return int(load().qmcrt_tail_workspace_bytes(nx, ny, nz))
+
+
+def qmcrt_tail_map(medium, obs, d_map: int, d_ws: int, ws_bytes: int, stream: int = 0) -> None:
+    _check(load().qmcrt_tail_map(C.byref(medium), C.byref(obs), C.c_void_p(d_map), C.c_void_p(d_ws), ws_bytes,
+                                 C.c_void_p(stream)))
+
+
 def qmcrt_wavefront_workspace_bytes(max_packets: int, precision: str = "f32") -> int:
     return int(load().qmcrt_wavefront_workspace_bytes(max_packets, PREC[precision]))
 
@@ -514,15 +535,20 @@ class Scene:
     """The descriptor structs of one problem, with its grid resident on the device: the
     sentinel-padded copy the fast walk reads (pad > 0) and the bound map of rays from the
     source (qmcrt_sky_bound over the source's radius, sky texels per cube-face edge; 0:
-    none; None: SKY_M for a point source, none for a finite star)."""
+    none; None: SKY_M for a point source, none for a finite star), and for a padded grid
+    the tail map of the observer's direction (qmcrt_tail_map; None: for single scattering
+    only), with which peel-off walks stop once what is left of their optical depth is
+    below TAIL_EPS."""
 
     def __init__(self, prob: scenes.Problem, grid_device=None, device="cuda", pad: int = MIN_PAD,
-                 sky: int | None = None):
+                 sky: int | None = None, tail: bool | None = None):
         torch = _torch()
         self.prob = prob
         self.pad = pad
         self.padded = None
         self.sky = None
+        self.tail = None
+        self._tails = {}
         if prob.grid is not None:
             if grid_device is None:
                 grid_device = torch.as_tensor(prob.grid, dtype=torch.float32).to(device).contiguous()
@@ -562,10 +588,22 @@ class Scene:
         self.dust = _new(qmcrt_dust, albedo=prob.albedo, g=prob.g, p_l=prob.p_l)
         self.obs = _new(qmcrt_observer, splat=SPLAT[prob.splat], theta=prob.theta_obs, phi=prob.phi_obs,
                         half_width=prob.half_width, nx=prob.nx, ny=prob.ny)
+        if tail is None:
+            # by default for single scattering: on the 256^3 disk the peel-off walks drop from
+            # 13.1 to 10.3 ms per 2^26 packets; in the clumpy envelope, which fills its box's
+            # inscribed ball, the map seldom ends a walk and the 2^24-packet wavefront takes
+            # 93.8 ms with it against 88.8 without
+            tail = prob.max_orders == 1
+        if tail and self.padded is not None:
+            nz, ny, nx = self.grid.shape
+            self.tail = torch.empty(qmcrt_tail_map_bytes(nx, ny, nz, pad), dtype=torch.uint8, device=device)
+            self.tail_ws_bytes = qmcrt_tail_workspace_bytes(nx, ny, nz)
+            self.tail_ws = torch.empty(self.tail_ws_bytes // 8 + 32, dtype=torch.float64, device=device)
+            self.obs.d_tail = self.tail.data_ptr()
         self.repad()
 
     def repad(self, stream=None) -> None:
-        """Refresh the padded copy and the bound map after the grid changed."""
+        """Refresh the padded copy, the bound map and the tail map after the grid changed."""
         if self.grid is None:
             return
         nz, ny, nx = self.grid.shape
@@ -575,12 +613,16 @@ class Scene:
             qmcrt_sky_bound(self.grid.data_ptr(), nx, ny, nz, self.prob.lo, self.prob.hi, self.medium.sky_r,
                             self.sky.shape[-1], self.sky.data_ptr(), self.sky_ws.data_ptr(), self.sky_ws_bytes,
                             _stream(stream))
+        if self.tail is not None:
+            qmcrt_tail_map(self.medium, self.obs, self.tail.data_ptr(), self.tail_ws.data_ptr(), self.tail_ws_bytes,
+                           _stream(stream))
+            self._tails = {}  # maps toward other observers are rebuilt on demand
 
     def opts(self, precision: str = "f32", block_size: int = 0) -> qmcrt_trace_opts:
         p = self.prob
         return _new(qmcrt_trace_opts, precision=PREC[precision], tau_min=p.tau_min, max_orders=p.max_orders,
                     force_mode=FORCE[p.force], rr_threshold=p.rr_threshold, rr_survival=p.rr_survival,
-                    per_order=1 if p.per_order else 0, block_size=block_size)
+                    per_order=1 if p.per_order else 0, block_size=block_size, tail_eps=TAIL_EPS[precision])
 
     def accum_buffer(self, accum: str = "i64", replicas: int = 1):
         torch = _torch()
@@ -624,14 +666,33 @@ class Scene:
         qmcrt_direct_light(self.medium, self.source, self.obs, subsamples, weight, self.opts(precision),
                            self.image_desc(buf, accum, frac_bits), _stream(stream))
 
-    def observer_array(self, angles, half_widths=None):
+    def tail_for(self, theta: float, phi: float):
+        """The tail map toward (theta, phi) on this scene's grid (built once, rebuilt by
+        repad), or None without a padded grid or with tail maps off."""
+        if self.tail is None:
+            return None
+        if theta == self.prob.theta_obs and phi == self.prob.phi_obs:
+            return self.tail
+        key = (float(theta), float(phi))
+        if key not in self._tails:
+            torch = _torch()
+            t = torch.empty_like(self.tail)
+            obs = _new(qmcrt_observer, splat=self.obs.splat, theta=theta, phi=phi, half_width=1.0, nx=1, ny=1)
+            qmcrt_tail_map(self.medium, obs, t.data_ptr(), self.tail_ws.data_ptr(), self.tail_ws_bytes, 0)
+            self._tails[key] = t
+        return self._tails[key]
+
+    def observer_array(self, angles, half_widths=None, tails: bool = True):
         """ctypes array of observers at (theta, phi) pairs sharing this problem's image
-        shape and splat; half widths default to the problem's."""
+        shape and splat; half widths default to the problem's; each with the tail map of
+        its direction unless tails is False."""
         p = self.prob
         arr = (qmcrt_observer * len(angles))()
         for o, (th, ph) in enumerate(angles):
             hw = p.half_width if half_widths is None else half_widths[o]
-            arr[o] = _new(qmcrt_observer, splat=SPLAT[p.splat], theta=th, phi=ph, half_width=hw, nx=p.nx, ny=p.ny)
+            t = self.tail_for(th, ph) if tails else None
+            arr[o] = _new(qmcrt_observer, splat=SPLAT[p.splat], theta=th, phi=ph, half_width=hw, nx=p.nx, ny=p.ny,
+                          d_tail=None if t is None else t.data_ptr())
         return arr
 
     def trace_observers(self, angles, first: int, count: int, buf, *, half_widths=None, accum: str = "i64",
@@ -741,16 +802,16 @@ class HostRenderer:
     qmcrt_render_single_host, the copy of the density grid from (pinned) host memory,
     its padding, the trace of a packet range, the reduction and the copy of the image
     back to host memory, all on one stream.  Device buffers are allocated once, at
-    construction.  The bound map of rays from the source (for a point source) is rebuilt
-    from every new grid inside the call (2 ms on the 256^3 disk against the 4 ms it saves on
-    a trace of 2^26 packets); sky=0 walks every ray instead."""
+    construction.  The bound map of rays from the source (for a point source) and the
+    observer's tail map are rebuilt from every new grid inside the call; sky=0 walks every
+    ray, tail=False walks every peel-off to the edge."""
 
     def __init__(self, prob: scenes.Problem, max_packets: int, *, precision: str = "f32",
-                 frac_bits: int | None = None, sky: int | None = None):
+                 frac_bits: int | None = None, sky: int | None = None, tail: bool | None = None):
         torch = _torch()
         if prob.max_orders > 1:
             raise QmcrtError(ERR_UNSUPPORTED, "HostRenderer renders single scattering")
-        self.scene = Scene(prob, sky=sky)
+        self.scene = Scene(prob, sky=sky, tail=tail)
         self.precision = precision
         self.frac_bits = default_frac_bits(prob, max_packets) if frac_bits is None else frac_bits
         self.buf = self.scene.accum_buffer("i64")
@@ -768,7 +829,9 @@ class HostRenderer:
                   d_k=None if sc.grid is None else sc.grid.data_ptr(), d_accum=self.buf.data_ptr(),
                   d_image=self.out.data_ptr(), h_image=host_out.data_ptr(),
                   d_sky_ws=None if sc.sky is None else sc.sky_ws.data_ptr(),
-                  sky_ws_bytes=0 if sc.sky is None else sc.sky_ws_bytes)
+                  sky_ws_bytes=0 if sc.sky is None else sc.sky_ws_bytes,
+                  d_tail_ws=None if sc.tail is None else sc.tail_ws.data_ptr(),
+                  tail_ws_bytes=0 if sc.tail is None else sc.tail_ws_bytes)
         pts = points_desc(p.generator, p.dims, first, count, "f64", p.seed, p.total_n)
         qmcrt_render_single_host(sc.medium, sc.source, sc.dust, sc.obs, pts, sc.opts(self.precision), io,
                                  self.frac_bits, 1.0 / count, _stream(stream))
@@ -839,6 +902,7 @@ class Batch:
             dust = _new(qmcrt_dust, albedo=I.albedo, g=I.g, p_l=self.prob.p_l)
             obs = qmcrt_observer.from_buffer_copy(sc.obs)
             obs.theta = I.theta_obs
+            obs.d_tail = None  # the scene's tail map is for its own direction
             pts = points_desc(self.prob.generator, self.prob.dims, I.first_index, n, "f64", self.prob.seed,
                               I.first_index + n - 1)
             img = _new(qmcrt_image, accum=ACCUM["i64"], d_accum=self.accum[k].data_ptr(), n_images=1,

@@ -36,7 +36,7 @@ def test_library_exports_every_declared_symbol(lib):
     for name in declared_functions():
         assert hasattr(lib, name), name
     assert sorted(Q.EXPORTED) == sorted(declared_functions())
-    assert lib.qmcrt_abi_version() == 2
+    assert lib.qmcrt_abi_version() == 3
 
 
 STRUCTS = ["qmcrt_points_desc", "qmcrt_medium", "qmcrt_source", "qmcrt_dust", "qmcrt_observer", "qmcrt_image",
@@ -111,6 +111,7 @@ BAD_TRACE = [
     dict(obs__splat=3), dict(pts__first_index=0), dict(pts__dims=2), dict(img__d_accum=None), dict(img__frac_bits=63),
     dict(img__accum=5), dict(img__n_images=2), dict(opts__precision=7), dict(opts__block_size=48),
     dict(medium__kind=0), dict(medium__kscale=0.0), dict(source__kind=1), dict(opts__tau_min=-1.0),
+    dict(obs__d_tail=0x7000),  # a tail map over an analytic sphere
 ]
 
 
@@ -330,6 +331,43 @@ def test_sky_bound_validation(lib):
         g["medium"].lo[a], g["medium"].hi[a] = -1.0, 1.0
     _expect(Q.ERR_INVALID_ARG, Q.qmcrt_trace_single, g["medium"], g["source"], g["dust"], g["obs"], g["pts"],
             g["opts"], g["img"], 0, 0)
+
+
+def _padded_grid_descs(**over):
+    base = dict(medium__kind=Q.MEDIUM_GRID, medium__d_k=0x5000, medium__nx=6, medium__ny=5, medium__nz=7,
+                medium__pad=Q.MIN_PAD)
+    base.update(over)
+    g = _descs(**base)
+    for a in range(3):
+        g["medium"].lo[a], g["medium"].hi[a] = -1.0, 1.0
+    return g
+
+
+def test_tail_map_validation(lib):
+    assert Q.qmcrt_tail_map_bytes(6, 5, 7, 4) == 14 * 13 * 15
+    assert Q.qmcrt_tail_map_bytes(0, 5, 7, 4) == 0
+    ws = Q.qmcrt_tail_workspace_bytes(6, 5, 7)
+    assert ws == 2 * ((2 * 2 * 2 * 4 + 255) // 256 * 256)  # two arrays of 4^3-cell block values
+    assert Q.qmcrt_tail_workspace_bytes(6, 5, 0) == 0
+    g = _padded_grid_descs()
+    _expect(Q.ERR_INVALID_ARG, Q.qmcrt_tail_map, g["medium"], g["obs"], 0, 0x2000, ws)  # no map
+    _expect(Q.ERR_INVALID_ARG, Q.qmcrt_tail_map, g["medium"], g["obs"], 0x1000, 0, ws)  # no workspace
+    _expect(Q.ERR_INVALID_ARG, Q.qmcrt_tail_map, g["medium"], g["obs"], 0x1000, 0x2010, ws)  # misaligned
+    _expect(Q.ERR_INVALID_ARG, Q.qmcrt_tail_map, g["medium"], g["obs"], 0x1000, 0x2000, ws - 1)
+    for over in (dict(medium__pad=0), dict(medium__pad=Q.MIN_PAD - 1), dict(medium__kind=Q.MEDIUM_SPHERE),
+                 dict(medium__d_k=None), dict(medium__nz=0), dict(obs__theta=float("nan")),
+                 dict(obs__phi=float("inf")), dict(medium__struct_size=8), dict(obs__struct_size=8)):
+        b = _padded_grid_descs(**over)
+        _expect(Q.ERR_INVALID_ARG, Q.qmcrt_tail_map, b["medium"], b["obs"], 0x1000, 0x2000, ws)
+    b = _padded_grid_descs()
+    b["medium"].hi[1] = -1.0
+    _expect(Q.ERR_INVALID_ARG, Q.qmcrt_tail_map, b["medium"], b["obs"], 0x1000, 0x2000, ws)
+    # a trace rejects a tail map on an unpadded grid and a tolerance that is negative or NaN
+    for over in (dict(medium__pad=0, obs__d_tail=0x7000), dict(obs__d_tail=0x7000, opts__tail_eps=-1e-9),
+                 dict(obs__d_tail=0x7000, opts__tail_eps=float("nan"))):
+        b = _padded_grid_descs(**over)
+        _expect(Q.ERR_INVALID_ARG, Q.qmcrt_trace_single, b["medium"], b["source"], b["dust"], b["obs"], b["pts"],
+                b["opts"], b["img"], 0, 0)
 
 
 def test_batch_validation(lib):
