@@ -222,12 +222,14 @@ int qmcrt_trace_multiple(const qmcrt_medium *medium, const qmcrt_source *source,
                          const qmcrt_image *image, void *stream);
 
 /* ---- batches of problems in one launch ---- */
-typedef struct qmcrt_instance {  /* device-resident table entry, 64 bytes */
+typedef struct qmcrt_instance {  /* device-resident table entry, 72 bytes */
     double theta, phi;       /* direction toward this instance's observer */
     double albedo, g, p_l;   /* dust at this instance's wavelength (as qmcrt_dust) */
     double kscale;           /* opacity multiplier (times qmcrt_medium.kscale) */
     uint64_t first_index;    /* first point index (>= 1); aligned to count keeps chunks full */
     uint64_t count;          /* packet budget */
+    const uint8_t *d_tail;   /* optional (NULL): qmcrt_tail_map of this direction on the medium's padded grid
+                                (as qmcrt_observer.d_tail, with opts->tail_eps; unused on a plain grid) */
 } qmcrt_instance;
 
 typedef struct qmcrt_batch_config {

@@ -387,6 +387,9 @@ int fill_trace(const qmcrt_medium *md, const qmcrt_source *src, const qmcrt_dust
     if (op->block_size != 0 && (op->block_size % 32 != 0 || op->block_size < 32 || op->block_size > 256))
         return fail(QMCRT_ERR_INVALID_ARG, "block_size must be a multiple of 32 in 32..256");
     P.tau_min = (T)op->tau_min;
+    if (!(op->tail_eps >= 0) || !std::isfinite(op->tail_eps))
+        return fail(QMCRT_ERR_INVALID_ARG, "tail_eps must be finite and >= 0");
+    P.tail_eps = op->tail_eps;
     P.max_orders = multiple ? op->max_orders : 1;
     if (multiple) {
         if (op->max_orders < 1 || op->max_orders > 64) return fail(QMCRT_ERR_INVALID_ARG, "max_orders outside 1..64");

@@ -74,7 +74,9 @@ __device__ __forceinline__ void set_instance(TraceP<T> &P, const TraceP<T> &base
     P.obs.ey[1] = (T)(-ct * sp);
     P.obs.ey[2] = (T)st;
     for (int a = 0; a < 3; ++a) P.obs.inv_k[a] = T(1) / P.obs.k[a];
-    P.obs.tail = nullptr;  // a tail map holds for one direction only
+    // a tail map holds for one direction: the instance's own, if it has one
+    P.obs.tail = base.med.pad ? I.d_tail : nullptr;
+    P.obs.tail_thr = tail_threshold(base.tail_eps, (double)base.med.kscale * I.kscale);
     // dust
     P.dust.albedo = (T)I.albedo;
     P.dust.g = (T)I.g;

@@ -3,6 +3,7 @@
 // passed to its kernel by value (one constant-bank parameter, no device allocation).
 #pragma once
 
+#include <cmath>
 #include <cstddef>
 #include <cstdint>
 
@@ -128,6 +129,7 @@ struct TraceP {
     float *train_log;        // optional [count][4]: coordinates used, total peel-off intensity
     int max_orders, force_all, per_order;
     T rr_threshold, rr_survival, inv_rr_survival;
+    double tail_eps;         // peel-off depth a tail map lets a walk leave out (with kscale)
 };
 
 // Observers fed by one trace (qmcrt_trace_observers); image o is the stack that
@@ -190,7 +192,14 @@ uint64_t tail_workspace_bytes(int nx, int ny, int nz);
 cudaError_t launch_tail_map(const float *k_padded, int nx, int ny, int nz, int pad, const double lo[3],
                             const double hi[3], const double dir[3], uint8_t *map, void *ws, cudaStream_t s);
 // Largest code a walk may stop at for a depth tolerance eps (with kscale): 0 when eps is 0.
-int tail_threshold(double eps, double kscale);
+__host__ __device__ inline int tail_threshold(double eps, double kscale)
+{
+    if (!(eps > 0)) return 0;
+    int e;
+    frexp(eps / kscale, &e);  // eps / kscale = m 2^e, 1/2 <= m < 1: 2^(e-1) <= it
+    const int c = e - 1 + 150;
+    return c < 0 ? 0 : (c > 254 ? 254 : c);
+}
 cudaError_t launch_image_reduce(const void *acc, int mode, double frac_scale, size_t elems, int replicas,
                                 double scale, double *out, cudaStream_t s);
 cudaError_t launch_trace_single_f32(const TraceP<float> &p, int block, cudaStream_t s);

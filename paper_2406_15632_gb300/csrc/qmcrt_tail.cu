@@ -137,14 +137,6 @@ uint64_t tail_workspace_bytes(int nx, int ny, int nz)
     return 2 * aligned(blocks * sizeof(float));
 }
 
-int tail_threshold(double eps, double kscale)
-{
-    if (!(eps > 0)) return 0;
-    int e;
-    std::frexp(eps / kscale, &e);  // eps / kscale = m 2^e, 1/2 <= m < 1: 2^(e-1) <= it
-    return std::min(254, std::max(0, e - 1 + 150));
-}
-
 cudaError_t launch_tail_map(const float *k_padded, int nx, int ny, int nz, int pad, const double lo[3],
                             const double hi[3], const double dir[3], uint8_t *map, void *ws, cudaStream_t s)
 {

@@ -85,7 +85,8 @@ class qmcrt_trace_opts(C.Structure):
 
 class qmcrt_instance(C.Structure):
     _fields_ = [("theta", C.c_double), ("phi", C.c_double), ("albedo", C.c_double), ("g", C.c_double),
-                ("p_l", C.c_double), ("kscale", C.c_double), ("first_index", C.c_uint64), ("count", C.c_uint64)]
+                ("p_l", C.c_double), ("kscale", C.c_double), ("first_index", C.c_uint64), ("count", C.c_uint64),
+                ("d_tail", C.c_void_p)]
 
 
 class qmcrt_batch_config(C.Structure):
@@ -845,16 +846,20 @@ class Batch:
 
     def __init__(self, prob: scenes.Problem, instances, *, precision: str = "f32", chunk_log2: int = 16,
                  block_size: int = 256, ctas_per_sm: int = 0, packets_per_thread: int = 4,
-                 frac_bits: int | None = None, scene: "Scene | None" = None):
+                 frac_bits: int | None = None, scene: "Scene | None" = None, tails: bool = True):
         torch = _torch()
         self.prob = prob
         self.scene = scene or Scene(prob)
         self.precision = precision
         self.n = len(instances)
         table = (qmcrt_instance * self.n)()
+        self.tails = []  # the tail map of each instance's direction (scene.tail_for), or None
         for t, I in zip(table, instances):
             t.theta, t.phi, t.albedo, t.g = I.theta_obs, prob.phi_obs, I.albedo, I.g
             t.p_l, t.kscale, t.first_index, t.count = prob.p_l, I.kscale, I.first_index, I.n_packets
+            m = self.scene.tail_for(I.theta_obs, prob.phi_obs) if tails else None
+            t.d_tail = None if m is None else m.data_ptr()
+            self.tails.append(m)
         raw = torch.frombuffer(bytearray(bytes(table)), dtype=torch.uint8)
         self.d_inst = raw.to("cuda")
         self.counts = [I.n_packets for I in instances]
@@ -902,7 +907,7 @@ class Batch:
             dust = _new(qmcrt_dust, albedo=I.albedo, g=I.g, p_l=self.prob.p_l)
             obs = qmcrt_observer.from_buffer_copy(sc.obs)
             obs.theta = I.theta_obs
-            obs.d_tail = None  # the scene's tail map is for its own direction
+            obs.d_tail = None if self.tails[k] is None else self.tails[k].data_ptr()  # this direction's map
             pts = points_desc(self.prob.generator, self.prob.dims, I.first_index, n, "f64", self.prob.seed,
                               I.first_index + n - 1)
             img = _new(qmcrt_image, accum=ACCUM["i64"], d_accum=self.accum[k].data_ptr(), n_images=1,

@@ -45,7 +45,7 @@ def alone(Q, prob, I, fb, precision):
     import torch
 
     p = prob.replace(theta_obs=I.theta_obs, albedo=I.albedo, g=I.g, kscale=prob.kscale * I.kscale)
-    sc = Q.Scene(p, tail=False)  # a batch's instances walk their peel-offs to the edge
+    sc = Q.Scene(p)  # with the tail map of its direction, as the batch's instance
     buf = sc.accum_buffer("i64")
     if I.n_packets:
         sc.trace(I.first_index, I.n_packets, buf, frac_bits=fb, precision=precision)
