@@ -795,10 +795,11 @@ def main():
     clk = clocks.summary()
     max_mhz = peaks.get("sm_max_mhz", 2070.0)
     peak_ops = SMS * LANES_PER_SM * max_mhz * 1e6
-    # the tracer skips, from one lookup of the bound map, the rays that cannot scatter, and
-    # resumes each march from a boundary of the first walk: its algorithmic work is the
-    # oracle's count of the other rays' walks with each cell of a ray walked once
-    cpp = cells_per_packet(key="cells_per_packet_scattering_rays_single_pass")
+    # the tracer skips, from one lookup of the bound map, the rays that cannot scatter,
+    # resumes each march from a boundary of the first walk and ends each peel-off walk on
+    # the tail map: its algorithmic work is the oracle's count of the other rays' walks with
+    # each cell of a ray walked once and the peel-offs' cells whose depth can matter
+    cpp = cells_per_packet(key="cells_per_packet_scattering_rays_single_pass_tail")
     kern_avg_s = kern_total / args.steps / 1e3
     achieved_ops = n * (cpp * OPS_PER_CELL + OPS_PER_PACKET) / kern_avg_s
     traffic = profiled_traffic()
@@ -810,7 +811,8 @@ def main():
                      "frac": achieved_ops / peak_ops, "traffic": traffic,
                      "kernel": "k_trace_single<float>", "kernel_ms": kern_avg_s * 1e3,
                      "per_unit": f"{OPS_PER_CELL} ops per cell visit x {cpp:.2f} cells per packet (oracle count "
-                                 f"of the walks of rays with tau_1 >= tau_min, without the march's second pass) "
+                                 f"of the walks of rays with tau_1 >= tau_min, without the march's second pass and "
+                                 f"the peel-off cells past a remaining depth of 2^-24) "
                                  f"+ {OPS_PER_PACKET} ops of setup per packet",
                      "peak_basis": f"{SMS} SMs x {LANES_PER_SM} lanes x {max_mhz:.0f} MHz (measured max clock)"},
         "e2e": {"value": e2e_value, "unit": "packets/s", "h2d_bytes_per_step": R.input_bytes(),

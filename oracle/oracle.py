@@ -109,6 +109,7 @@ def lib():
             L.or_direct_light.argtypes = [P, i32, C.c_double, dp]
             L.or_tau_ray.restype = C.c_double
             L.or_tau_ray.argtypes = [P, dp, dp]
+            L.or_ray_cells.argtypes = [P, dp, dp, C.c_double, dp]
             L.or_march_ray.argtypes = [P, dp, dp, C.c_double, dp]
             L.or_scatter_packet.argtypes = [P, C.c_double, C.c_double, dp, dp, dp]
             L.or_peel_packet.argtypes = [P, dp, dp, dp, dp, dp]
@@ -347,6 +348,21 @@ def _vec(v):
 def tau_ray(prob, p, d) -> float:
     h = _Holder(prob)
     return lib().or_tau_ray(h.ptr, _vec(p), _vec(d))
+
+
+def ray_cells(prob, points, d, eps: float):
+    """For walks from each of points [n][3] along d: the cells each visits, and how many
+    come before the optical depth still ahead is at most eps (what a walk allowed to leave
+    out eps must visit); int arrays [n][2]."""
+    h = _Holder(prob)
+    out = _D3()
+    dv = _vec(d)
+    res = np.zeros((len(points), 2), dtype=np.int64)
+    for j, p in enumerate(points):
+        if lib().or_ray_cells(h.ptr, _vec(p), dv, float(eps), out) != 0:
+            raise RuntimeError("oracle ray_cells needs a grid medium")
+        res[j] = int(out[0]), int(out[1])
+    return res
 
 
 def march_ray(prob, p, d, tau):

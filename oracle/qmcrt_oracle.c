@@ -480,6 +480,9 @@ static int or_start_cell(double x, double lo, double h, double dir)
  * algorithm's work, reported in the packet log). */
 static _Thread_local long long or_cells_visited;
 static _Thread_local long long or_cells_marched; /* of those, visited by forced-step marches */
+/* optional record of each cell's optical depth along one walk (or_ray_cells) */
+static _Thread_local double *or_dtau_log;
+static _Thread_local long long or_dtau_cap, or_dtau_n;
 
 static int or_grid_walk(const or_medium *M, const double p[3], const double d[3], double target,
                         double *tau_sum, double *t_hit, double *t_last)
@@ -509,6 +512,7 @@ static int or_grid_walk(const or_medium *M, const double p[3], const double d[3]
         double kc = M->kscale * (double)M->k[((size_t)c[2] * M->n[1] + c[1]) * M->n[0] + c[0]];
         double dtau = (te - t) * kc;
         ++or_cells_visited;
+        if (or_dtau_log && or_dtau_n < or_dtau_cap) or_dtau_log[or_dtau_n++] = dtau;
         if (target >= 0 && kc > 0 && tau + dtau >= target) {
             *t_hit = t + (target - tau) / kc;
             *tau_sum = target;
@@ -1112,6 +1116,31 @@ int or_trace_multiple_cells(const or_problem *Pr, uint64_t first, uint64_t count
 double or_tau_ray(const or_problem *Pr, const double p[3], const double d[3])
 {
     return or_tau_to_edge(&Pr->medium, p, d);
+}
+/* Cells the walk from p along d to the edge of a grid visits (out[0]), and how many of them
+ * come before the optical depth still ahead falls to eps or below (out[1]): the cells a walk
+ * that may leave out eps of its depth must visit.  Returns -1 for a sphere medium. */
+int or_ray_cells(const or_problem *Pr, const double p[3], const double d[3], double eps, double out[2])
+{
+    const or_medium *M = &Pr->medium;
+    if (M->kind != OR_MEDIUM_GRID) return -1;
+    or_dtau_cap = (long long)M->n[0] + M->n[1] + M->n[2] + 3;
+    or_dtau_log = malloc((size_t)or_dtau_cap * sizeof(double));
+    if (!or_dtau_log) return -1;
+    or_dtau_n = 0;
+    or_tau_to_edge(M, p, d);
+    long long n = or_dtau_n, needed = n;
+    double rest = 0.0;
+    for (long long j = n - 1; j >= 0; --j) {
+        rest += or_dtau_log[j];
+        if (!(rest <= eps)) break;
+        needed = j;
+    }
+    free(or_dtau_log);
+    or_dtau_log = NULL;
+    out[0] = (double)n;
+    out[1] = (double)needed;
+    return 0;
 }
 int or_march_ray(const or_problem *Pr, const double p[3], const double d[3], double tau, double q[3])
 {

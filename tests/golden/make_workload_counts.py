@@ -5,6 +5,7 @@ per-unit figure of the roofline.  Calls only oracle/ and the scene generators.
     python tests/golden/make_workload_counts.py
 """
 import json
+import math
 import os
 import sys
 
@@ -15,6 +16,15 @@ from oracle import oracle as O  # noqa: E402
 from paper_2406_15632_gb300 import scenes as S  # noqa: E402
 
 N = 1 << 18
+
+
+def peel_left_out(prob, log, eps):
+    """Mean over all packets of the peel-off cells a walk may leave out at tolerance eps."""
+    ok = log[:, 8] == 0
+    th, ph = prob.theta_obs, prob.phi_obs
+    k = [math.sin(th) * math.cos(ph), math.sin(th) * math.sin(ph), math.cos(th)]
+    cells = O.ray_cells(prob, log[ok, :3], k, eps)
+    return float((cells[:, 0] - cells[:, 1]).sum()) / len(log)
 
 
 def main():
@@ -29,6 +39,10 @@ def main():
         # and when the march to the scattering point does not walk again the cells of the
         # first walk that lie before it (each cell of the ray is walked once, plus the peel-off)
         "cells_per_packet_scattering_rays_single_pass": float(((log[:, 9] - log[:, 10]) * (log[:, 8] != 1)).mean()),
+        # and when each peel-off walk ends once the depth still ahead is at most 2^-24 (the
+        # FP32 tolerance of the tracer's tail maps): the cells it must visit
+        "cells_per_packet_scattering_rays_single_pass_tail": float(
+            ((log[:, 9] - log[:, 10]) * (log[:, 8] != 1)).mean() - peel_left_out(prob, log, 2.0 ** -24)),
         "packets": N,
         "contributing_fraction": float((log[:, 8] == 0).mean()),
         "note": "256^3 flared disk, point source, Sobol indices 1..2^18, all three walks per packet",

@@ -152,3 +152,19 @@ def test_clumpy_grid_mean_radial_tau_is_five():
     rng = np.random.default_rng(0)
     taus = [O.tau_ray(prob, [0.0, 0.0, 0.0], random_unit(rng)) for _ in range(400)]
     assert np.mean(taus) == pytest.approx(5.0, rel=0.25)
+
+
+def test_ray_cells_counts_the_cells_a_tolerance_leaves_out():
+    """Along a row of known cells: the walk from the middle of cell 1 visits cells 1..7;
+    with a tolerance it may leave out the trailing cells whose depths sum to at most it."""
+    n = 8
+    h = 2.0 / n
+    g = np.zeros((n, n, n), dtype=np.float32)
+    g[3, 3, :] = [5.0, 2.0, 0.0, 3.0, 1e-9, 0.0, 0.0, 0.0]
+    prob = S.Problem(grid=g)
+    p = [-1.0 + 1.5 * h, -1.0 + 3.5 * h, -1.0 + 3.5 * h]
+    d = [1.0, 0.0, 0.0]
+    depths = [2.0 * h / 2, 0.0, 3.0 * h, 1e-9 * h, 0.0, 0.0, 0.0]
+    assert O.tau_ray(prob, p, d) == pytest.approx(sum(depths), rel=1e-6)
+    for eps, needed in ((0.0, 4), (1.01e-9 * h, 3), (0.99e-9 * h, 4), (3.0 * h * 1.0001, 1), (10.0, 0)):
+        assert O.ray_cells(prob, [p], d, eps).tolist() == [[7, needed]], eps
