@@ -5,12 +5,12 @@
 // but from the second order on each lane scatters into its own direction and the warp
 // waits for its longest walk.  Here every order is a launch over the packets still
 // alive, and between orders the live packets are regrouped by a key built from their
-// position (its octant) and their new direction (32 bins in cos theta x 64 in phi), so a
-// warp again traces 32 similar rays:
+// position (one of 16^3 cells of the box) and their new direction (32 bins in cos theta
+// x 64 in phi), so a warp again traces 32 similar rays:
 //
 //   order 1:   emission, forced step, peel-off, roulette, scattering for order 2 ->
 //              queue (with each packet's key, counted in the bucket histogram)
-//   order k:   bucket offsets (one block, shared memory) -> record indices into
+//   order k:   bucket offsets (a tiled scan) -> record indices into
 //              buckets -> forced step (or march), peel-off, roulette, scattering for
 //              k+1 -> the other queue
 //
@@ -30,15 +30,19 @@ namespace qmcrt {
 
 namespace {
 
-// Key split measured on the clumpy envelope (2^24 packets, 20 orders): the octant of
-// the position with 32 x 64 direction bins beats 8^3 position cells with 4 x 8 direction
-// bins by 2 % (walks from one octant in one direction cross nearly the same cells).
-constexpr int WV_POS_BITS = 1;  // per axis: the octant
+// Key split measured on the clumpy envelope (2^24 packets, 20 orders): 16^3 position
+// cells with 32 x 64 direction bins (2^23 buckets, position-major) take 77 ms, against
+// 89 ms for the octant with the same direction bins (2^14 buckets) and 80 ms for 8^3
+// cells; finer direction bins or position cells gain nothing more (77-79 ms), 2^25 buckets
+// lose it again to the histogram's clearing and scan (83 ms).  Packets that start close
+// together in nearly one direction cross nearly the same cells, so a warp's loads share
+// cache lines.
+constexpr int WV_POS_BITS = 4;  // per axis: 16 position cells
 constexpr int WV_COS_BITS = 5;  // direction bins: 32 in cos theta
 constexpr int WV_PHI_BITS = 6;  //                 x 64 in phi
 constexpr int WV_KEY_BITS = 3 * WV_POS_BITS + WV_COS_BITS + WV_PHI_BITS;
 constexpr int WV_BUCKETS = 1 << WV_KEY_BITS;
-static_assert(WV_KEY_BITS == 14, "the shared-memory scan holds 2^14 buckets");
+static_assert(WV_KEY_BITS >= 20 && WV_KEY_BITS <= 30, "the scan takes 1024-bucket tiles, their totals in one block");
 
 template <class T>
 struct Packet {
@@ -219,34 +223,53 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_wave_first(cons
     if (live && !on && P.train_log) write_log(P, i, j, p);
 }
 
-// Exclusive scan of the bucket histogram into cursors, in shared memory (one block of
-// 1024 threads, 16 buckets each).
-__global__ void __launch_bounds__(1024) k_wave_scan(uint32_t *hist)
+// Exclusive scan of the bucket histogram into cursors, in three launches: each block scans
+// a tile of 1024 buckets in shared memory and records the tile's total; one block scans
+// the totals; every bucket then adds its tile's offset.
+__global__ void __launch_bounds__(1024) k_wave_scan_tiles(uint32_t *hist, uint32_t *tile_sum)
 {
-    __shared__ uint32_t h[WV_BUCKETS];
-    __shared__ uint32_t part[1024];
-    constexpr int PER = WV_BUCKETS / 1024;
+    __shared__ uint32_t s[1024];
     const int t = threadIdx.x;
-    for (int b = t; b < WV_BUCKETS; b += 1024) h[b] = hist[b];
-    __syncthreads();
-    uint32_t s = 0;
-    for (int b = 0; b < PER; ++b) s += h[t * PER + b];
-    part[t] = s;
+    const size_t b = (size_t)blockIdx.x * 1024 + t;
+    const uint32_t x = hist[b];
+    s[t] = x;
     __syncthreads();
     for (int off = 1; off < 1024; off <<= 1) {
-        const uint32_t v = t >= off ? part[t - off] : 0u;
+        const uint32_t v = t >= off ? s[t - off] : 0u;
         __syncthreads();
-        part[t] += v;
+        s[t] += v;
         __syncthreads();
     }
-    uint32_t run = t ? part[t - 1] : 0u;
-    for (int b = 0; b < PER; ++b) {
-        const uint32_t x = h[t * PER + b];
-        h[t * PER + b] = run;
+    hist[b] = s[t] - x;
+    if (t == 1023) tile_sum[blockIdx.x] = s[1023];
+}
+
+// exclusive scan of the n tile totals (n a multiple of 1024), one block
+__global__ void __launch_bounds__(1024) k_wave_scan_sums(uint32_t *tile_sum, int n)
+{
+    __shared__ uint32_t s[1024];
+    const int t = threadIdx.x, per = n / 1024;
+    uint32_t tot = 0;
+    for (int q = 0; q < per; ++q) tot += tile_sum[t * per + q];
+    s[t] = tot;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const uint32_t v = t >= off ? s[t - off] : 0u;
+        __syncthreads();
+        s[t] += v;
+        __syncthreads();
+    }
+    uint32_t run = s[t] - tot;
+    for (int q = 0; q < per; ++q) {
+        const uint32_t x = tile_sum[t * per + q];
+        tile_sum[t * per + q] = run;
         run += x;
     }
-    __syncthreads();
-    for (int b = t; b < WV_BUCKETS; b += 1024) hist[b] = h[b];
+}
+
+__global__ void __launch_bounds__(1024) k_wave_scan_add(uint32_t *hist, const uint32_t *tile_sum)
+{
+    hist[(size_t)blockIdx.x * 1024 + threadIdx.x] += tile_sum[blockIdx.x];
 }
 
 // Bucket order of the appended records: perm[cursor of its key] = record index, one
@@ -329,7 +352,7 @@ WaveWork<T> carve(void *ws, uint64_t cap)
     W.count = (uint32_t *)take(3 * 4);
     W.keys = (uint32_t *)take(cap * 4);
     W.perm = (uint32_t *)take(cap * 4);
-    W.hist = (uint32_t *)take(WV_BUCKETS * 4);
+    W.hist = (uint32_t *)take(WV_BUCKETS * 4 + WV_BUCKETS / 256);
     return W;
 }
 
@@ -348,7 +371,9 @@ cudaError_t launch_wave(const TraceP<T> &P, void *ws, uint64_t cap, int sms, cud
     for (int k = 2; k <= P.max_orders; ++k) {
         // the queue appended by order k - 1 holds order k's packets with their keys and
         // histogram: their indices in bucket order into perm
-        k_wave_scan<<<1, 1024, 0, s>>>(W.hist);
+        k_wave_scan_tiles<<<WV_BUCKETS / 1024, 1024, 0, s>>>(W.hist, W.hist + WV_BUCKETS);
+        k_wave_scan_sums<<<1, 1024, 0, s>>>(W.hist + WV_BUCKETS, WV_BUCKETS / 1024);
+        k_wave_scan_add<<<WV_BUCKETS / 1024, 1024, 0, s>>>(W.hist, W.hist + WV_BUCKETS);
         k_wave_scatter<T><<<grid, 256, 0, s>>>(W);
         if ((e = cudaMemcpyAsync(W.count, W.count + 1, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
             return e;
@@ -366,7 +391,7 @@ uint64_t wavefront_workspace_bytes(uint64_t cap, int precision)
 {
     const uint64_t rec = precision == QMCRT_PREC_F64 ? sizeof(Rec<double>) : sizeof(Rec<float>);
     auto pad = [](uint64_t b) { return (b + 255) & ~255ull; };
-    return 2 * pad(cap * rec) + pad(12) + 2 * pad(cap * 4) + pad(WV_BUCKETS * 4);
+    return 2 * pad(cap * rec) + pad(12) + 2 * pad(cap * 4) + pad(WV_BUCKETS * 4 + WV_BUCKETS / 256);
 }
 
 cudaError_t launch_trace_wavefront_f32(const TraceP<float> &p, void *ws, uint64_t cap, int sms, cudaStream_t s)
