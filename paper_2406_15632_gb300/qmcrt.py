@@ -593,7 +593,7 @@ class Scene:
             # by default for single scattering: on the 256^3 disk the peel-off walks drop from
             # 13.1 to 10.3 ms per 2^26 packets; in the clumpy envelope, which fills its box's
             # inscribed ball, the map seldom ends a walk and the 2^24-packet wavefront takes
-            # 93.8 ms with it against 88.8 without
+            # 80.7 ms with it against 77.3 without
             tail = prob.max_orders == 1
         if tail and self.padded is not None:
             nz, ny, nx = self.grid.shape
