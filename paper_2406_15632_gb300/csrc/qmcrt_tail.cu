@@ -31,6 +31,8 @@ struct TailGeom {
     int a, b, c;     // slab axis and the two lateral axes
     int sa, sb, sc;  // the direction's signs along them (0: no component)
     int lb, lc;      // lateral blocks a ray from one block can reach along b, c (offsets 0 .. l-1)
+    long long ta, tb, tc;  // block-index steps along a, b, c
+    int na, nbb, nbc;      // blocks along a, b, c
     float path;      // longest path through one slab, rounded up
 };
 
@@ -65,7 +67,7 @@ __global__ void __launch_bounds__(256) k_tail_block_max(const float *__restrict_
 // block of a slab in parallel.
 __global__ void __launch_bounds__(1024) k_tail_slabs(const float *__restrict__ Kb, TailGeom g, float *__restrict__ Bb)
 {
-    const int na = g.nb[g.a], nbb = g.nb[g.b], nbc = g.nb[g.c];
+    const int na = g.na, nbb = g.nbb, nbc = g.nbc;
     const int per_slab = nbb * nbc;
     for (int step = 0; step < na; ++step) {
         const int j = g.sa > 0 ? na - 1 - step : step;  // the exit side first
@@ -79,22 +81,12 @@ __global__ void __launch_bounds__(1024) k_tail_slabs(const float *__restrict__ K
                 for (int oc = 0; oc < g.lc; ++oc) {
                     const int qc = ic + g.sc * oc;
                     if (qc < 0 || qc >= nbc) continue;
-                    int q[3];
-                    q[g.a] = j;
-                    q[g.b] = qb;
-                    q[g.c] = qc;
-                    kmax = fmaxf(kmax, Kb[block_index(g.nb, q[0], q[1], q[2])]);
-                    if (jn >= 0 && jn < na) {
-                        q[g.a] = jn;
-                        nmax = fmaxf(nmax, Bb[block_index(g.nb, q[0], q[1], q[2])]);
-                    }
+                    const long long lat = qb * g.tb + qc * g.tc;
+                    kmax = fmaxf(kmax, Kb[j * g.ta + lat]);
+                    if (jn >= 0 && jn < na) nmax = fmaxf(nmax, Bb[jn * g.ta + lat]);
                 }
             }
-            int q[3];
-            q[g.a] = j;
-            q[g.b] = ib;
-            q[g.c] = ic;
-            Bb[block_index(g.nb, q[0], q[1], q[2])] = __fadd_ru(__fmul_ru(kmax, g.path), nmax);
+            Bb[j * g.ta + ib * g.tb + ic * g.tc] = __fadd_ru(__fmul_ru(kmax, g.path), nmax);
         }
         __syncthreads();
     }
@@ -154,6 +146,13 @@ cudaError_t launch_tail_map(const float *k_padded, int nx, int ny, int nz, int p
     g.b = g.a == 0 ? 1 : 0;
     g.c = g.a == 2 ? 1 : 2;
     auto sgn = [](double v) { return v > 0 ? 1 : (v < 0 ? -1 : 0); };
+    const long long step[3] = {1, g.nb[0], (long long)g.nb[0] * g.nb[1]};
+    g.na = g.nb[g.a];
+    g.nbb = g.nb[g.b];
+    g.nbc = g.nb[g.c];
+    g.ta = step[g.a];
+    g.tb = step[g.b];
+    g.tc = step[g.c];
     g.sa = sgn(dir[g.a]);
     g.sb = sgn(dir[g.b]);
     g.sc = sgn(dir[g.c]);
