@@ -277,6 +277,15 @@ def test_render_single_host_validation(lib):
         b = Q.qmcrt_host_io.from_buffer_copy(ok)
         b.d_sky_ws, b.sky_ws_bytes = ws, nbytes
         _expect(Q.ERR_INVALID_ARG, call, g2, b)
+    # so is a tail map of the observer's direction
+    g3 = _descs(medium__kind=0, medium__d_k=0x5000, medium__nx=4, medium__ny=4, medium__nz=4, medium__pad=8,
+                obs__d_tail=0x9000)
+    for a in range(3):
+        g3["medium"].lo[a], g3["medium"].hi[a] = -1.0, 1.0
+    for ws, nbytes in ((None, 0), (0x8000, 16), (0x8010, 1 << 20)):
+        b = Q.qmcrt_host_io.from_buffer_copy(ok)
+        b.d_tail_ws, b.tail_ws_bytes = ws, nbytes
+        _expect(Q.ERR_INVALID_ARG, call, g3, b)
     for over in BAD_TRACE[:8]:
         _expect(Q.ERR_INVALID_ARG, call, _descs(**over), io)
 
