@@ -620,7 +620,9 @@ class Scene:
         if self.tail is not None:
             qmcrt_tail_map(self.medium, self.obs, self.tail.data_ptr(), self.tail_ws.data_ptr(), self.tail_ws_bytes,
                            _stream(stream))
-            self._tails = {}  # maps toward other observers are rebuilt on demand
+            for (th, ph), t in self._tails.items():  # in place: batches hold their addresses
+                qmcrt_tail_map(self.medium, self._direction(th, ph), t.data_ptr(), self.tail_ws.data_ptr(),
+                               self.tail_ws_bytes, _stream(stream))
 
     def opts(self, precision: str = "f32", block_size: int = 0) -> qmcrt_trace_opts:
         p = self.prob
@@ -671,8 +673,8 @@ class Scene:
                            self.image_desc(buf, accum, frac_bits), _stream(stream))
 
     def tail_for(self, theta: float, phi: float):
-        """The tail map toward (theta, phi) on this scene's grid (built once, rebuilt by
-        repad), or None without a padded grid or with tail maps off."""
+        """The tail map toward (theta, phi) on this scene's grid (built once, rebuilt in place
+        by repad), or None without a padded grid or with tail maps off."""
         if self.tail is None:
             return None
         if theta == self.prob.theta_obs and phi == self.prob.phi_obs:
@@ -681,10 +683,14 @@ class Scene:
         if key not in self._tails:
             torch = _torch()
             t = torch.empty_like(self.tail)
-            obs = _new(qmcrt_observer, splat=self.obs.splat, theta=theta, phi=phi, half_width=1.0, nx=1, ny=1)
-            qmcrt_tail_map(self.medium, obs, t.data_ptr(), self.tail_ws.data_ptr(), self.tail_ws_bytes, 0)
+            qmcrt_tail_map(self.medium, self._direction(*key), t.data_ptr(), self.tail_ws.data_ptr(),
+                           self.tail_ws_bytes, 0)
             self._tails[key] = t
         return self._tails[key]
+
+    def _direction(self, theta: float, phi: float):
+        """An observer struct that only carries a direction (for building its tail map)."""
+        return _new(qmcrt_observer, splat=self.obs.splat, theta=theta, phi=phi, half_width=1.0, nx=1, ny=1)
 
     def observer_array(self, angles, half_widths=None, tails: bool = True):
         """ctypes array of observers at (theta, phi) pairs sharing this problem's image

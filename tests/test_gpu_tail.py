@@ -141,3 +141,29 @@ def test_without_a_tolerance_the_map_leaves_out_only_empty_cells(Q):
     a, b = logs
     assert np.array_equal(a[:, [0, 1, 2, 6, 7, 8]], b[:, [0, 1, 2, 6, 7, 8]])
     assert np.all(np.abs(a[:, 3:6] - b[:, 3:6]) <= 1e-14 * np.abs(b[:, 3:4]))
+
+
+def test_batch_maps_follow_a_new_grid(Q):
+    """A batch keeps the addresses of its instances' tail maps: after the scene's grid
+    changes, repad rebuilds them in place and the batch still equals lone traces of the
+    new grid bit for bit."""
+    import torch
+
+    prob = S.finite_star_disk_problem(n=32, nx=40, ny=36)
+    inst = [S.Instance(theta_obs=th, albedo=0.6, g=0.4, kscale=ks, n_packets=2048, first_index=2048)
+            for th, ks in ((0.3, 1.0), (1.2, 2.0), (2.5, 0.7))]
+    sc = Q.Scene(prob)
+    B = Q.Batch(prob, inst, scene=sc, chunk_log2=10, frac_bits=40)
+    B.run()
+    sc.grid.mul_(3.0)
+    sc.repad()
+    B.run()
+    torch.cuda.synchronize()
+    got = B.accum.cpu().numpy()
+    for k, I in enumerate(inst):
+        p = prob.replace(grid=prob.grid * 3.0, theta_obs=I.theta_obs, albedo=I.albedo, g=I.g, kscale=I.kscale)
+        lone = Q.Scene(p)
+        buf = lone.accum_buffer("i64")
+        lone.trace(I.first_index, I.n_packets, buf, frac_bits=40)
+        torch.cuda.synchronize()
+        assert np.array_equal(got[k], buf[0, 0].cpu().numpy()), k
