@@ -4,6 +4,7 @@
 
 Names:
   disk_single      single scattering, 256^3 flared disk (--grid G: G^3), 256x256 I/Q/U, FP32, 2^L packets
+  star_single      the same disk lit by the finite limb-darkened star (inverse order), 2^L packets
   clumpy_multiple  multiple scattering (20 orders), 128^3 clumpy envelope, 512x512, 2^L packets
   clumpy_wavefront the same packets order by order (live packets regrouped between orders)
   warp_forward     fused forward of the learned warp on 2^L Sobol points
@@ -41,8 +42,8 @@ def main(argv=None) -> int:
     from . import scenes as S
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("name", choices=["disk_single", "clumpy_multiple", "clumpy_wavefront", "warp_forward", "warp_train",
-                                     "batch"])
+    ap.add_argument("name", choices=["disk_single", "star_single", "clumpy_multiple", "clumpy_wavefront",
+                                     "warp_forward", "warp_train", "batch"])
     ap.add_argument("--log2-n", type=int, default=20)
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--instances", type=int, default=0, help="batch: the first N instances only (0: all 256)")
@@ -51,8 +52,10 @@ def main(argv=None) -> int:
     Q.load()
     n = 1 << a.log2_n
     t0 = time.perf_counter()
-    if a.name in ("disk_single", "clumpy_multiple"):
-        prob = S.flared_disk_problem(n=a.grid or 256) if a.name == "disk_single" else S.clumpy_problem(n=128)
+    if a.name in ("disk_single", "star_single", "clumpy_multiple"):
+        prob = {"disk_single": lambda: S.flared_disk_problem(n=a.grid or 256),
+                "star_single": lambda: S.finite_star_disk_problem(n=a.grid or 256),
+                "clumpy_multiple": lambda: S.clumpy_problem(n=128)}[a.name]()
         sc = Q.Scene(prob)
         fb = Q.default_frac_bits(prob, n)
         buf = sc.accum_buffer("i64")
