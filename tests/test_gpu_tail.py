@@ -30,8 +30,21 @@ def _uneven():
     return S.Problem(grid=g.astype(np.float32), lo=(-1.0, -0.4, -2.0), hi=(1.5, 0.8, 0.7))
 
 
+def _blobs():
+    """Dense boxes in an empty box of unequal cells (15 x 12 x 13): the bound is tight, so a
+    block a walk can reach but the map leaves out shows."""
+    rng = np.random.default_rng(5)
+    g = np.zeros((13, 12, 15), dtype=np.float32)
+    for _ in range(8):
+        size = rng.integers(2, 7, size=3)
+        at = rng.integers(0, np.array(g.shape) - size + 1)
+        g[at[0]:at[0] + size[0], at[1]:at[1] + size[1], at[2]:at[2] + size[2]] = rng.uniform(0.5, 4.0)
+    return S.Problem(grid=g, lo=(-1.2, -0.9, -1.0), hi=(1.0, 1.1, 0.8))
+
+
 MEDIA = {
     "disk": S.flared_disk_problem(n=32, nx=16, ny=16),
+    "blobs": _blobs(),
     "fractal": S.fractal_cloud_problem(n=24, nx=16, ny=16),
     "clumpy": S.clumpy_problem(n=16, max_orders=1, nx=16, ny=16),
     "uneven": _uneven(),
